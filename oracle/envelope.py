@@ -1,0 +1,78 @@
+"""Gradient of the Active Set bound at fixed duals (oracle; test infrastructure only).
+
+The paper does not differentiate its bounds. The quantity here is the envelope (Danskin) gradient:
+d(theta) = min over (x, z) of L(x, z, alpha, beta; theta) at fixed duals alpha, beta and fixed
+masks I, with the intermediate bounds lhat, uhat, l_k, u_k (k >= 1) held fixed and the signs of W
+held fixed. theta is the weights and biases of every layer and the input box (l_0, u_0). Where the
+minimiser is unique, dd/dtheta = dL/dtheta at (x*, z*), using the constraint form of L (App. D):
+  dW_k[i, j] = (alpha - beta_1)[i] x_{k-1}[j]
+               + sum_I beta_I[i] ( I[i,j] ((1 - z[i]) Lcheck[i,j] - x_{k-1}[j])
+                                   - z[i] (1 - I[i,j]) Ucheck[i,j] )
+  db_k[i]    = (alpha - beta_1)[i] - sum_I beta_I[i] z[i]
+  dW_n       = x_{n-1}*,  db_n = 1           (the property-folded output row)
+  dl_0[j]    = -f_0[j] [x_0*[j] = l_0[j]] + sum_i sum_I beta_I[i] ( (1 - z[i]) W I [W >= 0]
+                                                                  - z[i] W (1 - I) [W < 0] )[i, j]
+  du_0[j]    = -f_0[j] [x_0*[j] = u_0[j]] + sum_i sum_I beta_I[i] ( (1 - z[i]) W I [W < 0]
+                                                                  - z[i] W (1 - I) [W >= 0] )[i, j]
+(the last terms come from Lcheck and Ucheck of layer 1, which are built from l_0 and u_0).
+Parity unpinned against the paper (it has no such gradient); pinned by finite differences.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import dual as du
+from . import relaxation as rx
+
+
+def envelope_gradient(P, st: du.DualState):
+    """Returns dict: dW[k] dense (k = 1..n), db[k], dlo0, dhi0 for one subproblem."""
+    val, f, g, x, z = du.evaluate(P, st)
+    n = P.n
+    dW, db = [None] * (n + 1), [None] * (n + 1)
+    for k in range(1, n):
+        W = P.W[k]
+        Lc, Uc = rx.interval_matrices(W, P.lo[k - 1], P.hi[k - 1])
+        r = st.alpha[k] - st.beta1[k]
+        G = np.outer(r, x[k - 1])
+        gb = r.copy()
+        for sl in st.slots[k]:
+            If = sl.I.astype(np.float64)
+            G += sl.beta[:, None] * (If * ((1 - z[k])[:, None] * Lc - x[k - 1][None, :])
+                                     - z[k][:, None] * (1 - If) * Uc)
+            gb -= sl.beta * z[k]
+        dW[k], db[k] = G, gb
+    dW[n] = x[n - 1][None, :].copy()
+    db[n] = np.ones(1)
+    W1 = P.W[1]
+    pos = W1 >= 0
+    dlo = -f[0] * (x[0] == P.lo[0]) if n >= 1 else None
+    dhi = -f[0] * (x[0] == P.hi[0])
+    # where l_0 = u_0 both indicators hold; the box then moves as one point and f_0 enters once
+    same = P.lo[0] == P.hi[0]
+    dlo = np.where(same, -f[0] * 0.5, dlo)
+    dhi = np.where(same, -f[0] * 0.5, dhi)
+    if n >= 2:
+        for sl in st.slots[1]:
+            If = sl.I.astype(np.float64)
+            a = (1 - z[1])[:, None] * W1 * If
+            c = z[1][:, None] * W1 * (1 - If)
+            dlo = dlo + sl.beta @ (a * pos - c * ~pos)
+            dhi = dhi + sl.beta @ (a * ~pos - c * pos)
+    return dict(value=val, dW=dW, db=db, dlo0=dlo, dhi0=dhi, x=x, z=z)
+
+
+def filter_gradient(dWdense: np.ndarray, taps, filt_shape) -> np.ndarray:
+    """Sum a dense-operator gradient back onto the conv filter entries it was built from."""
+    out = np.zeros(int(np.prod(filt_shape)))
+    for row, col, fi in taps:
+        out[fi] += dWdense[row, col]
+    return out.reshape(filt_shape)
+
+
+def bias_gradient(db_dense: np.ndarray, L: dict) -> np.ndarray:
+    """Sum a per-neuron bias gradient of a conv layer over the channel's positions."""
+    if L["kind"] == "linear":
+        return db_dense
+    oc, oh, ow = L["out_shape"]
+    return db_dense.reshape(oc, oh * ow).sum(axis=1)
