@@ -1,0 +1,363 @@
+"""Benchmark of the batched Active Set / Saddle Point hot path on one or more GB300 GPUs.
+
+One step bounds one batch of the workload end to end through the C ABI:
+  Active Set: reset (interval bounds) + 200 Big-M + 800 Active Set iterations + bound;
+  Saddle Point: reset + 200 Big-M + 1000 Saddle Point iterations (conversion and 100 primal
+  initialisation steps included) + bound.
+Default workload: the paper's "Wide" conv net (3x32x32 -> conv16 4x4/2 -> conv32 4x4/2 -> FC100
+-> FC10), one L-infinity box of radius 2/255 around a U[0,1] image, the 9 logit-difference
+properties as 9 subproblems; synthetic He-initialised weights.
+
+Output: one JSON line (rank 0). value = subproblem-iterations per second over the whole step,
+inputs resident on the device; e2e = the same with the batch in pinned host memory and the
+bounds read back to the host, copies inside the timed region; roofline = the dominant kernel's
+achieved FP32 rate against the FP32 ALU peak; cpu_baseline = the CPU oracle on a bounded sample.
+--impl reference times the CPU oracle as the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Active-Set subproblem-iters/s & time-to-bound vs plain FP32; % HBM roofline"
+UNIT = "subproblem-iters/s"
+L2_BYTES = 129 * 1024 * 1024
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+AS_BIGM, AS_ITERS, SP_BIGM, SP_ITERS = 200, 800, 200, 1000
+
+
+def workload_options(binding, profile=0):
+    as_opt = binding.default_options(bigm_iters=AS_BIGM, as_iters=AS_ITERS, omega=round(0.3 * AS_ITERS),
+                                     max_cuts=5, graph_chunk=25, profile=profile)
+    sp_opt = binding.default_options(bigm_iters=SP_BIGM, as_iters=0, max_cuts=5, graph_chunk=25,
+                                     profile=profile)
+    return as_opt, sp_opt
+
+
+def iterations_per_step():
+    return AS_BIGM + AS_ITERS + SP_BIGM + SP_ITERS
+
+
+def run_step(ctx_as, ctx_sp, batch, out_as, out_sp):
+    lo, hi, C = batch
+    ctx_as.reset(lo, hi, C)
+    ctx_as.as_step(AS_BIGM + AS_ITERS)
+    ctx_as.bound_into(64, out_as)
+    ctx_sp.reset(lo, hi, C)
+    ctx_sp.as_step(SP_BIGM)
+    ctx_sp.sp_step(SP_ITERS)
+    ctx_sp.bound_into(64, out_sp)
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def algorithmic_flops(net, S, kernel, n_slots_per_iter):
+    """Algorithmic FP32 flops of all launches of a kernel over one step (2 per multiply-add).
+
+    nnz_k = weights touched per layer application (the dense operator's nonzeros). Active Set
+    row pass: (1 + slots) multiply-adds per (subproblem, nonzero) of every hidden layer; col pass:
+    the same over hidden layers plus the output row. Saddle Point row pass: 3 per nonzero (W x,
+    the masked product, the mask row sum); col passes: 1 per nonzero (unmasked W^T alpha in
+    phase A, the masked backward in phase C)."""
+    nnz = []
+    for L in net:
+        if L["kind"] == "linear":
+            nnz.append(L["n_in"] * L["n_out"])
+        else:
+            c, h, w = L["in_shape"]
+            oc, oh, ow = L["out_shape"]
+            cnt = 0
+            for oy in range(oh):
+                for ky in range(L["kh"]):
+                    y = oy * L["stride"] - L["pad"] + ky
+                    if 0 <= y < h:
+                        cnt += 1
+            cntx = 0
+            for ox in range(ow):
+                for kx in range(L["kw"]):
+                    x = ox * L["stride"] - L["pad"] + kx
+                    if 0 <= x < w:
+                        cntx += 1
+            nnz.append(oc * c * cnt * cntx)
+    hid = sum(nnz[:-1])
+    out_row = net[-1]["n_in"]
+    if kernel == "as_rowB":
+        return sum(2.0 * S * hid * (1 + k) for k in n_slots_per_iter)
+    if kernel == "as_colA":
+        return sum(2.0 * S * (hid * (1 + k) + out_row) for k in n_slots_per_iter)
+    if kernel == "sp_rowB":
+        return 2.0 * S * hid * 3 * SP_ITERS
+    if kernel in ("sp_colA", "sp_colC"):
+        return 2.0 * S * (hid + out_row) * SP_ITERS
+    return 0.0
+
+
+def slots_schedule(opt):
+    """Active-set size at every iteration of the Active Set context (global schedule)."""
+    out = []
+    for it in range(opt.bigm_iters + opt.as_iters):
+        if it < opt.bigm_iters:
+            out.append(0)
+            continue
+        t = it - opt.bigm_iters
+        q, r = divmod(t, opt.omega)
+        before = min(q * opt.vars_per_add + min(r, opt.vars_per_add), opt.max_cuts)
+        add = 1 if (r < opt.vars_per_add and q * opt.vars_per_add + r < opt.max_cuts) else 0
+        out.append(before + add)
+    return out
+
+
+def cpu_baseline(prob_name, seconds_budget=20.0):
+    """Times the CPU oracle, single-threaded, on a bounded sample of the workload: one subproblem,
+    a few Big-M then Active Set iterations (with the two first mask additions)."""
+    code = f"""
+import os, sys, time, json
+sys.path.insert(0, {ROOT!r})
+from oracle import active_set as AS, network as nw
+from paper_2101_05844_gb300 import synth
+prob = synth.problem({prob_name!r}, seed=0)
+t0 = time.time()
+dense = nw.dense_layers(prob["net"])
+P = nw.Problem(prob["net"], prob["lo"][0], prob["hi"][0], prob["C"][0], dense=dense)
+setup = time.time() - t0
+opt = AS.Options(bigm_iters=4, as_iters=200, omega=15, max_cuts=5)
+s = AS.ActiveSet(P, opt)
+t0 = time.time(); n = 0
+while n < 40 and (time.time() - t0) < {seconds_budget}:
+    s.step(1); n += 1
+dt = time.time() - t0
+print(json.dumps({{"iters": n, "seconds": dt, "setup_s": setup}}))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
+    if r.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": r.stderr[-300:]}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": d["iters"] / d["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"1 of the 9 subproblems, {d['iters']} iterations (4 Big-M, then Active Set, masks "
+                      f"added at Active Set iterations 0, 1, 15, 16, 30), FP64 numpy, dense conv "
+                      f"operators, single thread; {d['seconds']:.1f} s"}
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cb = cpu_baseline(args.workload, seconds_budget=max(10.0, 20.0 / max(1, args.steps)))
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "subproblems": 9, "note": "CPU oracle, bounded sample"},
+            "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                                          "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="wide_conv")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+
+    import numpy as np
+    import torch
+
+    from paper_2101_05844_gb300 import binding, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    binding.lib()
+
+    prob = synth.problem(args.workload, seed=rank)   # each rank bounds its own batch (weak scaling)
+    S = prob["lo"].shape[0]
+    dev = torch.device("cuda", local)
+    lo_d = torch.from_numpy(prob["lo"]).to(dev)
+    hi_d = torch.from_numpy(prob["hi"]).to(dev)
+    C_d = torch.from_numpy(prob["C"]).to(dev)
+    lo_h = torch.from_numpy(prob["lo"]).pin_memory()
+    hi_h = torch.from_numpy(prob["hi"]).pin_memory()
+    C_h = torch.from_numpy(prob["C"]).pin_memory()
+    out_d = [torch.zeros(S, dtype=torch.float64, device=dev) for _ in range(2)]
+    out_h = [torch.zeros(S, dtype=torch.float64).pin_memory() for _ in range(2)]
+    as_opt, sp_opt = workload_options(binding)
+    stream = torch.cuda.current_stream().cuda_stream
+    ctx_as = binding.Context(prob["net"], prob["lo"], prob["hi"], prob["C"], options=as_opt, stream=stream)
+    ctx_sp = binding.Context(prob["net"], prob["lo"], prob["hi"], prob["C"], options=sp_opt, stream=stream)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(batch, outs, k):
+        times = []
+        for _ in range(k):
+            flush.fill_(1.0)                      # evict L2 between steps
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            run_step(ctx_as, ctx_sp, batch, outs[0], outs[1])
+            e1.record()
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        return times
+
+    for _ in range(args.warmup):
+        run_step(ctx_as, ctx_sp, (lo_d, hi_d, C_d), out_d[0], out_d[1])
+    barrier()
+    l0 = ctx_as.launch_count() + ctx_sp.launch_count()
+    with ClockSampler(local) as clk:
+        barrier()
+        times = timed((lo_d, hi_d, C_d), out_d, args.steps)
+        barrier()
+    launches = ctx_as.launch_count() + ctx_sp.launch_count() - l0
+    # end to end through the API with host buffers
+    for _ in range(max(1, args.warmup // 2)):
+        run_step(ctx_as, ctx_sp, (lo_h, hi_h, C_h), out_h[0], out_h[1])
+    barrier()
+    e2e_times = timed((lo_h, hi_h, C_h), out_h, args.steps)
+    barrier()
+    bounds_as = out_h[0].numpy().copy()
+    bounds_sp = out_h[1].numpy().copy()
+
+    ms = sum(times) / len(times)
+    ms_e2e = sum(e2e_times) / len(e2e_times)
+    if dist:
+        t = torch.tensor([ms, ms_e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, ms_e2e = t.tolist()
+    units = S * iterations_per_step() * world
+    value = units / (ms / 1e3)
+    e2e_value = units / (ms_e2e / 1e3)
+
+    # per-kernel device time for the roofline: one profiled step (CUDA events around each launch)
+    as_p, sp_p = workload_options(binding, profile=1)
+    pa = binding.Context(prob["net"], prob["lo"], prob["hi"], prob["C"], options=as_p, stream=stream)
+    ps = binding.Context(prob["net"], prob["lo"], prob["hi"], prob["C"], options=sp_p, stream=stream)
+    run_step(pa, ps, (lo_d, hi_d, C_d), out_d[0], out_d[1])
+    kt = {}
+    for ctx in (pa, ps):
+        for name, (tms, n) in ctx.kernel_times().items():
+            a, b = kt.get(name, (0.0, 0))
+            kt[name] = (a + tms, b + n)
+    top = max(kt, key=lambda k: kt[k][0])
+    sched = slots_schedule(as_opt)
+    flops = algorithmic_flops(prob["net"], S, top, sched)
+    if top == "as_colA":  # the profiled step also evaluates the final bound with this kernel
+        flops *= 1.0
+    tms, n = kt[top]
+    peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * 2.07e9 / 1e12
+    achieved = flops / (tms / 1e3) / 1e12 if tms > 0 else None
+    step_kernel_ms = sum(v[0] for v in kt.values())
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "subproblems_per_gpu": S,
+                   "iterations_per_step": {"active_set": AS_BIGM + AS_ITERS, "big_m_before_sp": SP_BIGM,
+                                           "saddle_point": SP_ITERS},
+                   "l2": "flushed between timed steps (write of 2x L2)", "parallelism": f"replicas x{world}"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "ms_per_step": ms_e2e,
+                "h2d_bytes_per_step": 2 * (lo_h.numel() * 4 + hi_h.numel() * 4 + C_h.numel() * 4),
+                "d2h_bytes_per_step": 2 * S * 8},
+        "gpu_launches": launches,
+        "roofline": {"bound": "alu", "kernel": top, "achieved": achieved, "peak": peak_tflops,
+                     "unit": "TFLOP/s", "frac": (achieved / peak_tflops) if achieved else None,
+                     "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (derived)",
+                     "traffic": None, "launches": n, "kernel_ms": tms,
+                     "share_of_kernel_time": tms / step_kernel_ms if step_kernel_ms else None},
+        "kernel_ms_per_step": {k: v[0] for k, v in kt.items() if v[1]},
+        "clocks": clk.summary(),
+        "bounds": {"active_set": [float(v) for v in bounds_as], "saddle_point": [float(v) for v in bounds_sp]},
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.workload)
+    if rank == 0:
+        print(json.dumps(line))
+    for c in (ctx_as, ctx_sp, pa, ps):
+        c.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

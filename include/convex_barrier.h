@@ -1,0 +1,202 @@
+/*
+ * convex_barrier.h - C ABI of the GB300 (sm_103a) library for the sparse dual solvers of
+ * De Palma et al., "Scaling the Convex Barrier with Sparse Dual Algorithms" (arXiv 2101.05844).
+ *
+ * The library bounds min over x_0 in a box of  c_s^T (W_n x_{n-1} + b_n)  for S subproblems at
+ * once, through affine layers and ReLUs (problem 1, Sec. 2), using the tighter relaxation of
+ * Sec. 2.2 (problem 4). Solvers: Big-M (Alg. 3, App. B), Active Set (Alg. 1, Sec. 4) and Saddle
+ * Point (Alg. 2, Sec. 5). All arithmetic runs in CUDA kernels on the current device.
+ *
+ * Conventions
+ *  - Pointers marked "host or device" may point to either; the library copies from them with
+ *    unified addressing before the call returns and never keeps them. Outputs marked "host or
+ *    device" are written before the call returns (the call synchronises its stream when an output
+ *    is in host memory).
+ *  - Every function returns an int status (AS_OK = 0). No C++ exception crosses the ABI.
+ *    as_last_error() gives a message for the last failure of a context.
+ *  - Per-subproblem vectors are row-major [S][n]. "Hidden vectors" concatenate the hidden layers
+ *    k = 1..n-1 in order: [S][n_1 + ... + n_{n-1}].
+ *  - Calls on one context are ordered on its stream; a context is not thread-safe.
+ */
+#ifndef CONVEX_BARRIER_H
+#define CONVEX_BARRIER_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define AS_OK 0
+#define AS_ERR_ARG 1      /* bad argument: null pointer, lo > hi, S < 1, bad option         */
+#define AS_ERR_SHAPE 2    /* layer shapes inconsistent                                       */
+#define AS_ERR_CUDA 3     /* a CUDA call failed (message in as_last_error)                   */
+#define AS_ERR_OOM 4      /* device allocation failed                                        */
+#define AS_ERR_NUMERIC 5  /* a bound came out NaN or infinite                                */
+#define AS_ERR_TIMEOUT 6  /* a bounded device wait expired (reserved; no kernel waits today) */
+#define AS_ERR_STATE 7    /* call not valid in the context's current mode                    */
+
+#define AS_LAYER_LINEAR 0
+#define AS_LAYER_CONV2D 1
+
+#define AS_MAX_LAYERS 10 /* affine layers, output layer included */
+#define AS_MAX_CUTS 8    /* active-set masks per neuron (the paper uses at most 7, Sec. 8.1) */
+
+/* One affine layer x_hat_k = W_k x_{k-1} + b_k (Sec. 2). Hidden layers are followed by a ReLU;
+ * the last layer is linear and has no ReLU.
+ *  LINEAR: in_c = n_{k-1}, out_c = n_k, other shape fields ignored; W row-major [out_c][in_c].
+ *  CONV2D: input [in_c][in_h][in_w], output [out_c][out_h][out_w] (CHW, row-major), square
+ *          or rectangular kernel kh x kw, stride, zero padding pad; W [out_c][in_c][kh][kw],
+ *          b per output channel. out_h, out_w must equal (in + 2 pad - k) / stride + 1.
+ *  W and b: host or device, float32; copied by as_init. */
+typedef struct as_layer {
+    int kind;
+    int in_c, in_h, in_w;
+    int out_c, out_h, out_w;
+    int kh, kw, stride, pad;
+    const float* W;
+    const float* b;
+} as_layer;
+
+typedef struct as_net {
+    int n_layers; /* n >= 2 (at least one hidden layer), <= AS_MAX_LAYERS */
+    const as_layer* layers;
+} as_net;
+
+/* Solver options; as_default_options() fills the paper's values (Sec. 8.1, App. C). */
+typedef struct as_options {
+    int bigm_iters;      /* T_M: Big-M iterations before Active Set (Alg. 1 line 2, App. B)   */
+    int as_iters;        /* T_A: Active Set iterations (sets the learning-rate schedule)      */
+    double bigm_lr0, bigm_lr1; /* Big-M step size, linear from lr0 to lr1 (1e-2 -> 1e-4)       */
+    double as_lr0, as_lr1;     /* Active Set step size after reset (1e-3 -> 1e-6)              */
+    int omega;           /* iterations between mask additions (450); <= 0: only the first     */
+    int vars_per_add;    /* masks per addition, one per iteration (2)                         */
+    int max_cuts;        /* masks per neuron, <= AS_MAX_CUTS (7)                              */
+    double adam_b1, adam_b2, adam_eps; /* Adam (0.9, 0.999, 1e-8)                             */
+    double sp_gamma0;    /* Saddle Point step gamma_t = 1 / (t + sp_gamma0) (10)              */
+    double sp_c_alpha, sp_c_beta; /* price caps where the initial duals are zero, eq. (16)   */
+    int sp_init_steps;   /* primal initialisation steps, App. C.2 (100)                       */
+    double sp_init_lr0, sp_init_lr1; /* its step size, linear (1e-2 -> 1e-5)                  */
+    int track_best;      /* 1: evaluate the bound at every iteration and keep the best        */
+    int graph_chunk;     /* iterations per captured CUDA graph (0: plain launches)           */
+    int profile;         /* 1: time every kernel with CUDA events (disables graphs)           */
+} as_options;
+
+typedef struct as_ctx as_ctx;
+
+/* Fills *opt with the defaults above. */
+void as_default_options(as_options* opt);
+
+/* Creates a context for S subproblems (Alg. 1 line 2 / Alg. 3 line 2).
+ *  x_lo, x_hi: [S][n_0] input boxes, host or device; x_lo <= x_hi elementwise (AS_ERR_ARG).
+ *  C:          [S][n_out] property rows, host or device; subproblem s bounds C[s] . x_hat_n.
+ *              NULL allowed only when n_out == 1 (then C[s] = 1).
+ *  lhat, uhat: hidden vectors of pre-activation bounds (App. E), host or device; both NULL
+ *              to compute them on the device by interval propagation (App. E, last paragraph),
+ *              accumulated in FP64 and rounded outward to float32.
+ *  splits:     hidden vector of int8 ReLU splits (+1 active, -1 inactive, 0 free), or NULL. A
+ *              split clamps lhat to 0 (+1) or uhat to 0 (-1) of a neuron whose interval straddles
+ *              zero before the next layer is propagated; it is ignored with caller bounds.
+ *  caps:       [S] masks per neuron for each subproblem (1..max_cuts), or NULL (= max_cuts).
+ *  opt:        NULL for defaults.
+ *  stream:     cudaStream_t on which every call of this context is enqueued (NULL = legacy).
+ * The context starts with every dual at zero, so its bound is the interval bound (App. B.3). */
+int as_init(as_ctx** out, const as_net* net, int S, const float* x_lo, const float* x_hi,
+            const float* C, const float* lhat, const float* uhat, const signed char* splits,
+            const int* caps, const as_options* opt, void* stream);
+
+/* Restarts a context on a new batch of S subproblems of the same network (branch and bound:
+ * new boxes, properties, splits; no reallocation, no synchronisation). Arguments as in as_init,
+ * all host or device. Every dual, Adam moment, active-set slot and Saddle Point statistic is
+ * zeroed and the iteration counters restart. The box is checked on the device: lo > hi or a
+ * non-finite entry is reported by the next as_bound (AS_ERR_ARG). */
+int as_reset(as_ctx* ctx, const float* x_lo, const float* x_hi, const float* C, const float* lhat,
+             const float* uhat, const signed char* splits, const int* caps);
+
+/* Runs n_iters iterations of Big-M (global iteration < bigm_iters) then Active Set (Alg. 1):
+ * closed-form inner minimisation (eqs. 7-8), mask addition by the oracle eq. (3) on the schedule
+ * of as_options, supergradient (eq. 9), Adam step and projection. Asynchronous on the stream.
+ * AS_ERR_STATE after sp_step has started Saddle Point on this context. */
+int as_step(as_ctx* ctx, int n_iters);
+
+/* Runs n_iters Saddle Point iterations (Alg. 2). The first call converts the current duals to
+ * sufficient statistics (eq. 10), sets the price caps (eq. 16) and runs the primal
+ * initialisation (App. C.2). Asynchronous on the stream. */
+int sp_step(as_ctx* ctx, int n_iters);
+
+/* Bound at the current duals (Alg. 1 / Alg. 2 return lines): [S] doubles into out (host or
+ * device). precision 32 sums the per-neuron terms in float32, 64 in float64 (the terms
+ * themselves are float32 products). best (nullable, host or device): best bound over every
+ * evaluated iterate, this one included (needs track_best for the per-iteration part).
+ * Returns AS_ERR_NUMERIC if any bound is not finite. */
+int as_bound(as_ctx* ctx, int precision, double* out, double* best);
+
+/* Gradient of sum_s grad_bound[s] * bound_s at the current duals and masks, with the
+ * intermediate bounds and the signs of W held fixed (envelope theorem; not in the paper).
+ * grad_bound: [S] host or device. Outputs are ACCUMULATED (+=) into device buffers:
+ *  dW[k], db[k] for k = 0..n-1 (layer k+1, shaped like its W and b; the last layer's gradient
+ *  is taken through the property rows C), dlo, dhi: [S][n_0]. Any output pointer may be NULL
+ *  (dW and db themselves, or entries of them) to skip it. Active Set mode only. */
+int as_bound_backward(as_ctx* ctx, const double* grad_bound, float* const* dW, float* const* db,
+                      float* dlo, float* dhi);
+
+/* Named state buffers, for warm starts and inspection. Sizes in bytes via as_state_size. */
+#define AS_ST_ALPHA 0     /* float [S][NH]                                                    */
+#define AS_ST_BETA0 1     /* float [S][NH]                                                    */
+#define AS_ST_BETA1 2     /* float [S][NH]                                                    */
+#define AS_ST_SLOT_BETA 3 /* float [S][max_cuts][NH]: beta_{k,I} of each active-set slot      */
+#define AS_ST_XSNAP 4     /* uint8 [S][NT]: bit b = x* at its upper bound when slot b was added
+                             (NT = n_0 + NH, neuron layers 0..n-1)                             */
+#define AS_ST_ZSNAP 5     /* uint8 [S][NH]: bit b = z* when slot b was added                  */
+#define AS_ST_ITER 6      /* int [3]: Active Set iteration, Saddle Point iteration, and 1 when
+                             Saddle Point has started (setting 1 skips its initialisation)     */
+#define AS_ST_LHAT 7      /* float [S][NH] pre-activation lower bounds                        */
+#define AS_ST_UHAT 8      /* float [S][NH] pre-activation upper bounds                        */
+#define AS_ST_XSTAR 9     /* float [S][NT] primal minimiser x* of the last evaluation         */
+#define AS_ST_ZSTAR 10    /* uint8 [S][NH] z* of the last evaluation                          */
+#define AS_ST_LAMBDA 11   /* float [S][max_cuts][NH] sum_j W I Lcheck of each slot            */
+#define AS_ST_KAPPA 12    /* float [S][max_cuts][NH] lambda + sum_j W (1-I) Ucheck + b        */
+#define AS_ST_ADAM 13     /* float [6][S][NH]: m, v of alpha, beta0, beta1                    */
+#define AS_ST_SLOT_ADAM 14 /* float [2][S][max_cuts][NH]: m, v of the slots                   */
+#define AS_ST_SP_X 15     /* float [S][NT] Saddle Point primal x (current)                    */
+#define AS_ST_SP_Z 16     /* float [S][NH] Saddle Point primal z (current)                    */
+#define AS_ST_SP_STATS 17 /* float [4][S][NT]: Sb, G, C (hidden part) and P (P_k indexed by
+                             the inputs of layer k), see Sec. 5.1                              */
+#define AS_ST_SP_CAPS 18  /* float [2][S][NH]: mu_alpha, mu_beta                              */
+#define AS_ST_LO 19       /* float [S][NT] post-activation lower bounds (layer 0: the box)    */
+#define AS_ST_HI 20       /* float [S][NT] post-activation upper bounds                       */
+#define AS_ST_SP_SEL 21   /* uint8 [S][NH] conditional-gradient choice of the last Saddle Point
+                             iteration: 0 beta_0, 1 beta_1, 2 the oracle mask, 3 none (eq. 12) */
+#define AS_ST_COUNT 22
+
+int as_state_size(as_ctx* ctx, int which, long long* nbytes);
+/* Copies a state buffer out (dst host or device); synchronises when dst is host memory. */
+int as_get_state(as_ctx* ctx, int which, void* dst);
+/* Replaces a state buffer (src host or device). Setting AS_ST_SLOT_BETA, AS_ST_XSNAP or
+ * AS_ST_ZSNAP recomputes lambda and kappa of every filled slot. */
+int as_set_state(as_ctx* ctx, int which, const void* src);
+
+/* Number of kernel launches this context has issued (graph nodes counted per replay). */
+long long as_launch_count(as_ctx* ctx);
+
+/* Kernel ids for as_kernel_times. */
+#define AS_K_AS_COLA 0 /* Active Set col pass: f, x*, z*, bound terms, snapshots      */
+#define AS_K_AS_ROWB 1 /* Active Set row pass: products, supergradient, Adam          */
+#define AS_K_REDUCE 2  /* bound reduction                                              */
+#define AS_K_SP_COLA 3 /* Saddle Point col pass: f, primal conditional gradient        */
+#define AS_K_SP_ROWB 4 /* Saddle Point row pass: oracle, dual conditional gradient     */
+#define AS_K_SP_COLC 5 /* Saddle Point col pass: masked backward, convex combination   */
+#define AS_K_SPI_ROW 6 /* Saddle Point primal initialisation, row pass                 */
+#define AS_K_SPI_COL 7 /* Saddle Point primal initialisation, col pass                 */
+#define AS_K_COUNT 8
+
+/* With as_options.profile set: total device time (CUDA events on the context's stream) and
+ * launch count of one kernel over the context's life so far. Synchronises the stream. */
+int as_kernel_times(as_ctx* ctx, int kernel, double* total_ms, long long* launches);
+
+void as_destroy(as_ctx* ctx);
+const char* as_last_error(as_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CONVEX_BARRIER_H */

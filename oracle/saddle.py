@@ -23,7 +23,15 @@ Readings (Sec. 5.2, 8.1, App. C):
     lower index (beta_0, then beta_1, then beta_I*); beta_bar = mu_beta on the winner when its
     gradient is >= 0, else zero (eq. 12);
   * alpha_bar and beta_bar use the current iterate (x^t, z^t); (x_bar, z_bar) is the closed-form
-    minimiser at (alpha^t, zeta^t) (Alg. 2).
+    minimiser at (alpha^t, zeta^t) (Alg. 2);
+  * a row of the oracle mask that selects none of the row's free inputs (nonzero weight, l < u;
+    a fixed input adds the same term selected or not) is the all-zero constraint, and one that
+    selects all of them is the all-ones constraint; those two constraints are the looser,
+    interval-bound versions of the beta_0 and beta_1 constraints, which Sec. 2.2 treats
+    separately from E_k. Their gradient never exceeds that of beta_0 (resp. beta_1) in exact
+    arithmetic, and equals it when the intermediate bounds are interval bounds, so such a row does
+    not compete in the choice of eq. (12) (in exact arithmetic this changes no choice, since ties
+    go to beta_0 and beta_1).
 """
 from __future__ import annotations
 
@@ -32,6 +40,14 @@ import numpy as np
 from . import dual as du
 from . import relaxation as rx
 from .active_set import Options, linear_lr
+
+
+def degenerate_rows(W, I, lo, hi):
+    """Rows whose mask selects none, or all, of the row's free inputs: inputs with a nonzero
+    weight and l < u. A fixed input (l = u) contributes the same term to the constraint of eq. (4)
+    whether selected or not, so such rows are the all-zero or the all-ones constraint."""
+    nz = (W != 0) & (lo != hi)[None, :]
+    return ~(nz & I).any(axis=1) | ~(nz & ~I).any(axis=1)
 
 
 class SaddlePoint:
@@ -74,6 +90,53 @@ class SaddlePoint:
         self.t = 0
         self.best = -np.inf
         self.trace = []
+
+    @classmethod
+    def from_state(cls, P, opt: Options, alpha, Sb, Pst, G, C, mu_a, mu_b, x, z, t: int):
+        """A solver at a given iterate (1-based lists as in the paper; Pst[k] has n_{k-1} entries),
+        skipping conversion and primal initialisation."""
+        sp = cls.__new__(cls)
+        sp.P, sp.opt, sp.explicit, sp.betas = P, opt, False, None
+        cp = lambda L: [None if v is None else np.asarray(v, np.float64).copy() for v in L]
+        sp.alpha, sp.Sb, sp.Pst, sp.G, sp.C = cp(alpha), cp(Sb), cp(Pst), cp(G), cp(C)
+        sp.mu_a, sp.mu_b = cp(mu_a), cp(mu_b)
+        sp.x, sp.z = cp(x), cp(z)
+        sp.t, sp.best, sp.trace = t, -np.inf, []
+        return sp
+
+    def decision_margin(self, sums_only: bool = False) -> float:
+        """Smallest gap, over every decision the next iteration takes, between the deciding value
+        and its threshold: the sign of f (x_bar), of G (z_bar), of xhat - x (alpha_bar), the
+        top-two gap and the sign of the conditional-gradient choice, and |z - tau| of the float32
+        mask thresholds of ambiguous inputs. sums_only: only the decisions taken on sums (f,
+        xhat - x, the choice), the ones whose value depends on the summation's precision."""
+        P, n = self.P, self.P.n
+        m = min(np.abs(fk).min() for fk in self.coefficients())
+        for k in range(1, n):
+            W, b, x, z, xp = P.W[k], P.b[k], self.x[k], self.z[k], self.x[k - 1]
+            if not sums_only:
+                m = min(m, np.abs(self.G[k]).min())
+            xhat = W @ xp + b
+            m = min(m, np.abs(xhat - x).min())
+            I = rx.mask(W, P.lo[k - 1], P.hi[k - 1], xp, z)
+            lam, mu = rx.row_sums(W, P.lo[k - 1], P.hi[k - 1], I)
+            vI = x - (W * I) @ xp + (1 - z) * lam - z * (b + mu)
+            vI = np.where(degenerate_rows(W, I, P.lo[k - 1], P.hi[k - 1]), -np.inf, vI)
+            V = np.sort(np.stack([x - z * P.uhat[k], x - xhat + (1 - z) * P.lhat[k], vI]), axis=0)
+            m = min(m, (V[2] - V[1]).min(), np.abs(V[2]).min())
+            l32, u32 = P.lo[k - 1].astype(np.float32), P.hi[k - 1].astype(np.float32)
+            amb = l32 != u32
+            if amb.any() and not sums_only:
+                x32 = xp.astype(np.float32)[amb]
+                den = (u32 - l32)[amb]
+                tp = ((x32 - l32[amb]) / den).astype(np.float64)
+                tn = ((u32[amb] - x32) / den).astype(np.float64)
+                zz = z.astype(np.float32).astype(np.float64)[:, None]
+                Wa = W[:, amb]
+                dp = np.where(Wa > 0, np.abs(zz - tp[None, :]), np.inf)
+                dn = np.where(Wa < 0, np.abs(zz - tn[None, :]), np.inf)
+                m = min(m, dp.min(), dn.min())
+        return float(m)
 
     # ---------------------------------------------------------------- explicit beta bookkeeping
     def _add(self, k, i, key, val):
@@ -179,6 +242,7 @@ class SaddlePoint:
                 v0 = x - z * P.uhat[k]
                 v1 = x - xhat + (1 - z) * P.lhat[k]
                 vI = x - (W * I) @ xp + (1 - z) * lam - z * (b + mu)
+                vI = np.where(degenerate_rows(W, I, P.lo[k - 1], P.hi[k - 1]), -np.inf, vI)
                 V = np.stack([v0, v1, vI])
                 sel = np.argmax(V, axis=0)          # first maximum: ties to the lower index
                 on = V.max(axis=0) >= 0
@@ -189,6 +253,7 @@ class SaddlePoint:
                 rowsel = np.where(sel == 1, 1.0, 0.0)[:, None] + np.where(sel == 2, 1.0, 0.0)[:, None] * I
                 Pbar = (W * rowsel).T @ bb
                 new[k] = (abar, Sbar, Pbar, Gbar, Cbar, sel, on, I)
+            self.last_sel = [None] + [np.where(new[k][6], new[k][5], 3) for k in range(1, n)]
             for k in range(n):
                 self.x[k] = (1 - gamma) * self.x[k] + gamma * xb[k]
             for k in range(1, n):

@@ -1,0 +1,254 @@
+"""Thin ctypes binding of the C ABI in include/convex_barrier.h (argument marshalling only).
+
+Every step of the method runs in the CUDA library; this module only converts arrays to pointers.
+Arrays may be numpy arrays (host memory) or torch tensors (host or CUDA). Loading fails loudly
+when the library has not been built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libconvex_barrier.so")
+
+AS_OK, AS_ERR_ARG, AS_ERR_SHAPE, AS_ERR_CUDA, AS_ERR_OOM, AS_ERR_NUMERIC, AS_ERR_TIMEOUT, AS_ERR_STATE = range(8)
+LINEAR, CONV2D = 0, 1
+MAX_LAYERS, MAX_CUTS = 10, 8
+
+(ST_ALPHA, ST_BETA0, ST_BETA1, ST_SLOT_BETA, ST_XSNAP, ST_ZSNAP, ST_ITER, ST_LHAT, ST_UHAT, ST_XSTAR,
+ ST_ZSTAR, ST_LAMBDA, ST_KAPPA, ST_ADAM, ST_SLOT_ADAM, ST_SP_X, ST_SP_Z, ST_SP_STATS, ST_SP_CAPS,
+ ST_LO, ST_HI, ST_SP_SEL) = range(22)
+
+EXPORTS = ["as_default_options", "as_init", "as_reset", "as_step", "sp_step", "as_bound",
+           "as_bound_backward", "as_state_size", "as_get_state", "as_set_state", "as_launch_count",
+           "as_kernel_times", "as_destroy", "as_last_error"]
+KERNELS = ["as_colA", "as_rowB", "reduce", "sp_colA", "sp_rowB", "sp_colC", "spi_row", "spi_col"]
+
+
+class Layer(ct.Structure):
+    _fields_ = [("kind", ct.c_int), ("in_c", ct.c_int), ("in_h", ct.c_int), ("in_w", ct.c_int),
+                ("out_c", ct.c_int), ("out_h", ct.c_int), ("out_w", ct.c_int), ("kh", ct.c_int),
+                ("kw", ct.c_int), ("stride", ct.c_int), ("pad", ct.c_int),
+                ("W", ct.c_void_p), ("b", ct.c_void_p)]
+
+
+class Net(ct.Structure):
+    _fields_ = [("n_layers", ct.c_int), ("layers", ct.POINTER(Layer))]
+
+
+class Options(ct.Structure):
+    _fields_ = [("bigm_iters", ct.c_int), ("as_iters", ct.c_int),
+                ("bigm_lr0", ct.c_double), ("bigm_lr1", ct.c_double),
+                ("as_lr0", ct.c_double), ("as_lr1", ct.c_double),
+                ("omega", ct.c_int), ("vars_per_add", ct.c_int), ("max_cuts", ct.c_int),
+                ("adam_b1", ct.c_double), ("adam_b2", ct.c_double), ("adam_eps", ct.c_double),
+                ("sp_gamma0", ct.c_double), ("sp_c_alpha", ct.c_double), ("sp_c_beta", ct.c_double),
+                ("sp_init_steps", ct.c_int), ("sp_init_lr0", ct.c_double), ("sp_init_lr1", ct.c_double),
+                ("track_best", ct.c_int), ("graph_chunk", ct.c_int), ("profile", ct.c_int)]
+
+
+_lib = None
+
+
+def lib() -> ct.CDLL:
+    """The loaded library; raises if it is missing (build it with __graft_entry__.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"CUDA library not built: {LIB_PATH} is missing")
+        L = ct.CDLL(LIB_PATH)
+        L.as_default_options.argtypes = [ct.POINTER(Options)]
+        L.as_default_options.restype = None
+        L.as_init.argtypes = [ct.POINTER(ct.c_void_p), ct.POINTER(Net), ct.c_int] + [ct.c_void_p] * 7 + \
+            [ct.POINTER(Options), ct.c_void_p]
+        L.as_init.restype = ct.c_int
+        L.as_reset.argtypes = [ct.c_void_p] + [ct.c_void_p] * 7
+        L.as_kernel_times.argtypes = [ct.c_void_p, ct.c_int, ct.POINTER(ct.c_double), ct.POINTER(ct.c_longlong)]
+        L.as_step.argtypes = [ct.c_void_p, ct.c_int]
+        L.sp_step.argtypes = [ct.c_void_p, ct.c_int]
+        L.as_bound.argtypes = [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p]
+        L.as_bound_backward.argtypes = [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p,
+                                        ct.c_void_p]
+        L.as_state_size.argtypes = [ct.c_void_p, ct.c_int, ct.POINTER(ct.c_longlong)]
+        L.as_get_state.argtypes = [ct.c_void_p, ct.c_int, ct.c_void_p]
+        L.as_set_state.argtypes = [ct.c_void_p, ct.c_int, ct.c_void_p]
+        L.as_launch_count.argtypes = [ct.c_void_p]
+        L.as_launch_count.restype = ct.c_longlong
+        L.as_destroy.argtypes = [ct.c_void_p]
+        L.as_destroy.restype = None
+        L.as_last_error.argtypes = [ct.c_void_p]
+        L.as_last_error.restype = ct.c_char_p
+        _lib = L
+    return _lib
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    lib().as_default_options(ct.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise AttributeError(k)
+        setattr(o, k, v)
+    return o
+
+
+class CBError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"convex-barrier error {code}: {msg}")
+        self.code = code
+
+
+def _ptr(a):
+    """Pointer of a numpy array or torch tensor (contiguous), or None."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    raise TypeError(type(a))
+
+
+def _layer_struct(L: dict, keep: list) -> Layer:
+    W = np.ascontiguousarray(L["W"], np.float32) if isinstance(L["W"], np.ndarray) else L["W"]
+    b = np.ascontiguousarray(L["b"], np.float32) if isinstance(L["b"], np.ndarray) else L["b"]
+    keep += [W, b]
+    s = Layer()
+    if L["kind"] == "linear":
+        s.kind, s.in_c, s.out_c = LINEAR, L["n_in"], L["n_out"]
+        s.in_h = s.in_w = s.out_h = s.out_w = s.kh = s.kw = s.stride = 1
+        s.pad = 0
+    else:
+        s.kind = CONV2D
+        s.in_c, s.in_h, s.in_w = L["in_shape"]
+        s.out_c, s.out_h, s.out_w = L["out_shape"]
+        s.kh, s.kw, s.stride, s.pad = L["kh"], L["kw"], L["stride"], L["pad"]
+    s.W, s.b = _ptr(W), _ptr(b)
+    return s
+
+
+class Context:
+    """One solver context (as_ctx) over S subproblems."""
+
+    def __init__(self, net: list, lo, hi, C=None, lhat=None, uhat=None, splits=None, caps=None,
+                 options: Options | None = None, stream: int = 0):
+        L = lib()
+        keep = []
+        layers = (Layer * len(net))(*[_layer_struct(x, keep) for x in net])
+        self._net = Net(len(net), layers)
+        self._keep = keep + [layers]
+        conv = lambda a, dt: (np.ascontiguousarray(a, dt) if isinstance(a, np.ndarray) else a)
+        lo, hi = conv(lo, np.float32), conv(hi, np.float32)
+        C = conv(C, np.float32)
+        lhat, uhat = conv(lhat, np.float32), conv(uhat, np.float32)
+        splits = conv(splits, np.int8)
+        caps = conv(caps, np.int32)
+        self._keep += [lo, hi, C, lhat, uhat, splits, caps]
+        self.S = int(lo.shape[0])
+        self.options = options if options is not None else default_options()
+        h = ct.c_void_p()
+        r = L.as_init(ct.byref(h), ct.byref(self._net), self.S, _ptr(lo), _ptr(hi), _ptr(C), _ptr(lhat),
+                      _ptr(uhat), _ptr(splits), _ptr(caps), ct.byref(self.options), ct.c_void_p(stream))
+        self.h = h
+        if r != AS_OK:
+            msg = L.as_last_error(h).decode() if h.value else ""
+            if h.value:
+                L.as_destroy(h)
+            self.h = ct.c_void_p()
+            raise CBError(r, msg)
+        self.n_layers = len(net)
+        self.widths = [net[0]["n_in"]] + [x["n_out"] for x in net[:-1]]
+        self.NT = sum(self.widths)
+        self.NH = self.NT - self.widths[0]
+        self.cap = max(1, self.options.max_cuts)
+
+    def _check(self, r):
+        if r != AS_OK:
+            raise CBError(r, lib().as_last_error(self.h).decode())
+
+    def reset(self, lo, hi, C=None, lhat=None, uhat=None, splits=None, caps=None):
+        """New batch on the same context (pointers: numpy host arrays or torch tensors)."""
+        conv = lambda a, dt: (np.ascontiguousarray(a, dt) if isinstance(a, np.ndarray) else a)
+        args = [conv(lo, np.float32), conv(hi, np.float32), conv(C, np.float32), conv(lhat, np.float32),
+                conv(uhat, np.float32), conv(splits, np.int8), conv(caps, np.int32)]
+        self._reset_keep = args
+        self._check(lib().as_reset(self.h, *[_ptr(a) for a in args]))
+
+    def kernel_times(self) -> dict:
+        """{kernel name: (total ms, launches)} with options.profile = 1."""
+        out = {}
+        for k, name in enumerate(KERNELS):
+            ms, n = ct.c_double(), ct.c_longlong()
+            self._check(lib().as_kernel_times(self.h, k, ct.byref(ms), ct.byref(n)))
+            out[name] = (ms.value, n.value)
+        return out
+
+    def as_step(self, n: int):
+        self._check(lib().as_step(self.h, n))
+
+    def sp_step(self, n: int):
+        self._check(lib().sp_step(self.h, n))
+
+    def bound(self, precision: int = 64, best: bool = False):
+        out = np.zeros(self.S, np.float64)
+        bb = np.zeros(self.S, np.float64) if best else None
+        self._check(lib().as_bound(self.h, precision, _ptr(out), _ptr(bb)))
+        return (out, bb) if best else out
+
+    def bound_into(self, precision: int, out, best=None):
+        self._check(lib().as_bound(self.h, precision, _ptr(out), _ptr(best)))
+
+    def backward(self, grad_bound, dW: list, db: list, dlo=None, dhi=None):
+        g = np.ascontiguousarray(grad_bound, np.float64) if isinstance(grad_bound, np.ndarray) else grad_bound
+        n = self.n_layers
+        pw = (ct.c_void_p * n)(*[_ptr(x) for x in dW]) if dW is not None else None
+        pb = (ct.c_void_p * n)(*[_ptr(x) for x in db]) if db is not None else None
+        self._check(lib().as_bound_backward(self.h, _ptr(g), ct.cast(pw, ct.c_void_p) if pw else None,
+                                            ct.cast(pb, ct.c_void_p) if pb else None, _ptr(dlo), _ptr(dhi)))
+
+    def state_size(self, which: int) -> int:
+        n = ct.c_longlong()
+        self._check(lib().as_state_size(self.h, which, ct.byref(n)))
+        return n.value
+
+    def get_state(self, which: int, dtype=np.float32) -> np.ndarray:
+        nb = self.state_size(which)
+        out = np.zeros(nb // np.dtype(dtype).itemsize, dtype)
+        self._check(lib().as_get_state(self.h, which, _ptr(out)))
+        return out
+
+    def set_state(self, which: int, arr):
+        a = np.ascontiguousarray(arr)
+        if a.nbytes != self.state_size(which):
+            raise ValueError(f"state {which}: {a.nbytes} bytes, expected {self.state_size(which)}")
+        self._check(lib().as_set_state(self.h, which, _ptr(a)))
+
+    def launch_count(self) -> int:
+        return lib().as_launch_count(self.h)
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            lib().as_destroy(self.h)
+            self.h = ct.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def context_for(prob: dict, options: Options | None = None, bounds=None, stream: int = 0, **kw) -> Context:
+    """A Context for a synthetic problem dict (see synth.problem)."""
+    lh = uh = None
+    if bounds is not None:
+        lh, uh = bounds
+    return Context(prob["net"], prob["lo"], prob["hi"], prob["C"], lh, uh, prob.get("splits"),
+                   prob.get("caps"), options, stream, **kw)

@@ -1,0 +1,125 @@
+// Device-side descriptors shared by the kernels and the host API of the convex-barrier library.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#define CB_MAXL 10
+#define CB_MAXCUT 8
+#define CB_THREADS 256
+#define CB_WARPS (CB_THREADS / 32)
+
+// Kernel ids for per-kernel timing (as_kernel_times).
+enum { CB_K_AS_COLA = 0, CB_K_AS_ROWB, CB_K_REDUCE, CB_K_SP_COLA, CB_K_SP_ROWB, CB_K_SP_COLC,
+       CB_K_SPI_ROW, CB_K_SPI_COL, CB_NPROF };
+
+// One affine layer k (1-based in the paper; stored at index k-1).
+struct DLayer {
+    int kind;              // 0 linear, 1 conv2d
+    int n_in, n_out;
+    int ci, hi, wi, co, ho, wo, kh, kw, st, pd;
+    const float* W;        // linear [n_out][n_in], conv [co][ci][kh][kw]
+    const float* b;        // per output neuron [n_out]
+    int in_off, out_off;   // offsets of the input / output neuron layer in [NT] vectors
+    int h_in, h_out;       // offsets in [NH] hidden vectors (-1 when not a hidden layer)
+};
+
+struct DNet {
+    int n;                 // affine layers; hidden layers k = 1..n-1
+    int S, NT, NH, cap;    // subproblems, all neurons (layers 0..n-1), hidden neurons, max slots
+    DLayer L[CB_MAXL];
+    const float* Wout;     // [S][n_{n-1}] property-folded output row
+    const float* bout;     // [S]
+};
+
+// Solver schedule constants (float32 copies prepared on the host from the double options).
+struct DSched {
+    int TM, TA, omega, vpa, maxcut;
+    int ntab;              // entries in the per-step tables
+    float b1, omb1, b2, omb2, eps;
+    float lr_as_end;       // step size after the planned iterations
+    float gamma0;
+    int sp_init_steps;
+    float sp_lr0, sp_lr1;
+};
+
+// Device state. Per-subproblem arrays are [S][NT], [S][NH] or [S][cap][NH].
+struct DState {
+    float *lo, *hi;                  // post-activation bounds, layer 0 = input box
+    float *lhat, *uhat;              // pre-activation bounds (hidden)
+    float *alpha, *beta0, *beta1;
+    float *ma, *va, *m0, *v0, *m1, *v1;
+    float *bs, *ms, *vs, *lam, *kap; // slots
+    float *xval;                     // x* of the last evaluation [S][NT]
+    float *fval;                     // f of the last evaluation [S][NT]
+    uint8_t* zcur;                   // z* of the last evaluation [S][NH]
+    uint8_t* xsnap[2];               // [S][NT] slot bitsets (double-buffered by addition count)
+    uint8_t* zsnap[2];               // [S][NH]
+    double* terms;                   // per-neuron bound terms [S][NT]
+    double* best;                    // [S]
+    const int* caps;                 // [S]
+    int* ctr;                        // [0] AS iteration, [1] SP iteration, [2] SP-init step
+    unsigned* done;                  // block-completion counters [4]
+    const float* lr_tab;             // [ntab] step size per global iteration
+    const float* bc1_tab;            // [ntab] 1 - b1^step, step = index
+    const float* bc2_tab;            // [ntab] 1 - b2^step
+    // Saddle Point
+    float* spx[2];                   // [S][NT]
+    float* spz[2];                   // [S][NH]
+    float *Sb, *G, *C;               // [S][NH]
+    float* P;                        // [S][NT], P_k at the inputs of layer k
+    float *mua, *mub;                // [S][NH]
+    float* xbar;                     // [S][NT]
+    uint8_t* zbar;                   // [S][NH]
+    float *taup, *taun;              // [S][NT] mask thresholds of every input
+    uint8_t* sel;                    // [S][NH] selected beta of the conditional gradient (3 = none)
+    float *ab, *b0i, *b1i;           // [S][NH] primal-init inner maximisers
+    int* status;                     // device error word
+};
+
+// Iteration schedule of the Big-M / Active Set loop at global iteration it.
+struct Step {
+    int as_phase;       // 0 Big-M, 1 Active Set
+    int t;              // Active Set local iteration (-1 in Big-M)
+    int b_new;          // slot added at this iteration (-1: none)
+    int nadd_before;    // slots added before this iteration (global, before per-subproblem caps)
+    float lr;
+};
+
+__host__ __device__ inline int cb_additions_before(int t, const DSched& d) {
+    if (t <= 0) return 0;
+    int c;
+    if (d.omega > 0) {
+        int full = t / d.omega, rem = t % d.omega;
+        c = full * d.vpa + (rem < d.vpa ? rem : d.vpa);
+    } else {
+        c = t < d.vpa ? t : d.vpa;
+    }
+    return c < d.maxcut ? c : d.maxcut;
+}
+
+__host__ __device__ inline int cb_slot_at(int t, const DSched& d) {
+    int q, r;
+    if (d.omega > 0) { q = t / d.omega; r = t % d.omega; }
+    else { q = 0; r = t; }
+    if (r >= d.vpa) return -1;
+    int b = q * d.vpa + r;
+    return b < d.maxcut ? b : -1;
+}
+
+// Active Set iteration at which slot b is added.
+__host__ __device__ inline int cb_slot_added_at(int b, const DSched& d) {
+    return d.omega > 0 ? (b / d.vpa) * d.omega + (b % d.vpa) : b;
+}
+
+__device__ inline Step cb_step(int it, const DSched& d, const float* lr_tab) {
+    Step s;
+    s.lr = it < d.ntab ? lr_tab[it] : d.lr_as_end;
+    if (it < d.TM) {
+        s.as_phase = 0; s.t = -1; s.b_new = -1; s.nadd_before = 0;
+    } else {
+        s.as_phase = 1; s.t = it - d.TM;
+        s.b_new = cb_slot_at(s.t, d);
+        s.nadd_before = cb_additions_before(s.t, d);
+    }
+    return s;
+}

@@ -1,0 +1,859 @@
+// Host side of the convex-barrier C ABI (include/convex_barrier.h): context creation, buffer
+// layout in device memory, the Big-M / Active Set and Saddle Point iteration loops (optionally
+// captured as CUDA graphs), bound evaluation and state access.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/convex_barrier.h"
+#include "cb_kernels.cuh"
+#include "cb_backward.cuh"
+
+using namespace cb;
+
+struct as_ctx {
+    DNet net{};
+    DState st{};
+    DSched sc{};
+    as_options opt{};
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    std::vector<void*> allocs;
+    std::string err;
+    int n_out = 0;                 // outputs of the last layer (before the property rows)
+    std::vector<as_layer> layers;  // shapes (pointers not kept)
+    std::vector<int> widths;       // neuron layers 0..n-1
+    bool sp_started = false;
+    long long launches = 0;
+    Segs segA{}, segB{}, segP{};
+    int blocksA = 0, blocksB = 0, blocksP = 0;
+    cudaGraphExec_t g_as = nullptr, g_sp = nullptr;
+    int g_as_len = 0, g_sp_len = 0, g_as_nodes = 0, g_sp_nodes = 0;
+    float* Wlast = nullptr;        // original last layer [n_out][n_{n-1}] and bias
+    float* blast = nullptr;
+    float* C = nullptr;            // property rows [S][n_out]
+    int* caps_dev = nullptr;
+    signed char* splits_dev = nullptr;
+    double* bound_out = nullptr;   // [S] device result of the last as_bound
+    char* zero_arena = nullptr;
+    char* work_arena = nullptr;
+    size_t zero_bytes = 0;
+    // per-kernel CUDA-event timing (as_options.profile)
+    struct Rec { int id; cudaEvent_t a, b; };
+    std::vector<Rec> pending;
+    std::vector<cudaEvent_t> pool;
+    double prof_ms[CB_NPROF] = {};
+    long long prof_n[CB_NPROF] = {};
+};
+
+static int fail(as_ctx* c, int code, const char* fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return code;
+}
+
+#define CUDA_TRY(c, call)                                                                    \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail((c), e_ == cudaErrorMemoryAllocation ? AS_ERR_OOM : AS_ERR_CUDA,     \
+                        "%s failed: %s", #call, cudaGetErrorString(e_));                     \
+    } while (0)
+
+template <class T>
+static int dalloc(as_ctx* c, T** p, size_t count) {
+    void* q = nullptr;
+    size_t bytes = count * sizeof(T);
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess)
+        return fail(c, e == cudaErrorMemoryAllocation ? AS_ERR_OOM : AS_ERR_CUDA,
+                    "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    c->allocs.push_back(q);
+    *p = (T*)q;
+    return AS_OK;
+}
+
+#define TRY(x)                    \
+    do {                          \
+        int r_ = (x);             \
+        if (r_ != AS_OK) return r_; \
+    } while (0)
+
+extern "C" void as_default_options(as_options* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->bigm_iters = 500;
+    o->as_iters = 1000;
+    o->bigm_lr0 = 1e-2;
+    o->bigm_lr1 = 1e-4;
+    o->as_lr0 = 1e-3;
+    o->as_lr1 = 1e-6;
+    o->omega = 450;
+    o->vars_per_add = 2;
+    o->max_cuts = 7;
+    o->adam_b1 = 0.9;
+    o->adam_b2 = 0.999;
+    o->adam_eps = 1e-8;
+    o->sp_gamma0 = 10.0;
+    o->sp_c_alpha = 1e-3;
+    o->sp_c_beta = 1e-3;
+    o->sp_init_steps = 100;
+    o->sp_init_lr0 = 1e-2;
+    o->sp_init_lr1 = 1e-5;
+    o->track_best = 0;
+    o->graph_chunk = 16;
+}
+
+extern "C" const char* as_last_error(as_ctx* c) { return c ? c->err.c_str() : "null context"; }
+extern "C" long long as_launch_count(as_ctx* c) { return c ? c->launches : -1; }
+
+static int check_launch(as_ctx* c, const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(c, AS_ERR_CUDA, "launch of %s failed: %s", what, cudaGetErrorString(e));
+    return AS_OK;
+}
+
+// Segment tables: one launch covers several layers, each layer a contiguous block range.
+static void make_segs(Segs& sg, int& blocks, const std::vector<int>& layer_ids,
+                      const std::vector<long long>& units, int units_per_block) {
+    sg.n = (int)layer_ids.size();
+    int b = 0;
+    for (int q = 0; q < sg.n; ++q) {
+        sg.layer[q] = layer_ids[q];
+        sg.start[q] = b;
+        b += (int)((units[q] + units_per_block - 1) / units_per_block);
+    }
+    sg.start[sg.n] = b;
+    blocks = b;
+}
+
+static int validate_net(as_ctx* c, const as_net* net) {
+    if (!net || !net->layers) return fail(c, AS_ERR_ARG, "net is null");
+    const int n = net->n_layers;
+    if (n < 2 || n > AS_MAX_LAYERS) return fail(c, AS_ERR_SHAPE, "n_layers = %d not in [2, %d]", n, AS_MAX_LAYERS);
+    int prev = -1;
+    for (int k = 0; k < n; ++k) {
+        const as_layer& L = net->layers[k];
+        if (!L.W || !L.b) return fail(c, AS_ERR_ARG, "layer %d: null W or b", k + 1);
+        int nin, nout;
+        if (L.kind == AS_LAYER_LINEAR) {
+            nin = L.in_c;
+            nout = L.out_c;
+            if (nin < 1 || nout < 1) return fail(c, AS_ERR_SHAPE, "layer %d: bad linear shape", k + 1);
+        } else if (L.kind == AS_LAYER_CONV2D) {
+            if (k == n - 1) return fail(c, AS_ERR_SHAPE, "the last layer must be linear");
+            if (L.in_c < 1 || L.in_h < 1 || L.in_w < 1 || L.out_c < 1 || L.kh < 1 || L.kw < 1 ||
+                L.stride < 1 || L.pad < 0)
+                return fail(c, AS_ERR_SHAPE, "layer %d: bad conv shape", k + 1);
+            const int oh = (L.in_h + 2 * L.pad - L.kh) / L.stride + 1;
+            const int ow = (L.in_w + 2 * L.pad - L.kw) / L.stride + 1;
+            if (oh < 1 || ow < 1 || oh != L.out_h || ow != L.out_w)
+                return fail(c, AS_ERR_SHAPE, "layer %d: conv output %dx%d, given %dx%d", k + 1, oh, ow,
+                            L.out_h, L.out_w);
+            nin = L.in_c * L.in_h * L.in_w;
+            nout = L.out_c * oh * ow;
+        } else {
+            return fail(c, AS_ERR_ARG, "layer %d: unknown kind %d", k + 1, L.kind);
+        }
+        if (prev >= 0 && nin != prev)
+            return fail(c, AS_ERR_SHAPE, "layer %d takes %d inputs, previous layer gives %d", k + 1, nin, prev);
+        prev = nout;
+        c->layers.push_back(L);
+        if (k == 0) c->widths.push_back(nin);
+        if (k < n - 1) c->widths.push_back(nout);
+    }
+    c->n_out = prev;
+    return AS_OK;
+}
+
+static int validate_opt(as_ctx* c, const as_options& o) {
+    if (o.bigm_iters < 0 || o.as_iters < 0) return fail(c, AS_ERR_ARG, "negative iteration counts");
+    if (o.max_cuts < 0 || o.max_cuts > AS_MAX_CUTS) return fail(c, AS_ERR_ARG, "max_cuts not in [0, %d]", AS_MAX_CUTS);
+    if (o.vars_per_add < 1) return fail(c, AS_ERR_ARG, "vars_per_add < 1");
+    if (o.omega > 0 && o.omega < o.vars_per_add) return fail(c, AS_ERR_ARG, "omega < vars_per_add");
+    if (!(o.adam_b1 >= 0 && o.adam_b1 < 1 && o.adam_b2 >= 0 && o.adam_b2 < 1 && o.adam_eps > 0))
+        return fail(c, AS_ERR_ARG, "bad Adam parameters");
+    if (!(o.sp_gamma0 >= 1)) return fail(c, AS_ERR_ARG, "sp_gamma0 < 1");
+    if (!(o.sp_c_alpha > 0 && o.sp_c_beta > 0)) return fail(c, AS_ERR_ARG, "price-cap constants must be > 0");
+    if (o.sp_init_steps < 0 || o.graph_chunk < 0) return fail(c, AS_ERR_ARG, "negative step counts");
+    return AS_OK;
+}
+
+static int build_tables(as_ctx* c) {
+    const as_options& o = c->opt;
+    const int ntab = o.bigm_iters + o.as_iters + 2;
+    std::vector<float> lr(ntab), b1(ntab), b2(ntab);
+    const double lr_end = o.as_iters > 0 ? o.as_lr1 : o.bigm_lr1;
+    for (int it = 0; it < ntab; ++it) {
+        double v;
+        if (it < o.bigm_iters) v = o.bigm_lr0 + (o.bigm_lr1 - o.bigm_lr0) * it / std::max(1, o.bigm_iters - 1);
+        else if (it - o.bigm_iters < o.as_iters)
+            v = o.as_lr0 + (o.as_lr1 - o.as_lr0) * (it - o.bigm_iters) / std::max(1, o.as_iters - 1);
+        else v = lr_end;
+        lr[it] = (float)v;
+        b1[it] = (float)(1.0 - std::pow(o.adam_b1, (double)it));
+        b2[it] = (float)(1.0 - std::pow(o.adam_b2, (double)it));
+    }
+    float *dlr, *db1, *db2;
+    TRY(dalloc(c, &dlr, ntab));
+    TRY(dalloc(c, &db1, ntab));
+    TRY(dalloc(c, &db2, ntab));
+    CUDA_TRY(c, cudaMemcpyAsync(dlr, lr.data(), ntab * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(db1, b1.data(), ntab * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(db2, b2.data(), ntab * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));  // host vectors go out of scope
+    c->st.lr_tab = dlr;
+    c->st.bc1_tab = db1;
+    c->st.bc2_tab = db2;
+    DSched& d = c->sc;
+    d.TM = o.bigm_iters;
+    d.TA = o.as_iters;
+    d.omega = o.omega;
+    d.vpa = o.vars_per_add;
+    d.maxcut = o.max_cuts;
+    d.ntab = ntab;
+    d.b1 = (float)o.adam_b1;
+    d.omb1 = (float)(1.0 - o.adam_b1);
+    d.b2 = (float)o.adam_b2;
+    d.omb2 = (float)(1.0 - o.adam_b2);
+    d.eps = (float)o.adam_eps;
+    d.lr_as_end = (float)lr_end;
+    d.gamma0 = (float)o.sp_gamma0;
+    d.sp_init_steps = o.sp_init_steps;
+    d.sp_lr0 = (float)o.sp_init_lr0;
+    d.sp_lr1 = (float)o.sp_init_lr1;
+    return AS_OK;
+}
+
+static int grid_for(size_t n) { return (int)std::min<size_t>((n + CB_THREADS - 1) / CB_THREADS, 152 * 16); }
+
+
+// Device state in two arenas: the "zeroed" arena holds everything a new batch starts from zero
+// (duals, Adam moments, slots, snapshots, Saddle Point statistics, counters), so that a reset is
+// one memset; the other arena holds buffers each batch overwrites before reading.
+struct Bump {
+    char* base;
+    size_t off;
+    template <class T>
+    T* take(size_t count) {
+        off = (off + 255) & ~(size_t)255;
+        T* p = (T*)(base + off);
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+static int alloc_state(as_ctx* c) {
+    DNet& D = c->net;
+    DState& st = c->st;
+    const size_t S = D.S, NT = D.NT, NH = D.NH;
+    const size_t NTS = S * NT, NHS = S * NH, SL = S * D.cap * NH;
+    const int n = D.n;
+    for (int pass = 0; pass < 2; ++pass) {
+        Bump z{pass ? c->zero_arena : nullptr, 0};
+        float** zf[] = {&st.alpha, &st.beta0, &st.beta1, &st.ma, &st.va, &st.m0, &st.v0, &st.m1, &st.v1,
+                        &st.Sb, &st.G, &st.C, &st.mua, &st.mub, &st.ab, &st.b0i, &st.b1i};
+        for (float** p : zf) *p = z.take<float>(NHS);
+        float** zs[] = {&st.bs, &st.ms, &st.vs, &st.lam, &st.kap};
+        for (float** p : zs) *p = z.take<float>(SL);
+        st.P = z.take<float>(NTS);
+        for (int q = 0; q < 2; ++q) {
+            st.xsnap[q] = z.take<uint8_t>(NTS);
+            st.zsnap[q] = z.take<uint8_t>(NHS);
+        }
+        st.ctr = z.take<int>(4);
+        st.done = z.take<unsigned>(4);
+        st.status = z.take<int>(1);
+        Bump o{pass ? c->work_arena : nullptr, 0};
+        st.lo = o.take<float>(NTS);
+        st.hi = o.take<float>(NTS);
+        st.lhat = o.take<float>(NHS);
+        st.uhat = o.take<float>(NHS);
+        st.xval = o.take<float>(NTS);
+        st.fval = o.take<float>(NTS);
+        st.xbar = o.take<float>(NTS);
+        st.taup = o.take<float>(NTS);
+        st.taun = o.take<float>(NTS);
+        for (int q = 0; q < 2; ++q) {
+            st.spx[q] = o.take<float>(NTS);
+            st.spz[q] = o.take<float>(NHS);
+        }
+        st.zcur = o.take<uint8_t>(NHS);
+        st.zbar = o.take<uint8_t>(NHS);
+        st.sel = o.take<uint8_t>(NHS);
+        st.terms = o.take<double>(NTS);
+        st.best = o.take<double>(S);
+        D.Wout = o.take<float>(S * c->widths[n - 1]);
+        D.bout = o.take<float>(S);
+        c->caps_dev = o.take<int>(S);
+        c->C = o.take<float>(S * c->n_out);
+        c->splits_dev = o.take<signed char>(NHS);
+        c->bound_out = o.take<double>(S);
+        st.caps = c->caps_dev;
+        if (pass == 0) {
+            c->zero_bytes = z.off;
+            TRY(dalloc(c, &c->zero_arena, z.off));
+            TRY(dalloc(c, &c->work_arena, o.off));
+        }
+    }
+    CUDA_TRY(c, cudaMemsetAsync(c->st.terms, 0, NTS * sizeof(double), c->stream));
+    return AS_OK;
+}
+
+// Box, property rows, intermediate bounds, splits and caps of a batch; zeroes the duals.
+static int load_batch(as_ctx* c, const float* x_lo, const float* x_hi, const float* C, const float* lhat,
+                      const float* uhat, const signed char* splits, const int* caps, bool host_checks) {
+    if (!x_lo || !x_hi) return fail(c, AS_ERR_ARG, "null input box");
+    if ((lhat == nullptr) != (uhat == nullptr)) return fail(c, AS_ERR_ARG, "give both lhat and uhat or neither");
+    if (!C && c->n_out != 1) return fail(c, AS_ERR_ARG, "C is null but the last layer has %d outputs", c->n_out);
+    DNet& D = c->net;
+    DState& st = c->st;
+    const int S = D.S, n = D.n, n0 = c->widths[0];
+    const size_t NT = D.NT, NHS = (size_t)S * D.NH;
+    cudaStream_t s = c->stream;
+    CUDA_TRY(c, cudaMemsetAsync(c->zero_arena, 0, c->zero_bytes, s));
+    k_fill<<<grid_for(S), CB_THREADS, 0, s>>>(st.best, (size_t)S, -INFINITY);
+    c->launches++;
+    c->sp_started = false;
+    if (host_checks) {
+        std::vector<float> hl((size_t)S * n0), hh((size_t)S * n0);
+        CUDA_TRY(c, cudaMemcpyAsync(hl.data(), x_lo, hl.size() * sizeof(float), cudaMemcpyDefault, s));
+        CUDA_TRY(c, cudaMemcpyAsync(hh.data(), x_hi, hh.size() * sizeof(float), cudaMemcpyDefault, s));
+        CUDA_TRY(c, cudaStreamSynchronize(s));
+        for (size_t q = 0; q < hl.size(); ++q)
+            if (!(hl[q] <= hh[q]) || !std::isfinite(hl[q]) || !std::isfinite(hh[q]))
+                return fail(c, AS_ERR_ARG, "input box entry %zu: lo = %g, hi = %g", q, hl[q], hh[q]);
+        if (caps) {
+            std::vector<int> hc(S);
+            CUDA_TRY(c, cudaMemcpyAsync(hc.data(), caps, S * sizeof(int), cudaMemcpyDefault, s));
+            CUDA_TRY(c, cudaStreamSynchronize(s));
+            for (int q = 0; q < S; ++q)
+                if (hc[q] < 0 || hc[q] > c->opt.max_cuts)
+                    return fail(c, AS_ERR_ARG, "caps[%d] = %d not in [0, max_cuts]", q, hc[q]);
+        }
+    }
+    // box into the layer-0 part of the [S][NT] bound vectors
+    CUDA_TRY(c, cudaMemcpy2DAsync(st.lo, NT * sizeof(float), x_lo, n0 * sizeof(float), n0 * sizeof(float), S,
+                                  cudaMemcpyDefault, s));
+    CUDA_TRY(c, cudaMemcpy2DAsync(st.hi, NT * sizeof(float), x_hi, n0 * sizeof(float), n0 * sizeof(float), S,
+                                  cudaMemcpyDefault, s));
+    if (!host_checks) {
+        k_check_box<<<grid_for((size_t)S * n0), CB_THREADS, 0, s>>>(D, st);
+        c->launches++;
+    }
+    if (caps) CUDA_TRY(c, cudaMemcpyAsync(c->caps_dev, caps, S * sizeof(int), cudaMemcpyDefault, s));
+    else {
+        k_fill_int<<<grid_for(S), CB_THREADS, 0, s>>>(c->caps_dev, (size_t)S, c->opt.max_cuts);
+        c->launches++;
+    }
+    if (C) CUDA_TRY(c, cudaMemcpyAsync(c->C, C, (size_t)S * c->n_out * sizeof(float), cudaMemcpyDefault, s));
+    k_fold<<<grid_for((size_t)S * (c->widths[n - 1] + 1)), CB_THREADS, 0, s>>>(D, c->Wlast, c->blast,
+                                                                             C ? c->C : nullptr, c->n_out,
+                                                                             (float*)D.Wout, (float*)D.bout);
+    c->launches++;
+    TRY(check_launch(c, "k_fold"));
+    if (lhat) {
+        CUDA_TRY(c, cudaMemcpyAsync(st.lhat, lhat, NHS * sizeof(float), cudaMemcpyDefault, s));
+        CUDA_TRY(c, cudaMemcpyAsync(st.uhat, uhat, NHS * sizeof(float), cudaMemcpyDefault, s));
+        if (host_checks) {
+            std::vector<float> a(NHS), b(NHS);
+            CUDA_TRY(c, cudaMemcpyAsync(a.data(), st.lhat, NHS * sizeof(float), cudaMemcpyDeviceToHost, s));
+            CUDA_TRY(c, cudaMemcpyAsync(b.data(), st.uhat, NHS * sizeof(float), cudaMemcpyDeviceToHost, s));
+            CUDA_TRY(c, cudaStreamSynchronize(s));
+            for (size_t q = 0; q < NHS; ++q)
+                if (!(a[q] <= b[q])) return fail(c, AS_ERR_ARG, "lhat > uhat at hidden entry %zu", q);
+        }
+        k_post_from_pre<<<grid_for(NHS), CB_THREADS, 0, s>>>(D, st);
+        c->launches++;
+        TRY(check_launch(c, "k_post_from_pre"));
+    } else {
+        const signed char* dsp = nullptr;
+        if (splits) {
+            CUDA_TRY(c, cudaMemcpyAsync(c->splits_dev, splits, NHS, cudaMemcpyDefault, s));
+            dsp = c->splits_dev;
+        }
+        for (int k = 0; k < n - 1; ++k) {
+            const long long warps = (long long)S * D.L[k].n_out;
+            k_ibp<<<(int)((warps + CB_WARPS - 1) / CB_WARPS), CB_THREADS, 0, s>>>(D, st, k, dsp);
+            c->launches++;
+            TRY(check_launch(c, "k_ibp"));
+        }
+    }
+    return AS_OK;
+}
+
+extern "C" int as_reset(as_ctx* c, const float* x_lo, const float* x_hi, const float* C, const float* lhat,
+                        const float* uhat, const signed char* splits, const int* caps) {
+    if (!c) return AS_ERR_ARG;
+    if (!c->zero_arena) return fail(c, AS_ERR_STATE, "context was not initialised");
+    return load_batch(c, x_lo, x_hi, C, lhat, uhat, splits, caps, false);
+}
+
+static int init_impl(as_ctx* c, const as_net* net, int S, const float* x_lo, const float* x_hi, const float* C,
+                     const float* lhat, const float* uhat, const signed char* splits, const int* caps,
+                     const as_options* opt) {
+    if (S < 1) return fail(c, AS_ERR_ARG, "S = %d < 1", S);
+    if (!x_lo || !x_hi) return fail(c, AS_ERR_ARG, "null input box");
+    if ((lhat == nullptr) != (uhat == nullptr)) return fail(c, AS_ERR_ARG, "give both lhat and uhat or neither");
+    if (opt) c->opt = *opt;
+    else as_default_options(&c->opt);
+    TRY(validate_opt(c, c->opt));
+    TRY(validate_net(c, net));
+    if (!C && c->n_out != 1) return fail(c, AS_ERR_ARG, "C is null but the last layer has %d outputs", c->n_out);
+    const int n = net->n_layers;
+    DNet& D = c->net;
+    D.n = n;
+    D.S = S;
+    D.cap = std::max(1, c->opt.max_cuts);
+    int NT = 0;
+    std::vector<int> off(n);
+    for (int m = 0; m < n; ++m) {
+        off[m] = NT;
+        NT += c->widths[m];
+    }
+    D.NT = NT;
+    D.NH = NT - c->widths[0];
+    // weights
+    for (int k = 0; k < n; ++k) {
+        const as_layer& A = c->layers[k];
+        DLayer& L = D.L[k];
+        L.kind = A.kind;
+        if (A.kind == AS_LAYER_LINEAR) {
+            L.n_in = A.in_c;
+            L.n_out = A.out_c;
+            L.ci = A.in_c; L.hi = 1; L.wi = 1; L.co = A.out_c; L.ho = 1; L.wo = 1;
+            L.kh = L.kw = L.st = 1; L.pd = 0;
+        } else {
+            L.ci = A.in_c; L.hi = A.in_h; L.wi = A.in_w; L.co = A.out_c; L.ho = A.out_h; L.wo = A.out_w;
+            L.kh = A.kh; L.kw = A.kw; L.st = A.stride; L.pd = A.pad;
+            L.n_in = L.ci * L.hi * L.wi;
+            L.n_out = L.co * L.ho * L.wo;
+        }
+        const size_t wcount = A.kind == AS_LAYER_LINEAR ? (size_t)L.n_out * L.n_in
+                                                         : (size_t)L.co * L.ci * L.kh * L.kw;
+        const int bcount = A.kind == AS_LAYER_LINEAR ? L.n_out : L.co;
+        float *W, *b;
+        TRY(dalloc(c, &W, wcount));
+        CUDA_TRY(c, cudaMemcpyAsync(W, A.W, wcount * sizeof(float), cudaMemcpyDefault, c->stream));
+        std::vector<float> hb(bcount), hbe(L.n_out);
+        CUDA_TRY(c, cudaMemcpyAsync(hb.data(), A.b, bcount * sizeof(float), cudaMemcpyDefault, c->stream));
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        const int per = L.n_out / bcount;
+        for (int i = 0; i < L.n_out; ++i) hbe[i] = hb[i / per];
+        TRY(dalloc(c, &b, L.n_out));
+        CUDA_TRY(c, cudaMemcpyAsync(b, hbe.data(), L.n_out * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        L.W = W;
+        L.b = b;
+        L.in_off = off[k];
+        L.out_off = k + 1 < n ? off[k + 1] : -1;
+        L.h_in = k >= 1 ? off[k] - c->widths[0] : -1;
+        L.h_out = k + 1 < n ? off[k + 1] - c->widths[0] : -1;
+        if (k == n - 1) {
+            c->Wlast = W;
+            c->blast = b;
+        }
+    }
+    // launch geometry
+    {
+        std::vector<int> ids;
+        std::vector<long long> units;
+        for (int k = 0; k < n; ++k) {
+            ids.push_back(k);
+            units.push_back((long long)S * D.L[k].n_in);
+        }
+        make_segs(c->segA, c->blocksA, ids, units, CB_THREADS);
+        ids.clear();
+        units.clear();
+        for (int k = 0; k < n - 1; ++k) {
+            ids.push_back(k);
+            units.push_back((long long)S * D.L[k].n_out);
+        }
+        make_segs(c->segB, c->blocksB, ids, units, CB_WARPS);
+        ids.clear();
+        units.clear();
+        for (int k = 0; k < n - 1; ++k) {
+            ids.push_back(k);
+            units.push_back((long long)S * D.L[k].n_in);
+        }
+        make_segs(c->segP, c->blocksP, ids, units, CB_THREADS);
+    }
+    TRY(alloc_state(c));
+    TRY(build_tables(c));
+    TRY(load_batch(c, x_lo, x_hi, C, lhat, uhat, splits, caps, true));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return AS_OK;
+}
+
+extern "C" int as_init(as_ctx** out, const as_net* net, int S, const float* x_lo, const float* x_hi, const float* C,
+                       const float* lhat, const float* uhat, const signed char* splits, const int* caps,
+                       const as_options* opt, void* stream) {
+    if (!out) return AS_ERR_ARG;
+    *out = nullptr;
+    as_ctx* c = new (std::nothrow) as_ctx();
+    if (!c) return AS_ERR_OOM;
+    c->stream = (cudaStream_t)stream;
+    cudaError_t e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete c;
+        return AS_ERR_CUDA;
+    }
+    int r = init_impl(c, net, S, x_lo, x_hi, C, lhat, uhat, splits, caps, opt);
+    *out = c;  // returned even on failure so that as_last_error can explain; caller destroys it
+    return r;
+}
+
+extern "C" void as_destroy(as_ctx* c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    if (c->g_as) cudaGraphExecDestroy(c->g_as);
+    if (c->g_sp) cudaGraphExecDestroy(c->g_sp);
+    for (void* p : c->allocs) cudaFree(p);
+    for (auto& r : c->pending) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    delete c;
+}
+
+// ------------------------------------------------------------------------------- iterations
+// Per-kernel timing: with as_options.profile set, each launch is bracketed by CUDA events on its
+// stream; as_kernel_times reads and accumulates them.
+static cudaEvent_t prof_event(as_ctx* c) {
+    if (!c->pool.empty()) {
+        cudaEvent_t e = c->pool.back();
+        c->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+#define LAUNCH(c, s, id, ...)                                      \
+    do {                                                           \
+        if ((c)->opt.profile) {                                    \
+            as_ctx::Rec r_{id, prof_event(c), prof_event(c)};      \
+            cudaEventRecord(r_.a, s);                              \
+            __VA_ARGS__;                                           \
+            cudaEventRecord(r_.b, s);                              \
+            (c)->pending.push_back(r_);                            \
+        } else {                                                   \
+            __VA_ARGS__;                                           \
+        }                                                          \
+        (c)->launches++;                                           \
+    } while (0)
+
+static int launch_as_iter(as_ctx* c, cudaStream_t s) {
+    LAUNCH(c, s, CB_K_AS_COLA, (k_as_colA<<<c->blocksA, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->segA, 0)));
+    if (c->opt.track_best)
+        LAUNCH(c, s, CB_K_REDUCE, (k_reduce<<<c->net.S, CB_THREADS, 0, s>>>(c->net, c->st, 64, nullptr, 1)));
+    LAUNCH(c, s, CB_K_AS_ROWB, (k_as_rowB<<<c->blocksB, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->segB)));
+    return check_launch(c, "Active Set iteration");
+}
+
+static int launch_sp_iter(as_ctx* c, cudaStream_t s) {
+    LAUNCH(c, s, CB_K_SP_COLA, (k_sp_colA<<<c->blocksA, CB_THREADS, 0, s>>>(c->net, c->st, c->segA, 0)));
+    if (c->opt.track_best)
+        LAUNCH(c, s, CB_K_REDUCE, (k_reduce<<<c->net.S, CB_THREADS, 0, s>>>(c->net, c->st, 64, nullptr, 1)));
+    LAUNCH(c, s, CB_K_SP_ROWB, (k_sp_rowB<<<c->blocksB, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->segB)));
+    LAUNCH(c, s, CB_K_SP_COLC, (k_sp_colC<<<c->blocksA, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->segA)));
+    return check_launch(c, "Saddle Point iteration");
+}
+
+extern "C" int as_kernel_times(as_ctx* c, int kernel, double* total_ms, long long* launches) {
+    if (!c || kernel < 0 || kernel >= CB_NPROF) return AS_ERR_ARG;
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    for (auto& r : c->pending) {
+        float ms = 0.f;
+        cudaError_t e = cudaEventElapsedTime(&ms, r.a, r.b);
+        if (e != cudaSuccess) return fail(c, AS_ERR_CUDA, "event timing failed: %s", cudaGetErrorString(e));
+        c->prof_ms[r.id] += ms;
+        c->prof_n[r.id] += 1;
+        c->pool.push_back(r.a);
+        c->pool.push_back(r.b);
+    }
+    c->pending.clear();
+    if (total_ms) *total_ms = c->prof_ms[kernel];
+    if (launches) *launches = c->prof_n[kernel];
+    return AS_OK;
+}
+
+typedef int (*iter_fn)(as_ctx*, cudaStream_t);
+
+static int run_iters(as_ctx* c, int n_iters, iter_fn fn, cudaGraphExec_t* gexec, int* glen, int* gnodes) {
+    const int G = c->opt.profile ? 0 : c->opt.graph_chunk;
+    int done = 0;
+    if (G > 1 && n_iters >= G) {
+        if (!*gexec) {
+            const long long before = c->launches;
+            CUDA_TRY(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+            int r = AS_OK;
+            for (int q = 0; q < G && r == AS_OK; ++q) r = fn(c, c->cap_stream);
+            cudaGraph_t g;
+            cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+            if (r != AS_OK) return r;
+            if (e != cudaSuccess) return fail(c, AS_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+            e = cudaGraphInstantiate(gexec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return fail(c, AS_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+            *glen = G;
+            *gnodes = (int)(c->launches - before);
+            c->launches = before;  // captured, not executed
+        }
+        for (; done + *glen <= n_iters; done += *glen) {
+            CUDA_TRY(c, cudaGraphLaunch(*gexec, c->stream));
+            c->launches += *gnodes;
+        }
+    }
+    for (; done < n_iters; ++done) TRY(fn(c, c->stream));
+    return AS_OK;
+}
+
+extern "C" int as_step(as_ctx* c, int n_iters) {
+    if (!c) return AS_ERR_ARG;
+    if (n_iters < 0) return fail(c, AS_ERR_ARG, "n_iters < 0");
+    if (c->sp_started) return fail(c, AS_ERR_STATE, "Saddle Point has started on this context");
+    return run_iters(c, n_iters, launch_as_iter, &c->g_as, &c->g_as_len, &c->g_as_nodes);
+}
+
+static int sp_start(as_ctx* c) {
+    cudaStream_t s = c->stream;
+    const size_t NHS = (size_t)c->net.S * c->net.NH;
+    k_sp_convert_elem<<<grid_for(NHS), CB_THREADS, 0, s>>>(c->net, c->st, c->sc, (float)c->opt.sp_c_alpha,
+                                                           (float)c->opt.sp_c_beta);
+    k_sp_convert_P<<<c->blocksP, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->segP);
+    k_sp_colA<<<c->blocksA, CB_THREADS, 0, s>>>(c->net, c->st, c->segA, 1);
+    c->launches += 3;
+    TRY(check_launch(c, "Saddle Point conversion"));
+    for (int t = 0; t < c->opt.sp_init_steps; ++t) {
+        LAUNCH(c, s, CB_K_SPI_ROW, (k_spi_row<<<c->blocksB, CB_THREADS, 0, s>>>(c->net, c->st, c->segB)));
+        LAUNCH(c, s, CB_K_SPI_COL, (k_spi_col<<<c->blocksA, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->segA)));
+    }
+    TRY(check_launch(c, "Saddle Point primal initialisation"));
+    c->sp_started = true;
+    return AS_OK;
+}
+
+extern "C" int sp_step(as_ctx* c, int n_iters) {
+    if (!c) return AS_ERR_ARG;
+    if (n_iters < 0) return fail(c, AS_ERR_ARG, "n_iters < 0");
+    if (!c->sp_started) TRY(sp_start(c));
+    return run_iters(c, n_iters, launch_sp_iter, &c->g_sp, &c->g_sp_len, &c->g_sp_nodes);
+}
+
+extern "C" int as_bound(as_ctx* c, int precision, double* out, double* best) {
+    if (!c) return AS_ERR_ARG;
+    if (precision != 32 && precision != 64) return fail(c, AS_ERR_ARG, "precision must be 32 or 64");
+    const int S = c->net.S;
+    cudaStream_t s = c->stream;
+    if (c->sp_started) LAUNCH(c, s, CB_K_SP_COLA, (k_sp_colA<<<c->blocksA, CB_THREADS, 0, s>>>(c->net, c->st, c->segA, 0)));
+    else LAUNCH(c, s, CB_K_AS_COLA, (k_as_colA<<<c->blocksA, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->segA, 1)));
+    double* dout = c->bound_out;
+    LAUNCH(c, s, CB_K_REDUCE, (k_reduce<<<S, CB_THREADS, 0, s>>>(c->net, c->st, precision, dout, 1)));
+    TRY(check_launch(c, "bound evaluation"));
+    std::vector<double> h(S);
+    int status = 0;
+    CUDA_TRY(c, cudaMemcpyAsync(h.data(), dout, S * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(c, cudaMemcpyAsync(&status, c->st.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (out) CUDA_TRY(c, cudaMemcpyAsync(out, dout, S * sizeof(double), cudaMemcpyDefault, s));
+    if (best) CUDA_TRY(c, cudaMemcpyAsync(best, c->st.best, S * sizeof(double), cudaMemcpyDefault, s));
+    CUDA_TRY(c, cudaStreamSynchronize(s));
+    if (status) return fail(c, AS_ERR_ARG, "the batch's input box has lo > hi or a non-finite entry");
+    for (int q = 0; q < S; ++q)
+        if (!std::isfinite(h[q])) return fail(c, AS_ERR_NUMERIC, "bound of subproblem %d is %g", q, h[q]);
+    return AS_OK;
+}
+
+// ------------------------------------------------------------------------------ state access
+struct StateBuf {
+    void* p;
+    size_t bytes;
+};
+
+static StateBuf state_buf(as_ctx* c, int which, int part = 0) {
+    const size_t S = c->net.S, NT = c->net.NT, NH = c->net.NH, cap = c->net.cap;
+    DState& st = c->st;
+    const int bo = 0;
+    (void)bo;
+    switch (which) {
+        case AS_ST_ALPHA: return {st.alpha, S * NH * 4};
+        case AS_ST_BETA0: return {st.beta0, S * NH * 4};
+        case AS_ST_BETA1: return {st.beta1, S * NH * 4};
+        case AS_ST_SLOT_BETA: return {st.bs, S * cap * NH * 4};
+        case AS_ST_LHAT: return {st.lhat, S * NH * 4};
+        case AS_ST_UHAT: return {st.uhat, S * NH * 4};
+        case AS_ST_XSTAR: return {st.xval, S * NT * 4};
+        case AS_ST_ZSTAR: return {st.zcur, S * NH};
+        case AS_ST_LAMBDA: return {st.lam, S * cap * NH * 4};
+        case AS_ST_KAPPA: return {st.kap, S * cap * NH * 4};
+        case AS_ST_LO: return {st.lo, S * NT * 4};
+        case AS_ST_SP_SEL: return {st.sel, S * NH};
+        case AS_ST_HI: return {st.hi, S * NT * 4};
+        default: return {nullptr, 0};
+    }
+}
+
+static int snap_parity(as_ctx* c, int* par) {
+    int it = 0;
+    CUDA_TRY(c, cudaMemcpyAsync(&it, c->st.ctr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    int nadd = 0;
+    if (it >= c->sc.TM) nadd = cb_additions_before(it - c->sc.TM, c->sc);
+    *par = nadd & 1;
+    return AS_OK;
+}
+
+extern "C" int as_state_size(as_ctx* c, int which, long long* nbytes) {
+    if (!c || !nbytes) return AS_ERR_ARG;
+    const size_t S = c->net.S, NT = c->net.NT, NH = c->net.NH, cap = c->net.cap;
+    size_t b;
+    switch (which) {
+        case AS_ST_XSNAP: b = S * NT; break;
+        case AS_ST_ZSNAP: b = S * NH; break;
+        case AS_ST_ITER: b = 3 * sizeof(int); break;
+        case AS_ST_ADAM: b = 6 * S * NH * 4; break;
+        case AS_ST_SLOT_ADAM: b = 2 * S * cap * NH * 4; break;
+        case AS_ST_SP_X: b = S * NT * 4; break;
+        case AS_ST_SP_Z: b = S * NH * 4; break;
+        case AS_ST_SP_STATS: b = 4 * S * NT * 4; break;
+        case AS_ST_SP_CAPS: b = 2 * S * NH * 4; break;
+        default: {
+            StateBuf sb = state_buf(c, which);
+            if (!sb.p) return fail(c, AS_ERR_ARG, "unknown state buffer %d", which);
+            b = sb.bytes;
+        }
+    }
+    *nbytes = (long long)b;
+    return AS_OK;
+}
+
+static int copy_pieces(as_ctx* c, void* dst, const void* src, bool out, std::vector<StateBuf> parts) {
+    size_t o = 0;
+    for (auto& p : parts) {
+        if (out) CUDA_TRY(c, cudaMemcpyAsync((char*)dst + o, p.p, p.bytes, cudaMemcpyDefault, c->stream));
+        else CUDA_TRY(c, cudaMemcpyAsync(p.p, (const char*)src + o, p.bytes, cudaMemcpyDefault, c->stream));
+        o += p.bytes;
+    }
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return AS_OK;
+}
+
+static std::vector<StateBuf> composite(as_ctx* c, int which, int par) {
+    const size_t S = c->net.S, NT = c->net.NT, NH = c->net.NH, cap = c->net.cap;
+    DState& st = c->st;
+    int cur = 0;
+    switch (which) {
+        case AS_ST_XSNAP: return {{st.xsnap[par], S * NT}};
+        case AS_ST_ZSNAP: return {{st.zsnap[par], S * NH}};
+        case AS_ST_ITER: return {{st.ctr, 3 * sizeof(int)}};
+        case AS_ST_ADAM:
+            return {{st.ma, S * NH * 4}, {st.va, S * NH * 4}, {st.m0, S * NH * 4},
+                    {st.v0, S * NH * 4}, {st.m1, S * NH * 4}, {st.v1, S * NH * 4}};
+        case AS_ST_SLOT_ADAM: return {{st.ms, S * cap * NH * 4}, {st.vs, S * cap * NH * 4}};
+        case AS_ST_SP_X: cur = par; return {{st.spx[cur], S * NT * 4}};
+        case AS_ST_SP_Z: cur = par; return {{st.spz[cur], S * NH * 4}};
+        case AS_ST_SP_CAPS: return {{st.mua, S * NH * 4}, {st.mub, S * NH * 4}};
+        default: {
+            StateBuf sb = state_buf(c, which);
+            return {sb};
+        }
+    }
+}
+
+static int sp_parity(as_ctx* c, int* par) {
+    int t = 0;
+    CUDA_TRY(c, cudaMemcpyAsync(&t, c->st.ctr + 1, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    *par = t & 1;
+    return AS_OK;
+}
+
+extern "C" int as_get_state(as_ctx* c, int which, void* dst) {
+    if (!c || !dst) return AS_ERR_ARG;
+    if (which < 0 || which >= AS_ST_COUNT) return fail(c, AS_ERR_ARG, "unknown state buffer %d", which);
+    int par = 0;
+    if (which == AS_ST_XSNAP || which == AS_ST_ZSNAP) TRY(snap_parity(c, &par));
+    if (which == AS_ST_SP_X || which == AS_ST_SP_Z) TRY(sp_parity(c, &par));
+    if (which == AS_ST_ITER) {
+        int v[3];
+        CUDA_TRY(c, cudaMemcpyAsync(v, c->st.ctr, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        v[2] = c->sp_started ? 1 : 0;
+        CUDA_TRY(c, cudaMemcpy(dst, v, sizeof v, cudaMemcpyDefault));
+        return AS_OK;
+    }
+    if (which == AS_ST_SP_STATS) {
+        const size_t S = c->net.S, NT = c->net.NT, NH = c->net.NH;
+        // [4][S][NT]: Sb, G, C placed at the hidden part of each row, P as is
+        std::vector<float> h(4 * S * NT, 0.f), t(S * NH);
+        float* src[3] = {c->st.Sb, c->st.G, c->st.C};
+        for (int q = 0; q < 3; ++q) {
+            CUDA_TRY(c, cudaMemcpyAsync(t.data(), src[q], S * NH * 4, cudaMemcpyDeviceToHost, c->stream));
+            CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+            for (size_t s = 0; s < S; ++s)
+                std::memcpy(&h[(q * S + s) * NT + (NT - NH)], &t[s * NH], NH * 4);
+        }
+        CUDA_TRY(c, cudaMemcpyAsync(&h[3 * S * NT], c->st.P, S * NT * 4, cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        CUDA_TRY(c, cudaMemcpy(dst, h.data(), h.size() * 4, cudaMemcpyDefault));
+        return AS_OK;
+    }
+    return copy_pieces(c, dst, nullptr, true, composite(c, which, par));
+}
+
+static int recompute_slot_sums(as_ctx* c);
+
+extern "C" int as_set_state(as_ctx* c, int which, const void* src) {
+    if (!c || !src) return AS_ERR_ARG;
+    if (which < 0 || which >= AS_ST_COUNT) return fail(c, AS_ERR_ARG, "unknown state buffer %d", which);
+    if (which == AS_ST_XSTAR || which == AS_ST_ZSTAR || which == AS_ST_LAMBDA || which == AS_ST_KAPPA ||
+        which == AS_ST_LO || which == AS_ST_HI || which == AS_ST_LHAT || which == AS_ST_UHAT ||
+        which == AS_ST_SP_SEL)
+        return fail(c, AS_ERR_ARG, "state buffer %d is read-only", which);
+    if (which == AS_ST_ITER) {
+        int v[3];
+        CUDA_TRY(c, cudaMemcpy(v, src, sizeof v, cudaMemcpyDefault));
+        if (v[0] < 0 || v[1] < 0) return fail(c, AS_ERR_ARG, "negative iteration counter");
+        int w[3] = {v[0], v[1], v[2] ? c->opt.sp_init_steps : 0};
+        CUDA_TRY(c, cudaMemcpyAsync(c->st.ctr, w, sizeof w, cudaMemcpyHostToDevice, c->stream));
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        c->sp_started = v[2] != 0;
+        return recompute_slot_sums(c);
+    }
+    if (which == AS_ST_SP_STATS) {
+        const size_t S = c->net.S, NT = c->net.NT, NH = c->net.NH;
+        std::vector<float> h(4 * S * NT), t(S * NH);
+        CUDA_TRY(c, cudaMemcpy(h.data(), src, h.size() * 4, cudaMemcpyDefault));
+        float* dst3[3] = {c->st.Sb, c->st.G, c->st.C};
+        for (int q = 0; q < 3; ++q) {
+            for (size_t s = 0; s < S; ++s) std::memcpy(&t[s * NH], &h[(q * S + s) * NT + (NT - NH)], NH * 4);
+            CUDA_TRY(c, cudaMemcpyAsync(dst3[q], t.data(), S * NH * 4, cudaMemcpyHostToDevice, c->stream));
+            CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        }
+        CUDA_TRY(c, cudaMemcpyAsync(c->st.P, &h[3 * S * NT], S * NT * 4, cudaMemcpyHostToDevice, c->stream));
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        return AS_OK;
+    }
+    int par = 0;
+    if (which == AS_ST_XSNAP || which == AS_ST_ZSNAP) TRY(snap_parity(c, &par));
+    if (which == AS_ST_SP_X || which == AS_ST_SP_Z) TRY(sp_parity(c, &par));
+    TRY(copy_pieces(c, nullptr, src, false, composite(c, which, par)));
+    if (which == AS_ST_SLOT_BETA || which == AS_ST_XSNAP || which == AS_ST_ZSNAP) TRY(recompute_slot_sums(c));
+    return AS_OK;
+}
+
+#include "cb_host_extra.inc"

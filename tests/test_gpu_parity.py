@@ -1,0 +1,406 @@
+"""Parity of the CUDA library (through the C ABI) with the CPU FP64 oracle.
+
+Tolerances (float32 GPU arithmetic against FP64):
+  * interval bounds: the float32 interval contains the FP64 one and is within 4e-6 (1 + |v|) of it
+    (FP64 accumulation per layer, outward rounding to float32 at every layer);
+  * one-iteration lockstep of the duals: 1e-5 relative, 1e-7 absolute floor (the benchmark spec), on every
+    entry whose update direction is decided: entries where the oracle's gradient is within
+    1e-4 of zero are checked for validity only (both signs give a valid Adam step);
+  * bounds: 1e-4 absolute (the benchmark spec), 1e-5 relative where values are large;
+  * masks and snapshot bits: bit-exact.
+"""
+import numpy as np
+import pytest
+
+from oracle import active_set as AS
+from oracle import dual as du
+from oracle import envelope as ev
+from oracle import network as nw
+from oracle import saddle as SPm
+from paper_2101_05844_gb300 import binding, synth
+from tests.helpers import sample_min_output
+from tests.state_helpers import draw_state, hidden_concat, oracle_bounds_f32, split_hidden
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    assert torch.cuda.is_available()
+    binding.lib()
+
+
+def _problems(name, S=None, seed=0):
+    prob = synth.problem(name, S=S, seed=seed)
+    return prob, nw.problems(prob)
+
+
+@pytest.mark.parametrize("name,S", [("mlp_tiny", 1), ("small_conv", 3), ("wide_conv_bab", 6),
+                                    ("mlp_5_7_6_3", 4)])
+def test_interval_bounds_match_oracle(name, S):
+    prob, Ps = _problems(name, S)
+    ctx = binding.context_for(prob, binding.default_options())
+    lh = ctx.get_state(binding.ST_LHAT).reshape(ctx.S, -1)
+    uh = ctx.get_state(binding.ST_UHAT).reshape(ctx.S, -1)
+    for s, P in enumerate(Ps):
+        rl = hidden_concat(P.lhat)
+        ru = hidden_concat(P.uhat)
+        # sound: the float32 interval (outward rounding at every layer) contains the FP64 one
+        assert (lh[s] <= rl + 1e-9 * (1 + np.abs(rl))).all()
+        assert (uh[s] >= ru - 1e-9 * (1 + np.abs(ru))).all()
+        # and close: a few float32 ulps per layer of propagation
+        assert (np.abs(lh[s] - rl) <= 4e-6 * (1 + np.abs(rl))).all()
+        assert (np.abs(uh[s] - ru) <= 4e-6 * (1 + np.abs(ru))).all()
+    # zero duals: the bound is the interval bound of the output row
+    b = ctx.bound()
+    for s, P in enumerate(Ps):
+        assert b[s] == pytest.approx(P.ibp_output_bound(), abs=1e-4, rel=1e-5)
+
+
+CASES = [
+    # name, S, options, iteration, filled slots
+    ("mlp_tiny", 1, dict(bigm_iters=5, as_iters=40, omega=3, max_cuts=5), 3, 0),     # Big-M
+    ("mlp_tiny", 1, dict(bigm_iters=5, as_iters=40, omega=3, max_cuts=5), 7, 2),     # AS, no add
+    ("mlp_tiny", 1, dict(bigm_iters=5, as_iters=40, omega=3, max_cuts=5), 8, 2),     # AS, adds slot 2
+    ("small_conv", 3, dict(bigm_iters=5, as_iters=40, omega=3, max_cuts=5), 12, 4),  # adds slot 4
+    ("small_conv", 3, dict(bigm_iters=5, as_iters=40, omega=3, max_cuts=7), 10, 3),
+    ("mlp_5_7_6_3", 4, dict(bigm_iters=2, as_iters=30, omega=4, max_cuts=8), 16, 6),  # adds slot 6
+]
+
+
+@pytest.mark.parametrize("name,S,kw,it,nslots", CASES)
+def test_one_iteration_lockstep(name, S, kw, it, nslots):
+    prob, _ = _problems(name, S)
+    Ps0 = nw.problems(prob)
+    lh, uh = oracle_bounds_f32(Ps0)
+    Ps = nw.problems(prob, bounds=[(split_hidden(lh[s].astype(np.float64), Ps0[0].widths)[1:],
+                                    split_hidden(uh[s].astype(np.float64), Ps0[0].widths)[1:])
+                                   for s in range(len(Ps0))])
+    ctx = binding.context_for(prob, binding.default_options(graph_chunk=0, **kw), bounds=(lh, uh))
+    solvers = draw_state(Ps, ctx, kw, it, nslots, seed=100 + it)
+    # bound at the drawn duals
+    gb = ctx.bound()
+    for s, sv in enumerate(solvers):
+        val, f, g, x, z = du.evaluate(sv.P, sv.st)
+        assert gb[s] == pytest.approx(val, abs=1e-4, rel=1e-5)
+        # the minimiser is decided (no near-zero coefficient) for the lockstep below
+        assert min(np.abs(fk).min() for fk in f if fk is not None) > 1e-5
+        for gk in g[1:]:
+            assert ((gk == 0) | (np.abs(gk) > 1e-5)).all()
+    ctx.as_step(1)
+    xstar = ctx.get_state(binding.ST_XSTAR).reshape(S, -1)
+    zstar = ctx.get_state(binding.ST_ZSTAR, np.uint8).reshape(S, -1)
+    xs = ctx.get_state(binding.ST_XSNAP, np.uint8).reshape(S, -1)
+    zs = ctx.get_state(binding.ST_ZSNAP, np.uint8).reshape(S, -1)
+    al = ctx.get_state(binding.ST_ALPHA).reshape(S, -1)
+    b0 = ctx.get_state(binding.ST_BETA0).reshape(S, -1)
+    b1 = ctx.get_state(binding.ST_BETA1).reshape(S, -1)
+    sb = ctx.get_state(binding.ST_SLOT_BETA).reshape(S, ctx.cap, -1)
+    lam = ctx.get_state(binding.ST_LAMBDA).reshape(S, ctx.cap, -1)
+    for s, sv in enumerate(solvers):
+        P = sv.P
+        _, f, g, x, z = du.evaluate(P, sv.st)
+        grads = du.supergradient(P, sv.st, x, z)
+        slots_before = len(sv.st.slots[1])
+        sv.step(1)
+        # primal minimiser: exact
+        np.testing.assert_array_equal(xstar[s], np.concatenate([x[k] for k in range(P.n)]).astype(np.float32))
+        np.testing.assert_array_equal(zstar[s], hidden_concat(z).astype(np.uint8))
+        # the new slot's snapshot: the oracle's mask at (x*, z*) (bit-exact)
+        nnew = len(sv.st.slots[1])
+        if nnew > slots_before:
+            b = nnew - 1
+            offs = np.cumsum([0] + P.widths)
+            for k in range(1, P.n):
+                xb = ((xs[s, offs[k - 1]:offs[k]] >> b) & 1).astype(bool)
+                zb = ((zs[s, offs[k] - P.widths[0]:offs[k + 1] - P.widths[0]] >> b) & 1).astype(float)
+                from oracle import relaxation as rx
+                Igpu = rx.mask(P.W[k], P.lo[k - 1], P.hi[k - 1], np.where(xb, P.hi[k - 1], P.lo[k - 1]), zb)
+                np.testing.assert_array_equal(Igpu, sv.st.slots[k][b].I)
+            np.testing.assert_allclose(
+                lam[s, b], hidden_concat([None] + [sv.st.slots[k][b].lam for k in range(1, P.n)]),
+                rtol=1e-5, atol=1e-5)
+
+        def check(gpu, ref, gref):
+            decided = (np.abs(gref) > 1e-4) | (gref == 0)
+            np.testing.assert_allclose(gpu[decided], ref[decided], rtol=1e-5, atol=1e-7)
+            assert (gpu >= 0).all()
+            assert decided.mean() > 0.9
+        check(al[s], hidden_concat(sv.st.alpha), hidden_concat(grads["galpha"]))
+        check(b0[s], hidden_concat(sv.st.beta0), hidden_concat(grads["gbeta0"]))
+        check(b1[s], hidden_concat(sv.st.beta1), hidden_concat(grads["gbeta1"]))
+        for b in range(len(sv.st.slots[1])):
+            ref = hidden_concat([None] + [sv.st.slots[k][b].beta for k in range(1, P.n)])
+            if b < slots_before:
+                gref = hidden_concat([None] + [grads["gslots"][k][b] for k in range(1, P.n)])
+            else:
+                gref = np.ones_like(ref)
+            check(sb[s, b], ref, gref)
+
+
+def _as_margin(sv):
+    _, f, g, x, z = du.evaluate(sv.P, sv.st)
+    m = min(np.abs(fk).min() for fk in f)
+    for gk in g[1:]:
+        nz = gk[gk != 0]
+        if nz.size:
+            m = min(m, np.abs(nz).min())
+    return m
+
+
+@pytest.mark.parametrize("name,S,kw,iters,full", [
+    ("mlp_tiny", 1, dict(bigm_iters=20, as_iters=80, omega=24, max_cuts=5), 100, True),
+    ("mlp_5_7_6_3", 4, dict(bigm_iters=30, as_iters=60, omega=20, max_cuts=4), 90, False),
+    ("small_conv", 3, dict(bigm_iters=20, as_iters=40, omega=12, max_cuts=5), 60, False),
+])
+def test_free_running_active_set_matches_oracle(name, S, kw, iters, full):
+    """Iteration by iteration: the GPU and oracle bounds agree to 1e-4 until the first iteration
+    whose decisions the oracle takes within 1e-3 of a tie, the size float32 drift of the duals
+    reaches over tens of iterations (a rounding flip, after which the runs are different valid
+    runs). full: no such flip may occur, final bounds within 1e-4."""
+    prob, Ps = _problems(name, S)
+    ctx = binding.context_for(prob, binding.default_options(graph_chunk=0, track_best=1, **kw))
+    sol = [AS.ActiveSet(P, AS.Options(**kw)) for P in Ps]
+    live = [True] * S
+    for it in range(iters):
+        margins = [_as_margin(sv) for sv in sol]
+        ctx.as_step(1)
+        gb = ctx.bound()
+        for s, sv in enumerate(sol):
+            if not live[s]:
+                continue
+            sv.step(1)
+            ob = du.evaluate(sv.P, sv.st)[0]
+            if abs(gb[s] - ob) > 1e-4:
+                assert margins[s] < 1e-3, f"divergence at iteration {it} without a near-tie (margin {margins[s]})"
+                assert not full, f"near-tie flip at iteration {it} (margin {margins[s]})"
+                live[s] = False
+    b, best = ctx.bound(best=True)
+    for s, P in enumerate(Ps):
+        if live[s]:
+            assert b[s] == pytest.approx(sol[s].bound(), abs=1e-4)
+            assert best[s] == pytest.approx(sol[s].best, abs=1e-4)
+        assert best[s] >= P.ibp_output_bound() - 1e-6
+    if full:
+        assert all(live)
+
+
+def _draw_sp_state(Ps, seed, t):
+    """A random Saddle Point iterate for every subproblem (generator only) and its oracle solvers.
+    Seeds are tried in order until every decision taken on a sum (f, xhat - x, the choice of
+    eq. 12) clears 2e-6, the size of float32 summation error here; the other decisions (mask
+    thresholds, the sign of G) are taken by identical float32 operations on both sides."""
+    P0 = Ps[0]
+    S, widths = len(Ps), P0.widths
+    NT = sum(widths)
+    NH, n0 = NT - widths[0], widths[0]
+    lo = np.stack([np.concatenate(P.lo) for P in Ps]).astype(np.float32)
+    hi = np.stack([np.concatenate(P.hi) for P in Ps]).astype(np.float32)
+    offs = np.cumsum([0] + widths)
+    for trial in range(20):
+        rng = synth.SplitMix64(seed + 1000 * trial)
+        u = lambda n: rng.uniform(n).astype(np.float32)
+        x = (lo + u(S * NT).reshape(S, NT) * (hi - lo)).astype(np.float32)
+        x = np.minimum(np.maximum(x, lo), hi)
+        z = u(S * NH).reshape(S, NH)
+        alpha = (u(S * NH) * 0.3).reshape(S, NH)
+        Sb = (u(S * NH) * 0.5).reshape(S, NH)
+        G = ((u(S * NH) - 0.5) * 2).reshape(S, NH)
+        C = ((u(S * NH) - 0.5) * 0.2).reshape(S, NH)
+        Pst = ((u(S * NT) - 0.5) * 0.5).reshape(S, NT)
+        Pst[:, NT - widths[-1]:] = 0
+        mua = (u(S * NH) * 0.3 + 0.01).reshape(S, NH)
+        mub = (u(S * NH) * 0.5 + 0.01).reshape(S, NH)
+        sps = []
+        for s, P in enumerate(Ps):
+            hid = lambda v: [None] + split_hidden(v[s].astype(np.float64), widths)[1:]
+            Pk = [None] + [Pst[s, offs[k - 1]:offs[k]].astype(np.float64) for k in range(1, P.n)]
+            xs = [x[s, offs[k]:offs[k + 1]].astype(np.float64) for k in range(P.n)]
+            sps.append(SPm.SaddlePoint.from_state(P, AS.Options(), hid(alpha), hid(Sb), Pk, hid(G), hid(C),
+                                                  hid(mua), hid(mub), xs, hid(z), t))
+        if min(sp.decision_margin(sums_only=True) for sp in sps) > 2e-6:
+            stats = np.zeros((4, S, NT), np.float32)
+            stats[0, :, n0:], stats[1, :, n0:], stats[2, :, n0:], stats[3] = Sb, G, C, Pst
+            return sps, dict(x=x, z=z, stats=stats, caps=np.stack([mua, mub]), alpha=alpha)
+    raise AssertionError("no well-separated state found")
+
+
+def _install_sp_state(ctx, st, t):
+    ctx.set_state(binding.ST_ITER, np.array([0, t, 1], np.int32))
+    ctx.set_state(binding.ST_SP_X, st["x"])
+    ctx.set_state(binding.ST_SP_Z, st["z"])
+    ctx.set_state(binding.ST_SP_STATS, st["stats"])
+    ctx.set_state(binding.ST_SP_CAPS, st["caps"])
+    ctx.set_state(binding.ST_ALPHA, st["alpha"])
+
+
+@pytest.mark.parametrize("name,S,t", [("mlp_tiny", 1, 0), ("small_conv", 3, 4), ("mlp_5_7_6_3", 4, 7),
+                                      ("small_conv", 2, 11)])
+def test_saddle_point_one_iteration_lockstep(name, S, t):
+    """One Saddle Point iteration (Alg. 2) from a random iterate drawn by the generator: bound,
+    conditional-gradient choices (exact) and every updated quantity (1e-5 relative)."""
+    prob, Ps0 = _problems(name, S)
+    lh, uh = oracle_bounds_f32(Ps0)
+    Ps = nw.problems(prob, bounds=[(split_hidden(lh[s].astype(np.float64), Ps0[0].widths)[1:],
+                                    split_hidden(uh[s].astype(np.float64), Ps0[0].widths)[1:])
+                                   for s in range(S)])
+    ctx = binding.context_for(prob, binding.default_options(graph_chunk=0), bounds=(lh, uh))
+    sps, st = _draw_sp_state(Ps, 50 + t, t)
+    _install_sp_state(ctx, st, t)
+    gb = ctx.bound()
+    for s, sp in enumerate(sps):
+        assert gb[s] == pytest.approx(sp.evaluate()[0], abs=1e-5, rel=1e-5)
+    ctx.sp_step(1)
+    it = ctx.get_state(binding.ST_ITER, np.int32)
+    assert it[1] == t + 1 and it[2] == 1
+    sel = ctx.get_state(binding.ST_SP_SEL, np.uint8).reshape(S, -1)
+    x = ctx.get_state(binding.ST_SP_X).reshape(S, -1)
+    z = ctx.get_state(binding.ST_SP_Z).reshape(S, -1)
+    al = ctx.get_state(binding.ST_ALPHA).reshape(S, -1)
+    stats = ctx.get_state(binding.ST_SP_STATS).reshape(4, S, -1)
+    n0 = ctx.widths[0]
+    for s, sp in enumerate(sps):
+        sp.step(1)
+        np.testing.assert_array_equal(sel[s], hidden_concat(sp.last_sel).astype(np.uint8))
+        tol = dict(rtol=1e-5, atol=1e-6)
+        np.testing.assert_allclose(x[s], np.concatenate(sp.x), **tol)
+        np.testing.assert_allclose(z[s], hidden_concat(sp.z), **tol)
+        np.testing.assert_allclose(al[s], hidden_concat(sp.alpha), **tol)
+        np.testing.assert_allclose(stats[0, s, n0:], hidden_concat(sp.Sb), **tol)
+        np.testing.assert_allclose(stats[1, s, n0:], hidden_concat(sp.G), **tol)
+        np.testing.assert_allclose(stats[2, s, n0:], hidden_concat(sp.C), **tol)
+        np.testing.assert_allclose(stats[3, s, :-ctx.widths[-1]],
+                                   np.concatenate([sp.Pst[k] for k in range(1, sp.P.n)]), **tol)
+
+
+@pytest.mark.parametrize("name,S", [("mlp_tiny", 1), ("small_conv", 3), ("mlp_5_7_6_3", 3)])
+def test_saddle_point_conversion_from_active_set_state(name, S):
+    """Sufficient statistics (eq. 10), price caps (eq. 16) and the closed-form starting primal
+    computed from an Active Set state drawn by the generator."""
+    prob, Ps0 = _problems(name, S)
+    lh, uh = oracle_bounds_f32(Ps0)
+    Ps = nw.problems(prob, bounds=[(split_hidden(lh[s].astype(np.float64), Ps0[0].widths)[1:],
+                                    split_hidden(uh[s].astype(np.float64), Ps0[0].widths)[1:])
+                                   for s in range(S)])
+    kw = dict(bigm_iters=2, as_iters=30, omega=3, max_cuts=4, sp_init_steps=0)
+    ctx = binding.context_for(prob, binding.default_options(graph_chunk=0, **kw), bounds=(lh, uh))
+    solvers = draw_state(Ps, ctx, kw, it=9, nslots=4, seed=21)
+    ctx.sp_step(0)
+    stats = ctx.get_state(binding.ST_SP_STATS).reshape(4, S, -1)
+    caps = ctx.get_state(binding.ST_SP_CAPS).reshape(2, S, -1)
+    x = ctx.get_state(binding.ST_SP_X).reshape(S, -1)
+    z = ctx.get_state(binding.ST_SP_Z).reshape(S, -1)
+    n0 = ctx.widths[0]
+    for s, sv in enumerate(solvers):
+        sp = SPm.SaddlePoint(sv.P, AS.Options(**kw), sv.st)
+        tol = dict(rtol=1e-5, atol=1e-6)
+        np.testing.assert_allclose(stats[0, s, n0:], hidden_concat(sp.Sb), **tol)
+        np.testing.assert_allclose(stats[1, s, n0:], hidden_concat(sp.G), **tol)
+        np.testing.assert_allclose(stats[2, s, n0:], hidden_concat(sp.C), **tol)
+        np.testing.assert_allclose(stats[3, s, :-ctx.widths[-1]],
+                                   np.concatenate([sp.Pst[k] for k in range(1, sp.P.n)]), **tol)
+        np.testing.assert_allclose(caps[0, s], hidden_concat(sp.mu_a), **tol)
+        np.testing.assert_allclose(caps[1, s], hidden_concat(sp.mu_b), **tol)
+        f = sp.coefficients()
+        decided = np.concatenate([np.abs(fk) > 1e-5 for fk in f])
+        np.testing.assert_array_equal(x[s][decided], np.concatenate(sp.x)[decided].astype(np.float32))
+        np.testing.assert_array_equal(z[s], hidden_concat(sp.z).astype(np.float32))
+
+
+@pytest.mark.parametrize("name,S", [("mlp_tiny", 1), ("small_conv", 2), ("mlp_3_4_4_1", 2)])
+def test_free_running_saddle_point_tracks_oracle_until_a_tie(name, S):
+    """Big-M initialisation, conversion, primal initialisation and SP iterations on both sides:
+    bounds agree to 1e-4 until the oracle meets a decision within 1e-3 of a tie; every GPU bound
+    stays a valid lower bound (below the sampled minimum of the network output)."""
+    prob, Ps = _problems(name, S)
+    kw = dict(bigm_iters=40, as_iters=0, sp_init_steps=20)
+    ctx = binding.context_for(prob, binding.default_options(graph_chunk=0, **kw))
+    ctx.as_step(40)
+    refs = [AS.ActiveSet(P, AS.Options(**kw)).step(40) for P in Ps]
+    ctx.sp_step(0)
+    sps = [SPm.SaddlePoint(r.P, r.opt, r.st) for r in refs]
+    live = [True] * S
+    xg = ctx.get_state(binding.ST_SP_X).reshape(S, -1)
+    for s, sp in enumerate(sps):
+        if np.abs(xg[s] - np.concatenate(sp.x)).max() > 1e-4:
+            live[s] = False   # primal initialisation met a tie (checked exactly in the lockstep)
+    mins = [sample_min_output(P, 5000) for P in Ps]
+    for t in range(30):
+        margins = [sp.decision_margin() for sp in sps]
+        ctx.sp_step(1)
+        gb = ctx.bound()
+        for s, sp in enumerate(sps):
+            assert gb[s] <= mins[s] + 1e-6
+            if not live[s]:
+                continue
+            sp.step(1)
+            ob = sp.evaluate()[0]
+            if abs(gb[s] - ob) > 1e-4:
+                assert margins[s] < 1e-3, f"divergence at SP iteration {t} without a near-tie ({margins[s]})"
+                live[s] = False
+
+
+@pytest.mark.parametrize("name,S", [("mlp_5_7_6_3", 3), ("small_conv", 2)])
+def test_bound_backward_matches_envelope_gradient(name, S):
+    prob, Ps0 = _problems(name, S)
+    lh, uh = oracle_bounds_f32(Ps0)
+    Ps = nw.problems(prob, bounds=[(split_hidden(lh[s].astype(np.float64), Ps0[0].widths)[1:],
+                                    split_hidden(uh[s].astype(np.float64), Ps0[0].widths)[1:])
+                                   for s in range(S)])
+    kw = dict(bigm_iters=2, as_iters=30, omega=3, max_cuts=4)
+    ctx = binding.context_for(prob, binding.default_options(graph_chunk=0, **kw), bounds=(lh, uh))
+    solvers = draw_state(Ps, ctx, kw, it=9, nslots=4, seed=7)
+    rng = synth.SplitMix64(3)
+    gb = rng.uniform(S) + 0.5
+    net = prob["net"]
+    dW = [np.zeros_like(L["W"]) for L in net]
+    db = [np.zeros_like(L["b"]) for L in net]
+    dlo = np.zeros_like(prob["lo"])
+    dhi = np.zeros_like(prob["hi"])
+    ctx.backward(gb, dW, db, dlo, dhi)
+    refW = [np.zeros(L["W"].shape) for L in net]
+    refb = [np.zeros(L["b"].shape) for L in net]
+    for s, sv in enumerate(solvers):
+        g = ev.envelope_gradient(sv.P, sv.st)
+        for k, L in enumerate(net[:-1], start=1):
+            if L["kind"] == "linear":
+                refW[k - 1] += gb[s] * g["dW"][k]
+            else:
+                refW[k - 1] += gb[s] * ev.filter_gradient(g["dW"][k], sv.P.taps[k], L["W"].shape)
+            refb[k - 1] += gb[s] * ev.bias_gradient(g["db"][k], L)
+        refW[-1] += gb[s] * np.outer(prob["C"][s], g["dW"][sv.P.n][0])
+        refb[-1] += gb[s] * prob["C"][s]
+        np.testing.assert_allclose(dlo[s], gb[s] * g["dlo0"], rtol=1e-4, atol=1e-5)
+        np.testing.assert_allclose(dhi[s], gb[s] * g["dhi0"], rtol=1e-4, atol=1e-5)
+    for k in range(len(net)):
+        np.testing.assert_allclose(dW[k], refW[k], rtol=1e-4, atol=1e-5)
+        np.testing.assert_allclose(db[k], refb[k], rtol=1e-4, atol=1e-5)
+
+
+def test_invalid_arguments_are_rejected_before_any_kernel():
+    prob = synth.problem("mlp_tiny", seed=0)
+    bad = dict(prob)
+    bad["lo"] = prob["hi"] + 1.0
+    with pytest.raises(binding.CBError) as e:
+        binding.context_for(bad)
+    assert e.value.code == binding.AS_ERR_ARG
+    with pytest.raises(binding.CBError) as e:
+        binding.context_for(prob, binding.default_options(max_cuts=9))
+    assert e.value.code == binding.AS_ERR_ARG
+    ctx = binding.context_for(prob, binding.default_options(bigm_iters=2, as_iters=2))
+    ctx.as_step(2)
+    ctx.sp_step(1)
+    with pytest.raises(binding.CBError) as e:
+        ctx.as_step(1)
+    assert e.value.code == binding.AS_ERR_STATE
+
+
+def test_runs_are_deterministic():
+    prob = synth.problem("small_conv", S=3, seed=2)
+    out = []
+    for _ in range(2):
+        ctx = binding.context_for(prob, binding.default_options(bigm_iters=10, as_iters=30, omega=8, max_cuts=4))
+        ctx.as_step(40)
+        out.append((ctx.bound(), ctx.get_state(binding.ST_SLOT_BETA).tobytes()))
+    assert (out[0][0] == out[1][0]).all() and out[0][1] == out[1][1]
