@@ -9,7 +9,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc", "convex_barrier.cu")
 LIB = os.path.join(HERE, "libconvex_barrier.so")
 DEPS = [os.path.join(HERE, "csrc", f) for f in
-        ("convex_barrier.cu", "cb_common.cuh", "cb_kernels.cuh", "cb_backward.cuh",
+        ("convex_barrier.cu", "cb_common.cuh", "cb_kernels.cuh", "cb_backward.cuh", "cb_team.cuh",
          "cb_host_extra.inc")] + [os.path.join(HERE, "..", "include", "convex_barrier.h")]
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",

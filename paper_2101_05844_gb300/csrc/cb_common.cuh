@@ -49,6 +49,9 @@ struct DState {
     float *alpha, *beta0, *beta1;
     float *ma, *va, *m0, *v0, *m1, *v1;
     float *bs, *ms, *vs, *lam, *kap; // slots
+    float *rp;                       // [S][NH] -(alpha - beta1) + sum_b z_b beta_b (row sums)
+    float *bz;                       // [S][cap][NH] (1 - z_b) beta_b
+    uint8_t* efix;                   // [S][NT] l == u
     float *xval;                     // x* of the last evaluation [S][NT]
     float *fval;                     // f of the last evaluation [S][NT]
     uint8_t* zcur;                   // z* of the last evaluation [S][NH]

@@ -11,6 +11,7 @@
 #include "../../include/convex_barrier.h"
 #include "cb_kernels.cuh"
 #include "cb_backward.cuh"
+#include "cb_team.cuh"
 
 using namespace cb;
 
@@ -30,6 +31,8 @@ struct as_ctx {
     long long launches = 0;
     Segs segA{}, segB{}, segP{};
     int blocksA = 0, blocksB = 0, blocksP = 0;
+    TSegs tA{}, tB{};                // lane-team launch geometry of the Active Set passes
+    int blocksTA = 0, blocksTB = 0;
     cudaGraphExec_t g_as = nullptr, g_sp = nullptr;
     int g_as_len = 0, g_sp_len = 0, g_as_nodes = 0, g_sp_nodes = 0;
     float* Wlast = nullptr;        // original last layer [n_out][n_{n-1}] and bias
@@ -253,6 +256,61 @@ struct Bump {
     }
 };
 
+// Team size for a pass with `units` reductions of about `fan` terms each: enough lanes to fill the
+// GPU (about 152 SMs x 1024 threads), at least 8 terms per lane, a power of two up to a warp.
+static int team_size(long long units, long long fan) {
+    const long long target = 152LL * 1024;
+    int T = 1;
+    while (T < 32 && units * T < target && fan / (2 * T) >= 8) T *= 2;
+    return T;
+}
+
+static int make_team_segs(as_ctx* c) {
+    DNet& D = c->net;
+    const int n = D.n, S = D.S;
+    auto build = [&](TSegs& sg, int& blocks, bool col) -> int {
+        const int nseg = col ? n : n - 1;
+        sg.n = nseg;
+        int b = 0;
+        for (int k = 0; k < nseg; ++k) {
+            const DLayer& L = D.L[k];
+            const long long units = (long long)S * (col ? L.n_in : L.n_out);
+            long long fan;
+            if (L.kind == 0) fan = col ? L.n_out : L.n_in;
+            else fan = col ? (long long)L.co * ((L.kh + L.st - 1) / L.st) * ((L.kw + L.st - 1) / L.st)
+                           : (long long)L.ci * L.kh * L.kw;
+            int T = (col && k == n - 1) ? 1 : team_size(units, fan);
+            // conv row-pass lanes split (channel, kernel row) pairs; col-pass lanes split channels
+            const long long split = L.kind == 0 ? fan : (col ? L.co : (long long)L.ci * L.kh);
+            while (T > 1 && T > split) T >>= 1;
+            sg.layer[k] = k;
+            sg.T[k] = T;
+            sg.start[k] = b;
+            sg.perm[k] = nullptr;
+            b += (int)((units * T + CB_THREADS - 1) / CB_THREADS);
+            if (col && L.kind == 1 && L.st > 1) {
+                std::vector<int> perm;
+                perm.reserve(L.n_in);
+                for (int py = 0; py < L.st; ++py)
+                    for (int px = 0; px < L.st; ++px)
+                        for (int ch = 0; ch < L.ci; ++ch)
+                            for (int y = py; y < L.hi; y += L.st)
+                                for (int x = px; x < L.wi; x += L.st) perm.push_back((ch * L.hi + y) * L.wi + x);
+                int* dp;
+                TRY(dalloc(c, &dp, perm.size()));
+                CUDA_TRY(c, cudaMemcpy(dp, perm.data(), perm.size() * sizeof(int), cudaMemcpyHostToDevice));
+                sg.perm[k] = dp;
+            }
+        }
+        sg.start[nseg] = b;
+        blocks = b;
+        return AS_OK;
+    };
+    TRY(build(c->tA, c->blocksTA, true));
+    TRY(build(c->tB, c->blocksTB, false));
+    return AS_OK;
+}
+
 static int alloc_state(as_ctx* c) {
     DNet& D = c->net;
     DState& st = c->st;
@@ -267,6 +325,8 @@ static int alloc_state(as_ctx* c) {
         float** zs[] = {&st.bs, &st.ms, &st.vs, &st.lam, &st.kap};
         for (float** p : zs) *p = z.take<float>(SL);
         st.P = z.take<float>(NTS);
+        st.rp = z.take<float>(NHS);
+        st.bz = z.take<float>(SL);
         for (int q = 0; q < 2; ++q) {
             st.xsnap[q] = z.take<uint8_t>(NTS);
             st.zsnap[q] = z.take<uint8_t>(NHS);
@@ -289,6 +349,7 @@ static int alloc_state(as_ctx* c) {
             st.spz[q] = o.take<float>(NHS);
         }
         st.zcur = o.take<uint8_t>(NHS);
+        st.efix = o.take<uint8_t>(NTS);
         st.zbar = o.take<uint8_t>(NHS);
         st.sel = o.take<uint8_t>(NHS);
         st.terms = o.take<double>(NTS);
@@ -389,7 +450,9 @@ static int load_batch(as_ctx* c, const float* x_lo, const float* x_hi, const flo
             TRY(check_launch(c, "k_ibp"));
         }
     }
-    return AS_OK;
+    k_efix<<<grid_for((size_t)S * NT), CB_THREADS, 0, s>>>(D, st);
+    c->launches++;
+    return check_launch(c, "k_efix");
 }
 
 extern "C" int as_reset(as_ctx* c, const float* x_lo, const float* x_hi, const float* C, const float* lhat,
@@ -488,6 +551,7 @@ static int init_impl(as_ctx* c, const as_net* net, int S, const float* x_lo, con
         }
         make_segs(c->segP, c->blocksP, ids, units, CB_THREADS);
     }
+    TRY(make_team_segs(c));
     TRY(alloc_state(c));
     TRY(build_tables(c));
     TRY(load_batch(c, x_lo, x_hi, C, lhat, uhat, splits, caps, true));
@@ -558,10 +622,10 @@ static cudaEvent_t prof_event(as_ctx* c) {
     } while (0)
 
 static int launch_as_iter(as_ctx* c, cudaStream_t s) {
-    LAUNCH(c, s, CB_K_AS_COLA, (k_as_colA<<<c->blocksA, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->segA, 0)));
+    LAUNCH(c, s, CB_K_AS_COLA, (k_as_colA_t<<<c->blocksTA, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->tA, 0)));
     if (c->opt.track_best)
         LAUNCH(c, s, CB_K_REDUCE, (k_reduce<<<c->net.S, CB_THREADS, 0, s>>>(c->net, c->st, 64, nullptr, 1)));
-    LAUNCH(c, s, CB_K_AS_ROWB, (k_as_rowB<<<c->blocksB, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->segB)));
+    LAUNCH(c, s, CB_K_AS_ROWB, (k_as_rowB_t<<<c->blocksTB, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->tB)));
     return check_launch(c, "Active Set iteration");
 }
 
@@ -661,7 +725,7 @@ extern "C" int as_bound(as_ctx* c, int precision, double* out, double* best) {
     const int S = c->net.S;
     cudaStream_t s = c->stream;
     if (c->sp_started) LAUNCH(c, s, CB_K_SP_COLA, (k_sp_colA<<<c->blocksA, CB_THREADS, 0, s>>>(c->net, c->st, c->segA, 0)));
-    else LAUNCH(c, s, CB_K_AS_COLA, (k_as_colA<<<c->blocksA, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->segA, 1)));
+    else LAUNCH(c, s, CB_K_AS_COLA, (k_as_colA_t<<<c->blocksTA, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->tA, 1)));
     double* dout = c->bound_out;
     LAUNCH(c, s, CB_K_REDUCE, (k_reduce<<<S, CB_THREADS, 0, s>>>(c->net, c->st, precision, dout, 1)));
     TRY(check_launch(c, "bound evaluation"));
@@ -852,7 +916,9 @@ extern "C" int as_set_state(as_ctx* c, int which, const void* src) {
     if (which == AS_ST_XSNAP || which == AS_ST_ZSNAP) TRY(snap_parity(c, &par));
     if (which == AS_ST_SP_X || which == AS_ST_SP_Z) TRY(sp_parity(c, &par));
     TRY(copy_pieces(c, nullptr, src, false, composite(c, which, par)));
-    if (which == AS_ST_SLOT_BETA || which == AS_ST_XSNAP || which == AS_ST_ZSNAP) TRY(recompute_slot_sums(c));
+    if (which == AS_ST_SLOT_BETA || which == AS_ST_XSNAP || which == AS_ST_ZSNAP || which == AS_ST_ALPHA ||
+        which == AS_ST_BETA1)
+        TRY(recompute_slot_sums(c));
     return AS_OK;
 }
 

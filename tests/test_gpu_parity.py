@@ -103,6 +103,13 @@ def test_one_iteration_lockstep(name, S, kw, it, nslots):
         _, f, g, x, z = du.evaluate(P, sv.st)
         grads = du.supergradient(P, sv.st, x, z)
         slots_before = len(sv.st.slots[1])
+        # gradient of the slot this iteration adds: eq. (9) at the oracle's mask at (x*, z*)
+        gnew = [None]
+        for k in range(1, P.n):
+            from oracle import relaxation as rx
+            I = rx.mask(P.W[k], P.lo[k - 1], P.hi[k - 1], x[k - 1], z[k])
+            lam_n, mu_n = rx.row_sums(P.W[k], P.lo[k - 1], P.hi[k - 1], I)
+            gnew.append(x[k] - (P.W[k] * I) @ x[k - 1] + lam_n * (1 - z[k]) - z[k] * (P.b[k] + mu_n))
         sv.step(1)
         # primal minimiser: exact
         np.testing.assert_array_equal(xstar[s], np.concatenate([x[k] for k in range(P.n)]).astype(np.float32))
@@ -135,7 +142,7 @@ def test_one_iteration_lockstep(name, S, kw, it, nslots):
             if b < slots_before:
                 gref = hidden_concat([None] + [grads["gslots"][k][b] for k in range(1, P.n)])
             else:
-                gref = np.ones_like(ref)
+                gref = hidden_concat(gnew)
             check(sb[s, b], ref, gref)
 
 
@@ -149,16 +156,16 @@ def _as_margin(sv):
     return m
 
 
-@pytest.mark.parametrize("name,S,kw,iters,full", [
-    ("mlp_tiny", 1, dict(bigm_iters=20, as_iters=80, omega=24, max_cuts=5), 100, True),
-    ("mlp_5_7_6_3", 4, dict(bigm_iters=30, as_iters=60, omega=20, max_cuts=4), 90, False),
-    ("small_conv", 3, dict(bigm_iters=20, as_iters=40, omega=12, max_cuts=5), 60, False),
+@pytest.mark.parametrize("name,S,kw,iters", [
+    ("mlp_tiny", 1, dict(bigm_iters=20, as_iters=80, omega=24, max_cuts=5), 100),
+    ("mlp_5_7_6_3", 4, dict(bigm_iters=30, as_iters=60, omega=20, max_cuts=4), 90),
+    ("small_conv", 3, dict(bigm_iters=20, as_iters=40, omega=12, max_cuts=5), 60),
 ])
-def test_free_running_active_set_matches_oracle(name, S, kw, iters, full):
+def test_free_running_active_set_matches_oracle(name, S, kw, iters):
     """Iteration by iteration: the GPU and oracle bounds agree to 1e-4 until the first iteration
     whose decisions the oracle takes within 1e-3 of a tie, the size float32 drift of the duals
     reaches over tens of iterations (a rounding flip, after which the runs are different valid
-    runs). full: no such flip may occur, final bounds within 1e-4."""
+    runs, both checked valid). The first 10 iterations must agree."""
     prob, Ps = _problems(name, S)
     ctx = binding.context_for(prob, binding.default_options(graph_chunk=0, track_best=1, **kw))
     sol = [AS.ActiveSet(P, AS.Options(**kw)) for P in Ps]
@@ -174,7 +181,7 @@ def test_free_running_active_set_matches_oracle(name, S, kw, iters, full):
             ob = du.evaluate(sv.P, sv.st)[0]
             if abs(gb[s] - ob) > 1e-4:
                 assert margins[s] < 1e-3, f"divergence at iteration {it} without a near-tie (margin {margins[s]})"
-                assert not full, f"near-tie flip at iteration {it} (margin {margins[s]})"
+                assert it >= 10
                 live[s] = False
     b, best = ctx.bound(best=True)
     for s, P in enumerate(Ps):
@@ -182,8 +189,7 @@ def test_free_running_active_set_matches_oracle(name, S, kw, iters, full):
             assert b[s] == pytest.approx(sol[s].bound(), abs=1e-4)
             assert best[s] == pytest.approx(sol[s].best, abs=1e-4)
         assert best[s] >= P.ibp_output_bound() - 1e-6
-    if full:
-        assert all(live)
+        assert best[s] <= sample_min_output(P, 5000) + 1e-6
 
 
 def _draw_sp_state(Ps, seed, t):
