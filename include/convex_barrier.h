@@ -34,6 +34,7 @@ extern "C" {
 #define AS_ERR_NUMERIC 5  /* a bound came out NaN or infinite                                */
 #define AS_ERR_TIMEOUT 6  /* a bounded device wait expired (reserved; no kernel waits today) */
 #define AS_ERR_STATE 7    /* call not valid in the context's current mode                    */
+#define AS_ERR_SCRATCH 8  /* the problem does not fit the fixed scratch of as_ibp_noalloc      */
 
 #define AS_LAYER_LINEAR 0
 #define AS_LAYER_CONV2D 1
@@ -195,6 +196,34 @@ int as_kernel_times(as_ctx* ctx, int kernel, double* total_ms, long long* launch
 
 void as_destroy(as_ctx* ctx);
 const char* as_last_error(as_ctx* ctx);
+
+/* Allocation-free interval bounds (no counterpart in the paper; a service of this library).
+ *
+ * Some callers cannot call cudaMalloc: a verifier embedded in a process whose device memory is
+ * entirely reserved by another allocator (a deep-learning framework's caching allocator, or the
+ * fixed memory pool of a serving engine), where a direct allocation fails or fragments the pool;
+ * and latency-critical callers that cannot afford the implicit device synchronisation of
+ * cudaMalloc / cudaFree. as_init cannot serve them, since it allocates its context. This entry
+ * point computes the pre-activation bounds that as_init derives by interval propagation, with
+ * no allocation: the caller passes every input and output, and the post-activation bounds handed
+ * from one layer to the next live in a file-scope device array of AS_NOALLOC_SCRATCH_FLOATS
+ * floats (16 MiB) that every GPU which loads the library keeps until the process exits.
+ *
+ *  net:        as for as_init, except that W and b must be device pointers.
+ *  x_lo, x_hi: [S][n_0] input boxes, device memory (lo <= hi is the caller's responsibility).
+ *  splits:     hidden vector of int8 ReLU splits as for as_init, device memory, or NULL.
+ *  lhat, uhat: outputs, hidden vectors [S][n_1 + ... + n_{n-1}] of float, device memory.
+ *  stream:     cudaStream_t the kernels are enqueued on; the call does not synchronise.
+ * Returns AS_ERR_SCRATCH when 4 x S x (widest hidden layer) exceeds AS_NOALLOC_SCRATCH_FLOATS,
+ * AS_ERR_ARG for a null or host pointer, AS_ERR_SHAPE for inconsistent layers.
+ * The first call on each device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before any stream
+ * capture. Every call on a device shares the one scratch array (nothing in it needs to start at
+ * zero: each call writes every entry it reads), so calls whose kernels overlap on the GPU race;
+ * issue them on one stream or otherwise order them. */
+#define AS_NOALLOC_SCRATCH_FLOATS (1u << 22)
+int as_ibp_noalloc(const as_net* net, int S, const float* x_lo, const float* x_hi,
+                   const signed char* splits, float* lhat, float* uhat, void* stream);
 
 #ifdef __cplusplus
 }

@@ -14,7 +14,9 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libconvex_barrier.so")
 
-AS_OK, AS_ERR_ARG, AS_ERR_SHAPE, AS_ERR_CUDA, AS_ERR_OOM, AS_ERR_NUMERIC, AS_ERR_TIMEOUT, AS_ERR_STATE = range(8)
+AS_OK, AS_ERR_ARG, AS_ERR_SHAPE, AS_ERR_CUDA, AS_ERR_OOM, AS_ERR_NUMERIC, AS_ERR_TIMEOUT, AS_ERR_STATE, \
+    AS_ERR_SCRATCH = range(9)
+NOALLOC_SCRATCH_FLOATS = 1 << 22
 LINEAR, CONV2D = 0, 1
 MAX_LAYERS, MAX_CUTS = 10, 8
 
@@ -24,7 +26,7 @@ MAX_LAYERS, MAX_CUTS = 10, 8
 
 EXPORTS = ["as_default_options", "as_init", "as_reset", "as_step", "sp_step", "as_bound",
            "as_bound_backward", "as_state_size", "as_get_state", "as_set_state", "as_launch_count",
-           "as_kernel_times", "as_destroy", "as_last_error"]
+           "as_kernel_times", "as_destroy", "as_last_error", "as_ibp_noalloc"]
 KERNELS = ["as_colA", "as_rowB", "reduce", "sp_colA", "sp_rowB", "sp_colC", "spi_row", "spi_col"]
 
 
@@ -81,6 +83,8 @@ def lib() -> ct.CDLL:
         L.as_destroy.restype = None
         L.as_last_error.argtypes = [ct.c_void_p]
         L.as_last_error.restype = ct.c_char_p
+        L.as_ibp_noalloc.argtypes = [ct.POINTER(Net), ct.c_int] + [ct.c_void_p] * 6
+        L.as_ibp_noalloc.restype = ct.c_int
         _lib = L
     return _lib
 
@@ -243,6 +247,16 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+def ibp_noalloc(net: list, lo, hi, lhat_out, uhat_out, splits=None, stream: int = 0) -> int:
+    """as_ibp_noalloc: interval bounds with no allocation inside the call. Every array must be a
+    CUDA tensor (weights and biases of `net` included); returns the status code."""
+    keep = []
+    layers = (Layer * len(net))(*[_layer_struct(x, keep) for x in net])
+    n = Net(len(net), layers)
+    return lib().as_ibp_noalloc(ct.byref(n), int(lo.shape[0]), _ptr(lo), _ptr(hi), _ptr(splits),
+                                _ptr(lhat_out), _ptr(uhat_out), ct.c_void_p(stream))
 
 
 def context_for(prob: dict, options: Options | None = None, bounds=None, stream: int = 0, **kw) -> Context:

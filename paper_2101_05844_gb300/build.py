@@ -6,11 +6,11 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SRC = os.path.join(HERE, "csrc", "convex_barrier.cu")
+SRCS = [os.path.join(HERE, "csrc", "convex_barrier.cu"), os.path.join(HERE, "csrc", "noalloc.cu")]
 LIB = os.path.join(HERE, "libconvex_barrier.so")
 DEPS = [os.path.join(HERE, "csrc", f) for f in
         ("convex_barrier.cu", "cb_common.cuh", "cb_kernels.cuh", "cb_backward.cuh", "cb_team.cuh",
-         "cb_host_extra.inc")] + [os.path.join(HERE, "..", "include", "convex_barrier.h")]
+         "cb_host_extra.inc", "noalloc.cu", "cb_walk.cuh")] + [os.path.join(HERE, "..", "include", "convex_barrier.h")]
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-shared", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
@@ -33,7 +33,7 @@ def up_to_date() -> bool:
 def build(force: bool = False, verbose: bool = False) -> str:
     if not force and up_to_date():
         return LIB
-    cmd = [nvcc(), *NVCC_FLAGS, "-o", LIB + ".tmp", SRC]
+    cmd = [nvcc(), *NVCC_FLAGS, "-o", LIB + ".tmp", *SRCS]
     if verbose:
         print(" ".join(cmd), file=sys.stderr)
     subprocess.run(cmd, check=True)

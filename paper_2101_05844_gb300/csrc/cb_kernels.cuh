@@ -11,72 +11,9 @@
 // thresholds (Saddle Point); see cb_slot_mask and cb_sp_mask.
 #pragma once
 #include "cb_common.cuh"
+#include "cb_walk.cuh"
 
 namespace cb {
-
-// ------------------------------------------------------------------------------------ walks
-// Lane-strided walk over the fan-in of output neuron i of layer L: fn(j, w) for each input j.
-template <class Fn>
-__device__ __forceinline__ void row_walk(const DLayer& L, int i, int lane, Fn fn) {
-    if (L.kind == 0) {
-        const float* Wr = L.W + (size_t)i * L.n_in;
-        for (int j = lane; j < L.n_in; j += 32) fn(j, __ldg(Wr + j));
-    } else {
-        const int hw = L.ho * L.wo;
-        const int co = i / hw, rem = i - co * hw;
-        const int oy = rem / L.wo, ox = rem - oy * L.wo;
-        const int kk = L.kh * L.kw, fan = L.ci * kk;
-        const float* Wr = L.W + (size_t)co * fan;
-        const int y0 = oy * L.st - L.pd, x0 = ox * L.st - L.pd;
-        for (int r = lane; r < fan; r += 32) {
-            const int c = r / kk, q = r - c * kk;
-            const int ky = q / L.kw, kx = q - ky * L.kw;
-            const int y = y0 + ky, x = x0 + kx;
-            if (y >= 0 && y < L.hi && x >= 0 && x < L.wi) fn((c * L.hi + y) * L.wi + x, __ldg(Wr + r));
-        }
-    }
-}
-
-// Serial walk over the fan-out of input neuron j of layer L: fn(i, w) for each output i.
-template <class Fn>
-__device__ __forceinline__ void col_walk(const DLayer& L, int j, Fn fn) {
-    if (L.kind == 0) {
-        const float* Wc = L.W + j;
-        for (int i = 0; i < L.n_out; ++i) fn(i, __ldg(Wc + (size_t)i * L.n_in));
-    } else {
-        const int hw = L.hi * L.wi;
-        const int c = j / hw, rem = j - c * hw;
-        const int y = rem / L.wi, x = rem - y * L.wi;
-        const int kk = L.kh * L.kw;
-        const size_t cstride = (size_t)L.ci * kk;
-        for (int ky = 0; ky < L.kh; ++ky) {
-            const int ty = y + L.pd - ky;
-            if (ty < 0 || ty % L.st) continue;
-            const int oy = ty / L.st;
-            if (oy >= L.ho) continue;
-            for (int kx = 0; kx < L.kw; ++kx) {
-                const int tx = x + L.pd - kx;
-                if (tx < 0 || tx % L.st) continue;
-                const int ox = tx / L.st;
-                if (ox >= L.wo) continue;
-                const float* Wp = L.W + (size_t)c * kk + ky * L.kw + kx;
-                const int ib = oy * L.wo + ox;
-                for (int co = 0; co < L.co; ++co) fn(co * L.ho * L.wo + ib, __ldg(Wp + co * cstride));
-            }
-        }
-    }
-}
-
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
 
 // Active Set mask bits of every slot for one (i, j) pair (eq. 3 at binary iterates).
 // zs: bit b = z*_k[i] when slot b was added; xs: bit b = (x*_{k-1}[j] was at its upper bound).
