@@ -26,6 +26,7 @@ struct DLayer {
 struct DNet {
     int n;                 // affine layers; hidden layers k = 1..n-1
     int S, NT, NH, cap;    // subproblems, all neurons (layers 0..n-1), hidden neurons, max slots
+    int RS;                // floats per Active Set row record (1 + cap rounded up to 4)
     DLayer L[CB_MAXL];
     const float* Wout;     // [S][n_{n-1}] property-folded output row
     const float* bout;     // [S]
@@ -49,8 +50,9 @@ struct DState {
     float *alpha, *beta0, *beta1;
     float *ma, *va, *m0, *v0, *m1, *v1;
     float *bs, *ms, *vs, *lam, *kap; // slots
-    float *rp;                       // [S][NH] -(alpha - beta1) + sum_b z_b beta_b (row sums)
-    float *bz;                       // [S][cap][NH] (1 - z_b) beta_b
+    float *arec;                     // [S][NH][RS] row record: -(alpha - beta1) + sum_b z_b beta_b,
+                                     // then (1 - z_b) beta_b per slot (RS = 1 + cap rounded to 4)
+    float2 *xrec;                    // [S][NT] input record: {x*, snapshot bits | fixed << 8}
     uint8_t* efix;                   // [S][NT] l == u
     float *xval;                     // x* of the last evaluation [S][NT]
     float *fval;                     // f of the last evaluation [S][NT]
@@ -76,6 +78,9 @@ struct DState {
     float *taup, *taun;              // [S][NT] mask thresholds of every input
     uint8_t* sel;                    // [S][NH] selected beta of the conditional gradient (3 = none)
     float *ab, *b0i, *b1i;           // [S][NH] primal-init inner maximisers
+    float* arow;                     // [S][NH] ab - b1i (primal-init row values for the col pass)
+    float4* inrec;                   // [S][NT] per input: {x, tau+, tau-, l} of the current iterate
+    float4* rowrec;                  // [S][NH] per row: {beta_bar on beta_1, on I*, z, 0}
     int* status;                     // device error word
 };
 

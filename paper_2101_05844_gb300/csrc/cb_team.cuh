@@ -9,9 +9,10 @@
 // same branches.
 //
 // The masks of all active-set slots for one (i, j) pair form a bitset (cb_slot_mask). The col pass
-// uses the per-row sums the row pass leaves behind after its Adam step:
+// uses the per-row record the row pass leaves behind after its Adam step (one to three float4):
 //   rp[i]    = -(alpha_i - beta1_i) + sum_b z_b[i] beta_b[i]      (rows whose mask is all ones)
 //   bz[b][i] = (1 - z_b[i]) beta_b[i]
+// and the row pass reads one 8-byte record per input: x* and the snapshot bits with the fixed flag.
 // so that, with p_b = [x at its lower bound] or fixed, q_b = [x at its upper bound] or fixed,
 //   sum_i W_ij (-(alpha - beta1)_i + sum_b I_b(i,j) beta_b[i])
 //     = sum_i W_ij rp[i] + sum_b ( p_b sum_{W_ij > 0} W_ij bz[b][i] + q_b sum_{W_ij < 0} W_ij bz[b][i] ),
@@ -34,6 +35,7 @@ template <class Fn>
 __device__ __forceinline__ void row_walk_team(const DLayer& L, int i, int lane, int T, Fn fn) {
     if (L.kind == 0) {
         const float* Wr = L.W + (size_t)i * L.n_in;
+#pragma unroll 4
         for (int j = lane; j < L.n_in; j += T) fn(j, __ldg(Wr + j));
         return;
     }
@@ -51,6 +53,7 @@ __device__ __forceinline__ void row_walk_team(const DLayer& L, int i, int lane, 
         if (ky >= ky0 && ky < ky1) {
             const float* Wk = Wc + (c * L.kh + ky) * L.kw;
             const int jrow = (c * L.hi + y0 + ky) * L.wi + x0;
+#pragma unroll 4
             for (int kx = kx0; kx < kx1; ++kx) fn(jrow + kx, __ldg(Wk + kx));
         }
         c += cstep;
@@ -66,6 +69,7 @@ template <class Fn>
 __device__ __forceinline__ void col_walk_team(const DLayer& L, int j, int lane, int T, Fn fn) {
     if (L.kind == 0) {
         const float* Wc = L.W + j;
+#pragma unroll 4
         for (int i = lane; i < L.n_out; i += T) fn(i, __ldg(Wc + (size_t)i * L.n_in));
         return;
     }
@@ -107,17 +111,21 @@ __device__ __forceinline__ void as_colA_body(const DNet& net, const DState& st, 
 #pragma unroll
     for (int b = 0; b < NS; ++b) P[b] = Q[b] = 0.f;
     if (valid && k <= net.n - 1) {
-        const size_t rb = (size_t)s * NH + L.h_out;
-        const float* rp = st.rp + rb;
-        const float* bz = st.bz + (size_t)s * cap * NH + L.h_out;
+        const int RS = net.RS;
+        const float* ar = st.arec + ((size_t)s * NH + L.h_out) * RS;
         col_walk_team(L, j, lane, T, [&](int i, float w) {
-            acc += w * rp[i];
+            const float4* r = reinterpret_cast<const float4*>(ar + (size_t)i * RS);
+            float v[12];
+            const float4 r0 = r[0];
+            v[0] = r0.x; v[1] = r0.y; v[2] = r0.z; v[3] = r0.w;
+            if (NS >= 4) { const float4 r1 = r[1]; v[4] = r1.x; v[5] = r1.y; v[6] = r1.z; v[7] = r1.w; }
+            if (NS >= 8) { const float4 r2 = r[2]; v[8] = r2.x; v[9] = r2.y; v[10] = r2.z; v[11] = r2.w; }
+            acc += w * v[0];
             const float wp = fmaxf(w, 0.f), wn = fminf(w, 0.f);
 #pragma unroll
             for (int b = 0; b < NS; ++b) {
-                const float bb = bz[(size_t)b * NH + i];
-                P[b] += wp * bb;
-                Q[b] += wn * bb;
+                P[b] += wp * v[1 + b];
+                Q[b] += wn * v[1 + b];
             }
         });
     }
@@ -180,7 +188,12 @@ __device__ __forceinline__ void as_colA_body(const DNet& net, const DState& st, 
     st.fval[xo] = f;
     term -= (double)f * xv;
     st.terms[xo] = term;
-    if (add_iter) st.xsnap[bo ^ 1][xo] = (uint8_t)(xs | ((add && up) ? (1u << sp.b_new) : 0u));
+    unsigned xs_new = xs;
+    if (add_iter) {
+        xs_new = xs | ((add && up) ? (1u << sp.b_new) : 0u);
+        st.xsnap[bo ^ 1][xo] = (uint8_t)xs_new;
+    }
+    st.xrec[xo] = make_float2(xv, __uint_as_float(xs_new | (fixed ? 0x100u : 0u)));
 }
 
 __device__ __forceinline__ int tseg_of(const TSegs& sg, int blk) {
@@ -236,20 +249,20 @@ __device__ __forceinline__ void as_rowB_body(const DNet& net, const DState& st, 
     for (int b = 0; b < NS; ++b) acc[b] = 0.f;
     if (valid) {
         const size_t ib = (size_t)s * NT + L.in_off;
-        const float* xv = st.xval + ib;
-        const uint8_t* xsn = st.xsnap[bn] + ib;
-        const uint8_t* fx = st.efix + ib;
+        const float2* xr = st.xrec + ib;
         const float* lo = st.lo + ib;
         const float* hi = st.hi + ib;
         // products rounded once and added without contraction: where the mask selects exactly the
         // inputs at their interval end (Lcheck = x), the masked product and lambda of a new slot
         // then cancel exactly in the supergradient, as they do in exact arithmetic
         row_walk_team(L, i, lane, T, [&](int j, float w) {
-            const float wx = __fmul_rn(w, xv[j]);
+            const float2 r = xr[j];
+            const float wx = __fmul_rn(w, r.x);
             acc0 = __fadd_rn(acc0, wx);
             if (NS > 0) {
-                const unsigned xs = xsn[j];
-                const unsigned f = fx[j] ? 0xFFu : 0u;
+                const unsigned fl = __float_as_uint(r.y);
+                const unsigned xs = fl & 0xFFu;
+                const unsigned f = (fl & 0x100u) ? 0xFFu : 0u;
                 const unsigned msk = w > 0.f ? ((~xs) | f) : (w < 0.f ? (xs | f) : 0xFFu);
 #pragma unroll
                 for (int b = 0; b < NS; ++b)
@@ -273,44 +286,71 @@ __device__ __forceinline__ void as_rowB_body(const DNet& net, const DState& st, 
     }
     if (!valid || lane != 0) return;
     const int nsl = min(sp.nadd_before + (sp.b_new >= 0 ? 1 : 0), cap_s);
+    // every load before any store: the state arrays live in one arena and may not be reordered
     const float bi = L.b[i];
-    const float xhat = acc0 + bi;
     const float x = st.xval[(size_t)s * NT + L.out_off + i];
     const float z = st.zcur[h] ? 1.f : 0.f;
+    const float uh = st.uhat[h], lh = st.lhat[h];
+    float al = st.alpha[h], ma = st.ma[h], va = st.va[h];
+    float b0 = st.beta0[h], m0 = st.m0[h], v0 = st.v0[h];
+    float b1 = st.beta1[h], m1 = st.m1[h], v1 = st.v1[h];
+    const size_t hs0 = (size_t)s * cap * NH + L.h_out + i;
+    float sb[NS > 0 ? NS : 1], sm[NS > 0 ? NS : 1], sv[NS > 0 ? NS : 1], sl[NS > 0 ? NS : 1], sk[NS > 0 ? NS : 1];
+#pragma unroll
+    for (int b = 0; b < NS; ++b) {
+        const size_t hs = hs0 + (size_t)b * NH;
+        const bool live = b < nsl;
+        sb[b] = live ? st.bs[hs] : 0.f;
+        sm[b] = live ? st.ms[hs] : 0.f;
+        sv[b] = live ? st.vs[hs] : 0.f;
+        sl[b] = live ? st.lam[hs] : 0.f;
+        sk[b] = live ? st.kap[hs] : 0.f;
+    }
+    const float xhat = acc0 + bi;
     const int step = it + 1;
     float bc1 = bias_corr(st.bc1_tab, sc.ntab, step, sc.b1);
     float bc2 = bias_corr(st.bc2_tab, sc.ntab, step, sc.b2);
-    adam(st.alpha[h], st.ma[h], st.va[h], xhat - x, sp.lr, bc1, bc2, sc);
-    adam(st.beta0[h], st.m0[h], st.v0[h], x - z * st.uhat[h], sp.lr, bc1, bc2, sc);
-    adam(st.beta1[h], st.m1[h], st.v1[h], x - xhat + (1.f - z) * st.lhat[h], sp.lr, bc1, bc2, sc);
-    float rsum = -(st.alpha[h] - st.beta1[h]);
-    const size_t hs0 = (size_t)s * cap * NH + L.h_out + i;
+    adam(al, ma, va, xhat - x, sp.lr, bc1, bc2, sc);
+    adam(b0, m0, v0, x - z * uh, sp.lr, bc1, bc2, sc);
+    adam(b1, m1, v1, x - xhat + (1.f - z) * lh, sp.lr, bc1, bc2, sc);
+    float rec[12];
+    rec[0] = -(al - b1);
+#pragma unroll
+    for (int b = 0; b < NS; ++b) {
+        if (b >= nsl) { rec[1 + b] = 0.f; continue; }
+        if (ADD && b == newb) {
+            sl[b] = lamN;
+            sk[b] = lamN + muN + bi;
+        }
+        const bool zb = (zs >> b) & 1u;
+        const float prod = zb ? acc0 : acc[b];
+        const float gb = x - prod + sl[b] * (1.f - z) - z * (sk[b] - sl[b]);
+        const int sstep = sp.t - cb_slot_added_at(b, sc) + 1;
+        bc1 = bias_corr(st.bc1_tab, sc.ntab, sstep, sc.b1);
+        bc2 = bias_corr(st.bc2_tab, sc.ntab, sstep, sc.b2);
+        adam(sb[b], sm[b], sv[b], gb, sp.lr, bc1, bc2, sc);
+        if (zb) rec[0] += sb[b];
+        rec[1 + b] = zb ? 0.f : sb[b];
+    }
+    st.alpha[h] = al; st.ma[h] = ma; st.va[h] = va;
+    st.beta0[h] = b0; st.m0[h] = m0; st.v0[h] = v0;
+    st.beta1[h] = b1; st.m1[h] = m1; st.v1[h] = v1;
 #pragma unroll
     for (int b = 0; b < NS; ++b) {
         if (b >= nsl) continue;
         const size_t hs = hs0 + (size_t)b * NH;
-        float lam, kap;
-        if (ADD && b == newb) {
-            lam = lamN;
-            kap = lamN + muN + bi;
-            st.lam[hs] = lam;
-            st.kap[hs] = kap;
-        } else {
-            lam = st.lam[hs];
-            kap = st.kap[hs];
-        }
-        const bool zb = (zs >> b) & 1u;
-        const float prod = zb ? acc0 : acc[b];
-        const float gb = x - prod + lam * (1.f - z) - z * (kap - lam);
-        const int sstep = sp.t - cb_slot_added_at(b, sc) + 1;
-        bc1 = bias_corr(st.bc1_tab, sc.ntab, sstep, sc.b1);
-        bc2 = bias_corr(st.bc2_tab, sc.ntab, sstep, sc.b2);
-        adam(st.bs[hs], st.ms[hs], st.vs[hs], gb, sp.lr, bc1, bc2, sc);
-        const float bv = st.bs[hs];
-        if (zb) rsum += bv;
-        st.bz[hs] = zb ? 0.f : bv;
+        st.bs[hs] = sb[b]; st.ms[hs] = sm[b]; st.vs[hs] = sv[b];
+        if (ADD && b == newb) { st.lam[hs] = sl[b]; st.kap[hs] = sk[b]; }
     }
-    st.rp[h] = rsum;
+    float4* ar = reinterpret_cast<float4*>(st.arec + h * net.RS);
+    for (int q4 = 0; q4 < net.RS / 4; ++q4) {
+        float4 v;
+        v.x = 4 * q4 + 0 <= NS ? rec[4 * q4 + 0] : 0.f;
+        v.y = 4 * q4 + 1 <= NS ? rec[(4 * q4 + 1) % 12] : 0.f;
+        v.z = 4 * q4 + 2 <= NS ? rec[(4 * q4 + 2) % 12] : 0.f;
+        v.w = 4 * q4 + 3 <= NS ? rec[(4 * q4 + 3) % 12] : 0.f;
+        ar[q4] = v;
+    }
 }
 
 __global__ void __launch_bounds__(CB_THREADS) k_as_rowB_t(DNet net, DState st, DSched sc, TSegs sg) {
@@ -363,15 +403,20 @@ __global__ void k_rowprep(DNet net, DState st, DSched sc) {
         const int s = (int)(u / net.NH), hh = (int)(u - (size_t)s * net.NH);
         const int nsl = min(sp.nadd_before, st.caps[s]);
         const unsigned zs = st.zsnap[bo][u];
+        float* rec = st.arec + u * net.RS;
         float r = -(st.alpha[u] - st.beta1[u]);
-        for (int b = 0; b < net.cap; ++b) {
-            const size_t hs = ((size_t)s * net.cap + b) * net.NH + hh;
-            const float bv = b < nsl ? st.bs[hs] : 0.f;
-            const bool zb = (zs >> b) & 1u;
+        for (int b = 0; b < net.RS - 1; ++b) {
+            float bv = 0.f;
+            bool zb = false;
+            if (b < net.cap) {
+                const size_t hs = ((size_t)s * net.cap + b) * net.NH + hh;
+                bv = b < nsl ? st.bs[hs] : 0.f;
+                zb = (zs >> b) & 1u;
+            }
             if (zb) r += bv;
-            st.bz[hs] = zb ? 0.f : bv;
+            rec[1 + b] = zb ? 0.f : bv;
         }
-        st.rp[u] = r;
+        rec[0] = r;
     }
 }
 
@@ -380,6 +425,261 @@ __global__ void k_efix(DNet net, DState st) {
     const size_t n = (size_t)net.S * net.NT;
     for (size_t u = blockIdx.x * (size_t)blockDim.x + threadIdx.x; u < n; u += (size_t)gridDim.x * blockDim.x)
         st.efix[u] = st.lo[u] == st.hi[u];
+}
+
+
+// ---------------------------------------------------------------------- Saddle Point passes
+__device__ __forceinline__ bool team_any(bool v, int T) {
+    unsigned x = v ? 1u : 0u;
+    for (int o = T >> 1; o > 0; o >>= 1) x |= __shfl_xor_sync(0xffffffffu, x, o);
+    return x != 0u;
+}
+
+struct Unit {
+    int T, lane, s, idx;
+    bool valid;
+};
+
+__device__ __forceinline__ Unit team_unit(const TSegs& sg, int q, int count, int S) {
+    Unit u;
+    u.T = sg.T[q];
+    const int t = (blockIdx.x - sg.start[q]) * CB_THREADS + threadIdx.x;
+    const int unit = t / u.T;
+    u.lane = t - unit * u.T;
+    u.valid = unit < S * count;
+    const int o = u.valid ? unit / S : 0;
+    u.s = u.valid ? unit - o * S : 0;
+    u.idx = (u.valid && sg.perm[q]) ? sg.perm[q][o] : o;
+    return u;
+}
+
+// Phase A (col pass over k = 1..n) at the current (alpha, zeta): f_m = alpha_m - Sb_m -
+// W_{m+1}^T alpha_{m+1} + P_{m+1} (Sec. 5.1), the primal conditional gradient (eqs. 7-8 with
+// B = E), the bound terms, and the record {x, tau+, tau-, l} of input j for the row pass: the
+// float32 thresholds of the oracle eq. (3) at the current primal iterate. init != 0 also starts
+// the primal iterate at the conditional gradient.
+__global__ void __launch_bounds__(CB_THREADS) k_sp_colA_t(DNet net, DState st, TSegs sg, int init) {
+    const int q = tseg_of(sg, blockIdx.x);
+    const int li = sg.layer[q];
+    const DLayer& L = net.L[li];
+    const int k = li + 1, m = k - 1;
+    const Unit u = team_unit(sg, q, L.n_in, net.S);
+    const size_t NT = net.NT, NH = net.NH;
+    float acc = 0.f;
+    if (u.valid && k <= net.n - 1) {
+        const float* al = st.alpha + (size_t)u.s * NH + L.h_out;
+        col_walk_team(L, u.idx, u.lane, u.T, [&](int i, float w) { acc += w * al[i]; });
+    }
+    if (u.T > 1) acc = team_sum(acc, u.T);
+    if (!u.valid || u.lane != 0) return;
+    const int s = u.s, j = u.idx;
+    const int cur = st.ctr[1] & 1;
+    const size_t xo = (size_t)s * NT + L.in_off + j;
+    float f = k <= net.n - 1 ? st.P[xo] - acc : -net.Wout[(size_t)s * L.n_in + j];
+    const float lo = st.lo[xo], hi = st.hi[xo];
+    double term = 0.0;
+    if (m >= 1) {
+        const size_t h = (size_t)s * NH + L.h_in + j;
+        f += st.alpha[h] - st.Sb[h];
+        const float G = st.G[h];
+        const bool z = G >= 0.f;
+        st.zbar[h] = z;
+        if (init) st.spz[cur][h] = z ? 1.f : 0.f;
+        term = (double)net.L[m - 1].b[j] * st.alpha[h] + (double)st.C[h] - (z ? (double)G : 0.0);
+    }
+    const float xb = f >= 0.f ? hi : lo;
+    st.xbar[xo] = xb;
+    term -= (double)f * xb;
+    st.terms[xo] = term;
+    const float x = init ? xb : st.spx[cur][xo];
+    if (init) st.spx[cur][xo] = xb;
+    float tp = -INFINITY, tn = -INFINITY;
+    if (lo != hi) {
+        const float den = __fsub_rn(hi, lo);
+        tp = __fdiv_rn(__fsub_rn(x, lo), den);
+        tn = __fdiv_rn(__fsub_rn(hi, x), den);
+    }
+    st.inrec[xo] = make_float4(x, tp, tn, lo);
+}
+
+// Phase B (row pass over hidden layers) at the current primal iterate: the oracle mask I*
+// (eq. 3), the gradients of beta_0, beta_1, beta_I* (eq. 9 with B = E), the conditional
+// gradients alpha_bar (eq. 11) and beta_bar (eq. 12), the convex combination of alpha, Sb, G, C
+// (Alg. 2), and the row record for phase C.
+__global__ void __launch_bounds__(CB_THREADS) k_sp_rowB_t(DNet net, DState st, DSched sc, TSegs sg) {
+    const int q = tseg_of(sg, blockIdx.x);
+    const DLayer& L = net.L[sg.layer[q]];
+    const Unit u = team_unit(sg, q, L.n_out, net.S);
+    const int s = u.s, i = u.idx;
+    const int t = st.ctr[1];
+    const int cur = t & 1;
+    const size_t NT = net.NT, NH = net.NH;
+    const size_t h = (size_t)s * NH + L.h_out + i;
+    const float z = u.valid ? st.spz[cur][h] : 0.f;
+    float a0 = 0.f, A = 0.f, Lam = 0.f, Mu = 0.f;
+    bool any_in = false, any_out = false;
+    if (u.valid) {
+        const size_t ib = (size_t)s * NT + L.in_off;
+        const float4* rec = st.inrec + ib;
+        const float* hiv = st.hi + ib;
+        row_walk_team(L, i, u.lane, u.T, [&](int j, float w) {
+            const float4 r = rec[j];
+            const float uu = hiv[j];
+            const float wx = w * r.x;
+            a0 += wx;
+            const bool I = w > 0.f ? (z >= r.y) : (w < 0.f ? (z >= r.z) : true);
+            if (I) {
+                A += wx;
+                Lam += w * (w >= 0.f ? r.w : uu);
+                any_in |= (w != 0.f) && (r.w != uu);
+            } else {
+                Mu += w * (w >= 0.f ? uu : r.w);
+                any_out = true;   // I = 0 only for a nonzero weight on a free input
+            }
+        });
+    }
+    if (u.T > 1) {
+        a0 = team_sum(a0, u.T);
+        A = team_sum(A, u.T);
+        Lam = team_sum(Lam, u.T);
+        Mu = team_sum(Mu, u.T);
+    }
+    // a row selecting none or all of its free inputs is the all-zero / all-ones constraint, a
+    // looser copy of beta_0 / beta_1: it does not compete in the choice of eq. (12)
+    any_in = team_any(any_in, u.T);
+    any_out = team_any(any_out, u.T);
+    if (!u.valid || u.lane != 0) return;
+    const bool degenerate = !any_in || !any_out;
+    const float gamma = 1.f / ((float)t + sc.gamma0);
+    const float bi = L.b[i];
+    const float xhat = a0 + bi;
+    const float x = st.inrec[(size_t)s * NT + L.out_off + i].x;
+    const float uh = st.uhat[h], lh = st.lhat[h];
+    const float abar = (xhat - x >= 0.f) ? st.mua[h] : 0.f;
+    const float v0 = x - z * uh;
+    const float v1 = x - xhat + (1.f - z) * lh;
+    const float vI = x - A + (1.f - z) * Lam - z * (bi + Mu);
+    int sel = 0;
+    float vm = v0;
+    if (v1 > vm) { sel = 1; vm = v1; }
+    if (!degenerate && vI > vm) { sel = 2; vm = vI; }
+    const bool on = vm >= 0.f;
+    const float bb = on ? st.mub[h] : 0.f;
+    const float gsel = sel == 0 ? uh : (sel == 1 ? lh : Lam + Mu + bi);
+    const float csel = sel == 0 ? 0.f : (sel == 1 ? lh - bi : Lam);
+    const float om = 1.f - gamma;
+    st.alpha[h] = om * st.alpha[h] + gamma * abar;
+    st.Sb[h] = om * st.Sb[h] + gamma * bb;
+    st.G[h] = om * st.G[h] + gamma * (bb * gsel);
+    st.C[h] = om * st.C[h] + gamma * (bb * csel);
+    st.sel[h] = on ? (uint8_t)sel : (uint8_t)3;
+    st.rowrec[h] = make_float4(sel == 1 ? bb : 0.f, sel == 2 ? bb : 0.f, z, 0.f);
+}
+
+// Phase C (col pass over k = 1..n): P_bar_k = (W_k o I_dagger)^T beta_bar for input j (the masked
+// backward product of the chosen masks), the convex combination of P_k and of the primal iterate
+// (x_m, z_m) into the other buffer. The last block advances the iteration counter.
+__global__ void __launch_bounds__(CB_THREADS) k_sp_colC_t(DNet net, DState st, DSched sc, TSegs sg) {
+    const int q = tseg_of(sg, blockIdx.x);
+    const int li = sg.layer[q];
+    const DLayer& L = net.L[li];
+    const int k = li + 1, m = k - 1;
+    const Unit u = team_unit(sg, q, L.n_in, net.S);
+    const int t = st.ctr[1];
+    const size_t NT = net.NT, NH = net.NH;
+    const size_t xo = (size_t)u.s * NT + L.in_off + u.idx;
+    float acc = 0.f;
+    if (u.valid && k <= net.n - 1) {
+        const float4 r = st.inrec[xo];
+        const float4* rr = st.rowrec + (size_t)u.s * NH + L.h_out;
+        col_walk_team(L, u.idx, u.lane, u.T, [&](int i, float w) {
+            const float4 v = rr[i];
+            const bool I = w > 0.f ? (v.z >= r.y) : (w < 0.f ? (v.z >= r.z) : true);
+            acc += w * (v.x + (I ? v.y : 0.f));
+        });
+    }
+    if (u.T > 1) acc = team_sum(acc, u.T);
+    if (u.valid && u.lane == 0) {
+        const int cur = t & 1, nxt = cur ^ 1;
+        const float gamma = 1.f / ((float)t + sc.gamma0);
+        const float om = 1.f - gamma;
+        if (k <= net.n - 1) st.P[xo] = om * st.P[xo] + gamma * acc;
+        st.spx[nxt][xo] = om * st.spx[cur][xo] + gamma * st.xbar[xo];
+        if (m >= 1) {
+            const size_t hh = (size_t)u.s * NH + L.h_in + u.idx;
+            st.spz[nxt][hh] = om * st.spz[cur][hh] + gamma * (st.zbar[hh] ? 1.f : 0.f);
+        }
+    }
+    if (last_block(&st.done[1]) && threadIdx.x == 0) {
+        st.ctr[1] = t + 1;
+        st.done[1] = 0;
+    }
+}
+
+// Primal initialisation (App. C.2, Big-M variables), row pass: inner maximisers at (x, z).
+__global__ void __launch_bounds__(CB_THREADS) k_spi_row_t(DNet net, DState st, TSegs sg) {
+    const int q = tseg_of(sg, blockIdx.x);
+    const DLayer& L = net.L[sg.layer[q]];
+    const Unit u = team_unit(sg, q, L.n_out, net.S);
+    const int cur = st.ctr[1] & 1;
+    const size_t NT = net.NT, NH = net.NH;
+    float a0 = 0.f;
+    if (u.valid) {
+        const float* xv = st.spx[cur] + (size_t)u.s * NT + L.in_off;
+        row_walk_team(L, u.idx, u.lane, u.T, [&](int j, float w) { a0 += w * xv[j]; });
+    }
+    if (u.T > 1) a0 = team_sum(a0, u.T);
+    if (!u.valid || u.lane != 0) return;
+    const size_t h = (size_t)u.s * NH + L.h_out + u.idx;
+    const float xhat = a0 + L.b[u.idx];
+    const float x = st.spx[cur][(size_t)u.s * NT + L.out_off + u.idx];
+    const float z = st.spz[cur][h];
+    const float ab = (xhat - x >= 0.f) ? st.mua[h] : 0.f;
+    const float v0 = x - z * st.uhat[h];
+    const float v1 = x - xhat + (1.f - z) * st.lhat[h];
+    const bool on = fmaxf(v0, v1) >= 0.f;
+    const bool p0 = v0 >= v1;
+    const float b0 = (on && p0) ? st.mub[h] : 0.f;
+    const float b1 = (on && !p0) ? st.mub[h] : 0.f;
+    st.ab[h] = ab;
+    st.b0i[h] = b0;
+    st.b1i[h] = b1;
+    st.arow[h] = ab - b1;
+}
+
+// Primal initialisation, col pass: x_m += eta f_m(alpha*, beta*), z_m += eta g_m(beta*),
+// projected on the boxes (the primal view's subgradient in x_m is -f_m).
+__global__ void __launch_bounds__(CB_THREADS) k_spi_col_t(DNet net, DState st, DSched sc, TSegs sg) {
+    const int q = tseg_of(sg, blockIdx.x);
+    const int li = sg.layer[q];
+    const DLayer& L = net.L[li];
+    const int k = li + 1, m = k - 1;
+    const Unit u = team_unit(sg, q, L.n_in, net.S);
+    const int step = st.ctr[2];
+    const size_t NT = net.NT, NH = net.NH;
+    float acc = 0.f;
+    if (u.valid && k <= net.n - 1) {
+        const float* ar = st.arow + (size_t)u.s * NH + L.h_out;
+        col_walk_team(L, u.idx, u.lane, u.T, [&](int i, float w) { acc += w * ar[i]; });
+    }
+    if (u.T > 1) acc = team_sum(acc, u.T);
+    if (u.valid && u.lane == 0) {
+        const int cur = st.ctr[1] & 1;
+        const float eta = sc.sp_lr0 + (sc.sp_lr1 - sc.sp_lr0) * (float)step / (float)max(1, sc.sp_init_steps - 1);
+        float f = k <= net.n - 1 ? -acc : -net.Wout[(size_t)u.s * L.n_in + u.idx];
+        const size_t xo = (size_t)u.s * NT + L.in_off + u.idx;
+        if (m >= 1) {
+            const size_t h = (size_t)u.s * NH + L.h_in + u.idx;
+            f += st.ab[h] - st.b0i[h] - st.b1i[h];
+            const float g = st.b0i[h] * st.uhat[h] + st.b1i[h] * st.lhat[h];
+            st.spz[cur][h] = fminf(fmaxf(st.spz[cur][h] + eta * g, 0.f), 1.f);
+        }
+        st.spx[cur][xo] = fminf(fmaxf(st.spx[cur][xo] + eta * f, st.lo[xo]), st.hi[xo]);
+    }
+    if (last_block(&st.done[2]) && threadIdx.x == 0) {
+        st.ctr[2] = step + 1;
+        st.done[2] = 0;
+    }
 }
 
 }  // namespace cb

@@ -325,8 +325,7 @@ static int alloc_state(as_ctx* c) {
         float** zs[] = {&st.bs, &st.ms, &st.vs, &st.lam, &st.kap};
         for (float** p : zs) *p = z.take<float>(SL);
         st.P = z.take<float>(NTS);
-        st.rp = z.take<float>(NHS);
-        st.bz = z.take<float>(SL);
+        st.arec = z.take<float>(NHS * D.RS);
         for (int q = 0; q < 2; ++q) {
             st.xsnap[q] = z.take<uint8_t>(NTS);
             st.zsnap[q] = z.take<uint8_t>(NHS);
@@ -349,7 +348,11 @@ static int alloc_state(as_ctx* c) {
             st.spz[q] = o.take<float>(NHS);
         }
         st.zcur = o.take<uint8_t>(NHS);
+        st.xrec = o.take<float2>(NTS);
         st.efix = o.take<uint8_t>(NTS);
+        st.arow = o.take<float>(NHS);
+        st.inrec = o.take<float4>(NTS);
+        st.rowrec = o.take<float4>(NHS);
         st.zbar = o.take<uint8_t>(NHS);
         st.sel = o.take<uint8_t>(NHS);
         st.terms = o.take<double>(NTS);
@@ -478,6 +481,7 @@ static int init_impl(as_ctx* c, const as_net* net, int S, const float* x_lo, con
     D.n = n;
     D.S = S;
     D.cap = std::max(1, c->opt.max_cuts);
+    D.RS = ((1 + D.cap) + 3) / 4 * 4;
     int NT = 0;
     std::vector<int> off(n);
     for (int m = 0; m < n; ++m) {
@@ -630,11 +634,11 @@ static int launch_as_iter(as_ctx* c, cudaStream_t s) {
 }
 
 static int launch_sp_iter(as_ctx* c, cudaStream_t s) {
-    LAUNCH(c, s, CB_K_SP_COLA, (k_sp_colA<<<c->blocksA, CB_THREADS, 0, s>>>(c->net, c->st, c->segA, 0)));
+    LAUNCH(c, s, CB_K_SP_COLA, (k_sp_colA_t<<<c->blocksTA, CB_THREADS, 0, s>>>(c->net, c->st, c->tA, 0)));
     if (c->opt.track_best)
         LAUNCH(c, s, CB_K_REDUCE, (k_reduce<<<c->net.S, CB_THREADS, 0, s>>>(c->net, c->st, 64, nullptr, 1)));
-    LAUNCH(c, s, CB_K_SP_ROWB, (k_sp_rowB<<<c->blocksB, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->segB)));
-    LAUNCH(c, s, CB_K_SP_COLC, (k_sp_colC<<<c->blocksA, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->segA)));
+    LAUNCH(c, s, CB_K_SP_ROWB, (k_sp_rowB_t<<<c->blocksTB, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->tB)));
+    LAUNCH(c, s, CB_K_SP_COLC, (k_sp_colC_t<<<c->blocksTA, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->tA)));
     return check_launch(c, "Saddle Point iteration");
 }
 
@@ -700,12 +704,12 @@ static int sp_start(as_ctx* c) {
     k_sp_convert_elem<<<grid_for(NHS), CB_THREADS, 0, s>>>(c->net, c->st, c->sc, (float)c->opt.sp_c_alpha,
                                                            (float)c->opt.sp_c_beta);
     k_sp_convert_P<<<c->blocksP, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->segP);
-    k_sp_colA<<<c->blocksA, CB_THREADS, 0, s>>>(c->net, c->st, c->segA, 1);
+    k_sp_colA_t<<<c->blocksTA, CB_THREADS, 0, s>>>(c->net, c->st, c->tA, 1);
     c->launches += 3;
     TRY(check_launch(c, "Saddle Point conversion"));
     for (int t = 0; t < c->opt.sp_init_steps; ++t) {
-        LAUNCH(c, s, CB_K_SPI_ROW, (k_spi_row<<<c->blocksB, CB_THREADS, 0, s>>>(c->net, c->st, c->segB)));
-        LAUNCH(c, s, CB_K_SPI_COL, (k_spi_col<<<c->blocksA, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->segA)));
+        LAUNCH(c, s, CB_K_SPI_ROW, (k_spi_row_t<<<c->blocksTB, CB_THREADS, 0, s>>>(c->net, c->st, c->tB)));
+        LAUNCH(c, s, CB_K_SPI_COL, (k_spi_col_t<<<c->blocksTA, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->tA)));
     }
     TRY(check_launch(c, "Saddle Point primal initialisation"));
     c->sp_started = true;
@@ -724,7 +728,7 @@ extern "C" int as_bound(as_ctx* c, int precision, double* out, double* best) {
     if (precision != 32 && precision != 64) return fail(c, AS_ERR_ARG, "precision must be 32 or 64");
     const int S = c->net.S;
     cudaStream_t s = c->stream;
-    if (c->sp_started) LAUNCH(c, s, CB_K_SP_COLA, (k_sp_colA<<<c->blocksA, CB_THREADS, 0, s>>>(c->net, c->st, c->segA, 0)));
+    if (c->sp_started) LAUNCH(c, s, CB_K_SP_COLA, (k_sp_colA_t<<<c->blocksTA, CB_THREADS, 0, s>>>(c->net, c->st, c->tA, 0)));
     else LAUNCH(c, s, CB_K_AS_COLA, (k_as_colA_t<<<c->blocksTA, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->tA, 1)));
     double* dout = c->bound_out;
     LAUNCH(c, s, CB_K_REDUCE, (k_reduce<<<S, CB_THREADS, 0, s>>>(c->net, c->st, precision, dout, 1)));
