@@ -65,8 +65,8 @@ struct DState {
     int* ctr;                        // [0] AS iteration, [1] SP iteration, [2] SP-init step
     unsigned* done;                  // block-completion counters [4]
     const float* lr_tab;             // [ntab] step size per global iteration
-    const float* bc1_tab;            // [ntab] 1 - b1^step, step = index
-    const float* bc2_tab;            // [ntab] 1 - b2^step
+    const float* bc1_tab;            // [ntab] 1 / (1 - b1^step), step = index
+    const float* bc2_tab;            // [ntab] 1 / (1 - b2^step)
     // Saddle Point
     float* spx[2];                   // [S][NT]
     float* spz[2];                   // [S][NH]

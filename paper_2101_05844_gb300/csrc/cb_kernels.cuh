@@ -58,16 +58,20 @@ __device__ __forceinline__ bool last_block(unsigned* counter) {
     return is_last;
 }
 
-__device__ __forceinline__ float bias_corr(const float* tab, int ntab, int step, float beta) {
-    return step < ntab ? tab[step] : 1.f - powf(beta, (float)step);
+// 1 / (1 - beta^step), the Adam bias corrections, from a table built in FP64 on the host.
+__device__ __forceinline__ float inv_bias_corr(const float* tab, int ntab, int step, float beta) {
+    return step < ntab ? tab[step] : 1.f / (1.f - powf(beta, (float)step));
 }
 
-__device__ __forceinline__ void adam(float& th, float& m, float& v, float g, float lr, float bc1,
-                                     float bc2, const DSched& sc) {
+// One projected Adam ascent step (Kingma and Ba) of a dual variable: returns the new value and
+// updates the moments. Fast reciprocal square root and division (a few float32 ulps).
+__device__ __forceinline__ float adam_step(float th, float& m, float& v, float g, float lr, float ibc1,
+                                           float ibc2, const DSched& sc) {
     m = sc.b1 * m + sc.omb1 * g;
     v = sc.b2 * v + sc.omb2 * g * g;
-    const float mh = m / bc1, vh = v / bc2;
-    th = fmaxf(th + lr * mh / (sqrtf(vh) + sc.eps), 0.f);
+    const float mh = m * ibc1, vh = v * ibc2;
+    const float sq = vh > 0.f ? vh * rsqrtf(vh) : 0.f;
+    return fmaxf(th + lr * __fdividef(mh, sq + sc.eps), 0.f);
 }
 
 // ------------------------------------------------------------------------- interval bounds
@@ -152,186 +156,6 @@ __global__ void k_fold(DNet net, const float* Wlast, const float* blast, const f
         }
         if (j < nin) Wout[(size_t)s * nin + j] = (float)a;
         else bout[s] = (float)a;
-    }
-}
-
-// ------------------------------------------------------------- Big-M / Active Set: phase A
-// Col pass over layers k = 1..n. For input neuron j of layer k (neuron j of layer m = k-1):
-//   f_m[j] = alpha_m - beta0 - beta1 - sum_b beta_b                         (m >= 1)
-//            - (W_k^T (alpha_k - beta1_k))[j] + sum_b ((W_k o I_b)^T beta_b)[j]   (k <= n-1)
-//            - Wout[j]                                                      (k = n, alpha_n = 1)
-// (f of Sec. 4.1), the closed-form minimiser x*_m = u if f >= 0 else l (eqs. 7-8), and for
-// m >= 1: g_m = beta0 uhat + beta1 lhat + sum_b beta_b kappa_b, z* = [g >= 0]. Writes the
-// per-neuron bound terms of eq. (6). On addition iterations (mode 0) also records x*, z* into
-// the new slot's snapshot bits: the oracle eq. (3) called at (x*, z*) (Alg. 1, Prop. 1).
-// mode 0: iteration; mode 1: bound evaluation only.
-__global__ void __launch_bounds__(CB_THREADS) k_as_colA(DNet net, DState st, DSched sc, Segs sg, int mode) {
-    const int q = seg_of(sg, blockIdx.x);
-    const int li = sg.layer[q];
-    const DLayer& L = net.L[li];
-    const int k = li + 1, m = k - 1;
-    const int u = (blockIdx.x - sg.start[q]) * CB_THREADS + threadIdx.x;
-    if (u < net.S * L.n_in) {
-        const int s = u / L.n_in, j = u - s * L.n_in;
-        const Step sp = cb_step(st.ctr[0], sc, st.lr_tab);
-        const int cap_s = st.caps[s];
-        const int nsl = min(sp.nadd_before, cap_s);
-        const int bo = sp.nadd_before & 1;
-        const bool add_iter = (mode == 0) && sp.b_new >= 0;
-        const bool add = add_iter && sp.b_new < cap_s;
-        const size_t NT = net.NT, NH = net.NH, cap = net.cap;
-        const size_t xo = (size_t)s * NT + L.in_off + j;
-        const float lo = st.lo[xo], hi = st.hi[xo];
-        const unsigned xs = st.xsnap[bo][xo];
-        float acc0 = 0.f, accM = 0.f;
-        if (k <= net.n - 1) {
-            const size_t rb = (size_t)s * NH + L.h_out;
-            const float* al = st.alpha + rb;
-            const float* b1 = st.beta1 + rb;
-            const float* bsl = st.bs + (size_t)s * cap * NH + L.h_out;
-            const uint8_t* zs = st.zsnap[bo] + rb;
-            const bool fixed = lo == hi;
-            col_walk(L, j, [&](int i, float w) {
-                acc0 += w * (al[i] - b1[i]);
-                if (nsl) {
-                    const unsigned I = cb_slot_mask(zs[i], xs, fixed, w);
-                    float sb = 0.f;
-#pragma unroll
-                    for (int b = 0; b < CB_MAXCUT; ++b)
-                        if (b < nsl && ((I >> b) & 1u)) sb += bsl[(size_t)b * NH + i];
-                    accM += w * sb;
-                }
-            });
-        } else {
-            acc0 = net.Wout[(size_t)s * L.n_in + j];
-        }
-        float f = accM - acc0;
-        double term = 0.0;
-        if (m >= 1) {
-            const size_t h = (size_t)s * NH + L.h_in + j;
-            const size_t hs = (size_t)s * cap * NH + L.h_in + j;
-            float sb = 0.f, gk = st.beta0[h] * st.uhat[h] + st.beta1[h] * st.lhat[h];
-            double cterm = 0.0;
-#pragma unroll
-            for (int b = 0; b < CB_MAXCUT; ++b)
-                if (b < nsl) {
-                    const float bb = st.bs[hs + (size_t)b * NH];
-                    sb += bb;
-                    gk += bb * st.kap[hs + (size_t)b * NH];
-                    cterm += (double)bb * st.lam[hs + (size_t)b * NH];
-                }
-            f += st.alpha[h] - st.beta0[h] - st.beta1[h] - sb;
-            const bool z = gk >= 0.f;
-            st.zcur[h] = z;
-            const float bm = net.L[m - 1].b[j];
-            term = (double)bm * st.alpha[h] + (double)st.beta1[h] * ((double)st.lhat[h] - bm) + cterm
-                   - (z ? (double)gk : 0.0);
-            if (add_iter) {
-                const unsigned zs_old = st.zsnap[bo][h];
-                st.zsnap[bo ^ 1][h] = (uint8_t)(zs_old | ((add && z) ? (1u << sp.b_new) : 0u));
-            }
-        }
-        const bool up = f >= 0.f;
-        const float xv = up ? hi : lo;
-        st.xval[xo] = xv;
-        st.fval[xo] = f;
-        term -= (double)f * xv;
-        st.terms[xo] = term;
-        if (add_iter) st.xsnap[bo ^ 1][xo] = (uint8_t)(xs | ((add && up) ? (1u << sp.b_new) : 0u));
-    }
-}
-
-// ------------------------------------------------------------- Big-M / Active Set: phase B
-// Row pass over hidden layers. For (s, i) of layer k: xhat = W x* + b and, for every slot b,
-// (W o I_b) x*; on addition iterations lambda and kappa of the new slot (mask row sums).
-// Supergradient eq. (9), then the Adam ascent step and projection (Alg. 1 lines 10-11).
-// The last block advances the iteration counter.
-__global__ void __launch_bounds__(CB_THREADS) k_as_rowB(DNet net, DState st, DSched sc, Segs sg) {
-    const int q = seg_of(sg, blockIdx.x);
-    const DLayer& L = net.L[sg.layer[q]];
-    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int u = (blockIdx.x - sg.start[q]) * CB_WARPS + wib;
-    const int it = st.ctr[0];
-    if (u < net.S * L.n_out) {
-        const int s = u / L.n_out, i = u - s * L.n_out;
-        const Step sp = cb_step(it, sc, st.lr_tab);
-        const int cap_s = st.caps[s];
-        const int newb = (sp.b_new >= 0 && sp.b_new < cap_s) ? sp.b_new : -1;
-        const int nsl = min(sp.nadd_before + (sp.b_new >= 0 ? 1 : 0), cap_s);
-        const int bn = (sp.nadd_before + (sp.b_new >= 0 ? 1 : 0)) & 1;
-        const size_t NT = net.NT, NH = net.NH, cap = net.cap;
-        const size_t h = (size_t)s * NH + L.h_out + i;
-        const unsigned zs = st.zsnap[bn][h];
-        const float* xv = st.xval + (size_t)s * NT + L.in_off;
-        const float* lo = st.lo + (size_t)s * NT + L.in_off;
-        const float* hi = st.hi + (size_t)s * NT + L.in_off;
-        const uint8_t* xsn = st.xsnap[bn] + (size_t)s * NT + L.in_off;
-        float acc0 = 0.f, lamN = 0.f, muN = 0.f;
-        float acc[CB_MAXCUT];
-#pragma unroll
-        for (int b = 0; b < CB_MAXCUT; ++b) acc[b] = 0.f;
-        row_walk(L, i, lane, [&](int j, float w) {
-            const float x = xv[j];
-            const float wx = w * x;
-            acc0 += wx;
-            if (nsl) {
-                const float l = lo[j], uu = hi[j];
-                const unsigned I = cb_slot_mask(zs, xsn[j], l == uu, w);
-#pragma unroll
-                for (int b = 0; b < CB_MAXCUT; ++b)
-                    if (b < nsl && ((I >> b) & 1u)) acc[b] += wx;
-                if (newb >= 0) {
-                    if ((I >> newb) & 1u) lamN += w * (w >= 0.f ? l : uu);
-                    else muN += w * (w >= 0.f ? uu : l);
-                }
-            }
-        });
-        acc0 = warp_sum(acc0);
-#pragma unroll
-        for (int b = 0; b < CB_MAXCUT; ++b)
-            if (b < nsl) acc[b] = warp_sum(acc[b]);
-        if (newb >= 0) { lamN = warp_sum(lamN); muN = warp_sum(muN); }
-        const float bi = L.b[i];
-        const float xhat = acc0 + bi;
-        const float x = st.xval[(size_t)s * NT + L.out_off + i];
-        const float z = st.zcur[h] ? 1.f : 0.f;
-        const int step = it + 1;
-        if (lane == 0) {
-            const float bc1 = bias_corr(st.bc1_tab, sc.ntab, step, sc.b1);
-            const float bc2 = bias_corr(st.bc2_tab, sc.ntab, step, sc.b2);
-            const float ga = xhat - x;
-            const float g0 = x - z * st.uhat[h];
-            const float g1 = x - xhat + (1.f - z) * st.lhat[h];
-            adam(st.alpha[h], st.ma[h], st.va[h], ga, sp.lr, bc1, bc2, sc);
-            adam(st.beta0[h], st.m0[h], st.v0[h], g0, sp.lr, bc1, bc2, sc);
-            adam(st.beta1[h], st.m1[h], st.v1[h], g1, sp.lr, bc1, bc2, sc);
-        } else if (lane - 1 < nsl) {
-            const int b = lane - 1;
-            const size_t hs = (size_t)s * cap * NH + (size_t)b * NH + L.h_out + i;
-            float lam, kap;
-            if (b == newb) {
-                lam = lamN;
-                kap = lamN + muN + bi;
-                st.lam[hs] = lam;
-                st.kap[hs] = kap;
-            } else {
-                lam = st.lam[hs];
-                kap = st.kap[hs];
-            }
-            float ab = 0.f;
-#pragma unroll
-            for (int bb = 0; bb < CB_MAXCUT; ++bb)
-                if (bb == b) ab = acc[bb];
-            const float gb = x - ab + lam * (1.f - z) - z * (kap - lam);
-            const int sstep = sp.t - cb_slot_added_at(b, sc) + 1;
-            const float bc1 = bias_corr(st.bc1_tab, sc.ntab, sstep, sc.b1);
-            const float bc2 = bias_corr(st.bc2_tab, sc.ntab, sstep, sc.b2);
-            adam(st.bs[hs], st.ms[hs], st.vs[hs], gb, sp.lr, bc1, bc2, sc);
-        }
-    }
-    if (last_block(&st.done[0]) && threadIdx.x == 0) {
-        st.ctr[0] = it + 1;
-        st.done[0] = 0;
     }
 }
 
@@ -427,249 +251,6 @@ __global__ void __launch_bounds__(CB_THREADS) k_sp_convert_P(DNet net, DState st
         acc += w * sb;
     });
     st.P[xo] = acc;
-}
-
-// --------------------------------------------------------------- Saddle Point: phase A
-// Col pass over k = 1..n for neuron j of layer m = k-1 at the current (alpha, zeta):
-// f_m = alpha_m - Sb_m - W_{m+1}^T alpha_{m+1} + P_{m+1} (Sec. 5.1), the primal conditional
-// gradient x_bar, z_bar (eqs. 7-8 with B = E), the bound terms, and the oracle thresholds of
-// neuron j at the current primal iterate. init != 0: also start the primal iterate there.
-__global__ void __launch_bounds__(CB_THREADS) k_sp_colA(DNet net, DState st, Segs sg, int init) {
-    const int q = seg_of(sg, blockIdx.x);
-    const int li = sg.layer[q];
-    const DLayer& L = net.L[li];
-    const int k = li + 1, m = k - 1;
-    const int u = (blockIdx.x - sg.start[q]) * CB_THREADS + threadIdx.x;
-    if (u >= net.S * L.n_in) return;
-    const int s = u / L.n_in, j = u - s * L.n_in;
-    const int cur = st.ctr[1] & 1;
-    const size_t NT = net.NT, NH = net.NH;
-    const size_t xo = (size_t)s * NT + L.in_off + j;
-    float acc = 0.f;
-    if (k <= net.n - 1) {
-        const float* al = st.alpha + (size_t)s * NH + L.h_out;
-        col_walk(L, j, [&](int i, float w) { acc += w * al[i]; });
-    } else {
-        acc = net.Wout[(size_t)s * L.n_in + j];
-    }
-    float f = -acc;
-    if (k <= net.n - 1) f += st.P[xo];
-    const float lo = st.lo[xo], hi = st.hi[xo];
-    double term = 0.0;
-    if (m >= 1) {
-        const size_t h = (size_t)s * NH + L.h_in + j;
-        f += st.alpha[h] - st.Sb[h];
-        const float G = st.G[h];
-        const bool z = G >= 0.f;
-        st.zbar[h] = z;
-        if (init) st.spz[cur][h] = z ? 1.f : 0.f;
-        term = (double)net.L[m - 1].b[j] * st.alpha[h] + (double)st.C[h] - (z ? (double)G : 0.0);
-    }
-    const float xb = f >= 0.f ? hi : lo;
-    st.xbar[xo] = xb;
-    term -= (double)f * xb;
-    st.terms[xo] = term;
-    const float x = init ? xb : st.spx[cur][xo];
-    if (init) st.spx[cur][xo] = xb;
-    if (lo == hi) {
-        st.taup[xo] = -INFINITY;
-        st.taun[xo] = -INFINITY;
-    } else {
-        const float den = __fsub_rn(hi, lo);
-        st.taup[xo] = __fdiv_rn(__fsub_rn(x, lo), den);
-        st.taun[xo] = __fdiv_rn(__fsub_rn(hi, x), den);
-    }
-}
-
-// --------------------------------------------------------------- Saddle Point: phase B
-// Row pass over hidden layers at the current primal iterate (x^t, z^t): the oracle mask I*
-// (eq. 3), the gradients of beta_0, beta_1, beta_I* (eq. 9 with B = E), the dual conditional
-// gradients alpha_bar (eq. 11) and beta_bar (eq. 12, ties to the lower index), and the convex
-// combination of alpha and of the elementwise statistics Sb, G, C (Alg. 2).
-__global__ void __launch_bounds__(CB_THREADS) k_sp_rowB(DNet net, DState st, DSched sc, Segs sg) {
-    const int q = seg_of(sg, blockIdx.x);
-    const DLayer& L = net.L[sg.layer[q]];
-    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int u = (blockIdx.x - sg.start[q]) * CB_WARPS + wib;
-    if (u >= net.S * L.n_out) return;
-    const int s = u / L.n_out, i = u - s * L.n_out;
-    const int t = st.ctr[1];
-    const int cur = t & 1;
-    const float gamma = 1.f / ((float)t + sc.gamma0);
-    const size_t NT = net.NT, NH = net.NH;
-    const size_t h = (size_t)s * NH + L.h_out + i;
-    const float z = st.spz[cur][h];
-    const size_t ib = (size_t)s * NT + L.in_off;
-    const float* xv = st.spx[cur] + ib;
-    const float* lo = st.lo + ib;
-    const float* hi = st.hi + ib;
-    const float* tp = st.taup + ib;
-    const float* tn = st.taun + ib;
-    float a0 = 0.f, A = 0.f, Lam = 0.f, Mu = 0.f;
-    bool any_in = false, any_out = false;
-    row_walk(L, i, lane, [&](int j, float w) {
-        const float x = xv[j];
-        const float wx = w * x;
-        a0 += wx;
-        const bool I = cb_sp_mask(z, tp[j], tn[j], w);
-        const float l = lo[j], uu = hi[j];
-        if (I) {
-            A += wx;
-            Lam += w * (w >= 0.f ? l : uu);
-            any_in |= (w != 0.f) && (l != uu);
-        } else {
-            Mu += w * (w >= 0.f ? uu : l);
-            any_out = true;   // I = 0 only for a nonzero weight on a free input
-        }
-    });
-    // a row selecting none or all of its free inputs (nonzero weight, l < u; a fixed input adds the
-    // same term selected or not) is the all-zero / all-ones constraint: a looser copy of the
-    // beta_0 / beta_1 constraint, which does not compete in the choice of eq. (12)
-    const bool degenerate = !__any_sync(0xffffffffu, any_in) || !__any_sync(0xffffffffu, any_out);
-    a0 = warp_sum(a0);
-    A = warp_sum(A);
-    Lam = warp_sum(Lam);
-    Mu = warp_sum(Mu);
-    if (lane == 0) {
-        const float bi = L.b[i];
-        const float xhat = a0 + bi;
-        const float x = st.spx[cur][(size_t)s * NT + L.out_off + i];
-        const float uh = st.uhat[h], lh = st.lhat[h];
-        const float abar = (xhat - x >= 0.f) ? st.mua[h] : 0.f;
-        const float v0 = x - z * uh;
-        const float v1 = x - xhat + (1.f - z) * lh;
-        const float vI = x - A + (1.f - z) * Lam - z * (bi + Mu);
-        int sel = 0;
-        float vm = v0;
-        if (v1 > vm) { sel = 1; vm = v1; }
-        if (!degenerate && vI > vm) { sel = 2; vm = vI; }
-        const bool on = vm >= 0.f;
-        const float bb = on ? st.mub[h] : 0.f;
-        const float gsel = sel == 0 ? uh : (sel == 1 ? lh : Lam + Mu + bi);
-        const float csel = sel == 0 ? 0.f : (sel == 1 ? lh - bi : Lam);
-        const float om = 1.f - gamma;
-        st.alpha[h] = om * st.alpha[h] + gamma * abar;
-        st.Sb[h] = om * st.Sb[h] + gamma * bb;
-        st.G[h] = om * st.G[h] + gamma * (bb * gsel);
-        st.C[h] = om * st.C[h] + gamma * (bb * csel);
-        st.sel[h] = on ? (uint8_t)sel : (uint8_t)3;
-    }
-}
-
-// --------------------------------------------------------------- Saddle Point: phase C
-// Col pass over k = 1..n for neuron j of layer m = k-1: the masked backward product of the
-// selected conditional-gradient masks, P_bar_k = (W_k o I_dagger)^T beta_bar (eq. 10's second
-// statistic), and the convex combination of P_k and of the primal iterate (x_m, z_m) into the
-// other buffer. The last block advances the iteration counter.
-__global__ void __launch_bounds__(CB_THREADS) k_sp_colC(DNet net, DState st, DSched sc, Segs sg) {
-    const int q = seg_of(sg, blockIdx.x);
-    const int li = sg.layer[q];
-    const DLayer& L = net.L[li];
-    const int k = li + 1, m = k - 1;
-    const int u = (blockIdx.x - sg.start[q]) * CB_THREADS + threadIdx.x;
-    const int t = st.ctr[1];
-    if (u < net.S * L.n_in) {
-        const int s = u / L.n_in, j = u - s * L.n_in;
-        const int cur = t & 1, nxt = cur ^ 1;
-        const float gamma = 1.f / ((float)t + sc.gamma0);
-        const float om = 1.f - gamma;
-        const size_t NT = net.NT, NH = net.NH;
-        const size_t xo = (size_t)s * NT + L.in_off + j;
-        if (k <= net.n - 1) {
-            const size_t rb = (size_t)s * NH + L.h_out;
-            const uint8_t* sel = st.sel + rb;
-            const float* mub = st.mub + rb;
-            const float* zr = st.spz[cur] + rb;
-            const float tp = st.taup[xo], tn = st.taun[xo];
-            float acc = 0.f;
-            col_walk(L, j, [&](int i, float w) {
-                const int sl = sel[i];
-                if (sl == 1 || (sl == 2 && cb_sp_mask(zr[i], tp, tn, w))) acc += w * mub[i];
-            });
-            st.P[xo] = om * st.P[xo] + gamma * acc;
-        }
-        st.spx[nxt][xo] = om * st.spx[cur][xo] + gamma * st.xbar[xo];
-        if (m >= 1) {
-            const size_t hh = (size_t)s * NH + L.h_in + j;
-            st.spz[nxt][hh] = om * st.spz[cur][hh] + gamma * (st.zbar[hh] ? 1.f : 0.f);
-        }
-    }
-    if (last_block(&st.done[1]) && threadIdx.x == 0) {
-        st.ctr[1] = t + 1;
-        st.done[1] = 0;
-    }
-}
-
-// ------------------------------------------------------ Saddle Point: primal initialisation
-// App. C.2, simplified to the Big-M variables. Row pass: inner maximisers at (x, z):
-// alpha* = mu_alpha [xhat - x >= 0]; beta0*, beta1* = mu_beta on the larger of their gradients
-// (ties to beta0) when it is >= 0.
-__global__ void __launch_bounds__(CB_THREADS) k_spi_row(DNet net, DState st, Segs sg) {
-    const int q = seg_of(sg, blockIdx.x);
-    const DLayer& L = net.L[sg.layer[q]];
-    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int u = (blockIdx.x - sg.start[q]) * CB_WARPS + wib;
-    if (u >= net.S * L.n_out) return;
-    const int s = u / L.n_out, i = u - s * L.n_out;
-    const int cur = st.ctr[1] & 1;
-    const size_t NT = net.NT, NH = net.NH;
-    const float* xv = st.spx[cur] + (size_t)s * NT + L.in_off;
-    float a0 = 0.f;
-    row_walk(L, i, lane, [&](int j, float w) { a0 += w * xv[j]; });
-    a0 = warp_sum(a0);
-    if (lane == 0) {
-        const size_t h = (size_t)s * NH + L.h_out + i;
-        const float xhat = a0 + L.b[i];
-        const float x = st.spx[cur][(size_t)s * NT + L.out_off + i];
-        const float z = st.spz[cur][h];
-        st.ab[h] = (xhat - x >= 0.f) ? st.mua[h] : 0.f;
-        const float v0 = x - z * st.uhat[h];
-        const float v1 = x - xhat + (1.f - z) * st.lhat[h];
-        const bool on = fmaxf(v0, v1) >= 0.f;
-        const bool p0 = v0 >= v1;
-        st.b0i[h] = (on && p0) ? st.mub[h] : 0.f;
-        st.b1i[h] = (on && !p0) ? st.mub[h] : 0.f;
-    }
-}
-
-// Col pass: subgradient step x_m += eta f_m(alpha*, beta*), z_m += eta g_m(beta*), projected on
-// the boxes. The primal view's subgradient in x_m is -f_m since L holds -f_m^T x_m.
-__global__ void __launch_bounds__(CB_THREADS) k_spi_col(DNet net, DState st, DSched sc, Segs sg) {
-    const int q = seg_of(sg, blockIdx.x);
-    const int li = sg.layer[q];
-    const DLayer& L = net.L[li];
-    const int k = li + 1, m = k - 1;
-    const int u = (blockIdx.x - sg.start[q]) * CB_THREADS + threadIdx.x;
-    const int step = st.ctr[2];
-    if (u < net.S * L.n_in) {
-        const int s = u / L.n_in, j = u - s * L.n_in;
-        const int cur = st.ctr[1] & 1;
-        const size_t NT = net.NT, NH = net.NH;
-        const float eta = sc.sp_lr0 + (sc.sp_lr1 - sc.sp_lr0) * (float)step /
-                          (float)max(1, sc.sp_init_steps - 1);
-        float acc = 0.f;
-        if (k <= net.n - 1) {
-            const size_t rb = (size_t)s * NH + L.h_out;
-            const float* ab = st.ab + rb;
-            const float* b1 = st.b1i + rb;
-            col_walk(L, j, [&](int i, float w) { acc += w * (ab[i] - b1[i]); });
-        } else {
-            acc = net.Wout[(size_t)s * L.n_in + j];
-        }
-        float f = -acc;
-        const size_t xo = (size_t)s * NT + L.in_off + j;
-        if (m >= 1) {
-            const size_t h = (size_t)s * NH + L.h_in + j;
-            f += st.ab[h] - st.b0i[h] - st.b1i[h];
-            const float g = st.b0i[h] * st.uhat[h] + st.b1i[h] * st.lhat[h];
-            st.spz[cur][h] = fminf(fmaxf(st.spz[cur][h] + eta * g, 0.f), 1.f);
-        }
-        st.spx[cur][xo] = fminf(fmaxf(st.spx[cur][xo] + eta * f, st.lo[xo]), st.hi[xo]);
-    }
-    if (last_block(&st.done[2]) && threadIdx.x == 0) {
-        st.ctr[2] = step + 1;
-        st.done[2] = 0;
-    }
 }
 
 }  // namespace cb

@@ -1,8 +1,8 @@
 // Active Set iteration kernels with lane teams.
 //
 // A unit is one (output neuron, subproblem) pair of a row pass, or one (input neuron,
-// subproblem) pair of a col pass; subproblems vary fastest, so the lanes of a warp read the same
-// weights (broadcast loads) and, for conv layers, walk the same taps. A team of T lanes (a power
+// subproblem) pair of a col pass; neurons vary fastest, so the lanes of a warp read neighbouring
+// entries of one subproblem's vectors and, for conv layers, share weights (broadcast loads). A team of T lanes (a power
 // of two chosen per layer on the host) splits one unit's reduction; the team then reduces with
 // shuffles. Conv taps are walked without integer division in the loop, and col-pass units of a
 // strided conv are ordered by stride parity (a permutation table) so that a warp's lanes take the
@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(CB_THREADS) k_as_colA_t(DNet net, DState st, D
     const int t = (blockIdx.x - sg.start[q]) * CB_THREADS + threadIdx.x;
     const int unit = t / T, lane = t - unit * T;
     const bool valid = unit < net.S * L.n_in;
-    const int o = valid ? unit / net.S : 0, s = valid ? unit - o * net.S : 0;
+    const int s = valid ? unit / L.n_in : 0, o = valid ? unit - s * L.n_in : 0;
     const int j = (valid && sg.perm[q]) ? sg.perm[q][o] : o;
     const Step sp = cb_step(st.ctr[0], sc, st.lr_tab);
     const int ns = min(sp.nadd_before, sc.maxcut);
@@ -284,73 +284,63 @@ __device__ __forceinline__ void as_rowB_body(const DNet& net, const DState& st, 
             muN = team_sum(muN, T);
         }
     }
-    if (!valid || lane != 0) return;
+    // epilogue: the team's lanes share the Adam updates (variable v = alpha, beta_0, beta_1, then
+    // the slots), each lane handling v = lane, lane + T, ...
     const int nsl = min(sp.nadd_before + (sp.b_new >= 0 ? 1 : 0), cap_s);
-    // every load before any store: the state arrays live in one arena and may not be reordered
-    const float bi = L.b[i];
-    const float x = st.xval[(size_t)s * NT + L.out_off + i];
-    const float z = st.zcur[h] ? 1.f : 0.f;
-    const float uh = st.uhat[h], lh = st.lhat[h];
-    float al = st.alpha[h], ma = st.ma[h], va = st.va[h];
-    float b0 = st.beta0[h], m0 = st.m0[h], v0 = st.v0[h];
-    float b1 = st.beta1[h], m1 = st.m1[h], v1 = st.v1[h];
-    const size_t hs0 = (size_t)s * cap * NH + L.h_out + i;
-    float sb[NS > 0 ? NS : 1], sm[NS > 0 ? NS : 1], sv[NS > 0 ? NS : 1], sl[NS > 0 ? NS : 1], sk[NS > 0 ? NS : 1];
+    float contrib = 0.f;   // this lane's share of rp = -(alpha - beta_1) + sum_b z_b beta_b
+    if (valid) {
+        const float bi = L.b[i];
+        const float x = st.xval[(size_t)s * NT + L.out_off + i];
+        const float z = st.zcur[h] ? 1.f : 0.f;
+        const float xhat = acc0 + bi;
+        const size_t hs0 = (size_t)s * cap * NH + L.h_out + i;
+        float* ar = st.arec + h * net.RS;
+        for (int v = lane; v < 3 + NS; v += T) {
+            if (v < 3) {
+                float* th = v == 0 ? st.alpha : (v == 1 ? st.beta0 : st.beta1);
+                float* mm = v == 0 ? st.ma : (v == 1 ? st.m0 : st.m1);
+                float* vv = v == 0 ? st.va : (v == 1 ? st.v0 : st.v1);
+                const float g = v == 0 ? xhat - x : (v == 1 ? x - z * st.uhat[h] : x - xhat + (1.f - z) * st.lhat[h]);
+                const int step = it + 1;
+                float m = mm[h], w2 = vv[h];
+                const float nv = adam_step(th[h], m, w2, g, sp.lr, inv_bias_corr(st.bc1_tab, sc.ntab, step, sc.b1),
+                                           inv_bias_corr(st.bc2_tab, sc.ntab, step, sc.b2), sc);
+                th[h] = nv; mm[h] = m; vv[h] = w2;
+                if (v == 0) contrib -= nv;
+                if (v == 2) contrib += nv;
+            } else {
+                const int b = v - 3;
+                if (b >= nsl) { ar[1 + b] = 0.f; continue; }
+                const size_t hs = hs0 + (size_t)b * NH;
+                float lam, kap;
+                if (ADD && b == newb) {
+                    lam = lamN;
+                    kap = lamN + muN + bi;
+                    st.lam[hs] = lam;
+                    st.kap[hs] = kap;
+                } else {
+                    lam = st.lam[hs];
+                    kap = st.kap[hs];
+                }
+                float ab = 0.f;
 #pragma unroll
-    for (int b = 0; b < NS; ++b) {
-        const size_t hs = hs0 + (size_t)b * NH;
-        const bool live = b < nsl;
-        sb[b] = live ? st.bs[hs] : 0.f;
-        sm[b] = live ? st.ms[hs] : 0.f;
-        sv[b] = live ? st.vs[hs] : 0.f;
-        sl[b] = live ? st.lam[hs] : 0.f;
-        sk[b] = live ? st.kap[hs] : 0.f;
-    }
-    const float xhat = acc0 + bi;
-    const int step = it + 1;
-    float bc1 = bias_corr(st.bc1_tab, sc.ntab, step, sc.b1);
-    float bc2 = bias_corr(st.bc2_tab, sc.ntab, step, sc.b2);
-    adam(al, ma, va, xhat - x, sp.lr, bc1, bc2, sc);
-    adam(b0, m0, v0, x - z * uh, sp.lr, bc1, bc2, sc);
-    adam(b1, m1, v1, x - xhat + (1.f - z) * lh, sp.lr, bc1, bc2, sc);
-    float rec[12];
-    rec[0] = -(al - b1);
-#pragma unroll
-    for (int b = 0; b < NS; ++b) {
-        if (b >= nsl) { rec[1 + b] = 0.f; continue; }
-        if (ADD && b == newb) {
-            sl[b] = lamN;
-            sk[b] = lamN + muN + bi;
+                for (int bb = 0; bb < NS; ++bb)
+                    if (bb == b) ab = acc[bb];
+                const bool zb = (zs >> b) & 1u;
+                const float prod = zb ? acc0 : ab;
+                const float gb = x - prod + lam * (1.f - z) - z * (kap - lam);
+                const int sstep = sp.t - cb_slot_added_at(b, sc) + 1;
+                float m = st.ms[hs], w2 = st.vs[hs];
+                const float nv = adam_step(st.bs[hs], m, w2, gb, sp.lr, inv_bias_corr(st.bc1_tab, sc.ntab, sstep, sc.b1),
+                                           inv_bias_corr(st.bc2_tab, sc.ntab, sstep, sc.b2), sc);
+                st.bs[hs] = nv; st.ms[hs] = m; st.vs[hs] = w2;
+                if (zb) contrib += nv;
+                ar[1 + b] = zb ? 0.f : nv;
+            }
         }
-        const bool zb = (zs >> b) & 1u;
-        const float prod = zb ? acc0 : acc[b];
-        const float gb = x - prod + sl[b] * (1.f - z) - z * (sk[b] - sl[b]);
-        const int sstep = sp.t - cb_slot_added_at(b, sc) + 1;
-        bc1 = bias_corr(st.bc1_tab, sc.ntab, sstep, sc.b1);
-        bc2 = bias_corr(st.bc2_tab, sc.ntab, sstep, sc.b2);
-        adam(sb[b], sm[b], sv[b], gb, sp.lr, bc1, bc2, sc);
-        if (zb) rec[0] += sb[b];
-        rec[1 + b] = zb ? 0.f : sb[b];
     }
-    st.alpha[h] = al; st.ma[h] = ma; st.va[h] = va;
-    st.beta0[h] = b0; st.m0[h] = m0; st.v0[h] = v0;
-    st.beta1[h] = b1; st.m1[h] = m1; st.v1[h] = v1;
-#pragma unroll
-    for (int b = 0; b < NS; ++b) {
-        if (b >= nsl) continue;
-        const size_t hs = hs0 + (size_t)b * NH;
-        st.bs[hs] = sb[b]; st.ms[hs] = sm[b]; st.vs[hs] = sv[b];
-        if (ADD && b == newb) { st.lam[hs] = sl[b]; st.kap[hs] = sk[b]; }
-    }
-    float4* ar = reinterpret_cast<float4*>(st.arec + h * net.RS);
-    for (int q4 = 0; q4 < net.RS / 4; ++q4) {
-        float4 v;
-        v.x = 4 * q4 + 0 <= NS ? rec[4 * q4 + 0] : 0.f;
-        v.y = 4 * q4 + 1 <= NS ? rec[(4 * q4 + 1) % 12] : 0.f;
-        v.z = 4 * q4 + 2 <= NS ? rec[(4 * q4 + 2) % 12] : 0.f;
-        v.w = 4 * q4 + 3 <= NS ? rec[(4 * q4 + 3) % 12] : 0.f;
-        ar[q4] = v;
-    }
+    if (T > 1) contrib = team_sum(contrib, T);
+    if (valid && lane == 0) st.arec[h * net.RS] = contrib;
 }
 
 __global__ void __launch_bounds__(CB_THREADS) k_as_rowB_t(DNet net, DState st, DSched sc, TSegs sg) {
@@ -360,7 +350,7 @@ __global__ void __launch_bounds__(CB_THREADS) k_as_rowB_t(DNet net, DState st, D
     const int t = (blockIdx.x - sg.start[q]) * CB_THREADS + threadIdx.x;
     const int unit = t / T, lane = t - unit * T;
     const bool valid = unit < net.S * L.n_out;
-    const int i = valid ? unit / net.S : 0, s = valid ? unit - i * net.S : 0;
+    const int s = valid ? unit / L.n_out : 0, i = valid ? unit - s * L.n_out : 0;
     const int it = st.ctr[0];
     const Step sp = cb_step(it, sc, st.lr_tab);
     const int ns = min(sp.nadd_before + (sp.b_new >= 0 ? 1 : 0), sc.maxcut);
@@ -447,8 +437,8 @@ __device__ __forceinline__ Unit team_unit(const TSegs& sg, int q, int count, int
     const int unit = t / u.T;
     u.lane = t - unit * u.T;
     u.valid = unit < S * count;
-    const int o = u.valid ? unit / S : 0;
-    u.s = u.valid ? unit - o * S : 0;
+    u.s = u.valid ? unit / count : 0;
+    const int o = u.valid ? unit - u.s * count : 0;
     u.idx = (u.valid && sg.perm[q]) ? sg.perm[q][o] : o;
     return u;
 }

@@ -204,8 +204,9 @@ static int build_tables(as_ctx* c) {
             v = o.as_lr0 + (o.as_lr1 - o.as_lr0) * (it - o.bigm_iters) / std::max(1, o.as_iters - 1);
         else v = lr_end;
         lr[it] = (float)v;
-        b1[it] = (float)(1.0 - std::pow(o.adam_b1, (double)it));
-        b2[it] = (float)(1.0 - std::pow(o.adam_b2, (double)it));
+        // reciprocal bias corrections 1 / (1 - beta^step); entry 0 is never used
+        b1[it] = it ? (float)(1.0 / (1.0 - std::pow(o.adam_b1, (double)it))) : 1.f;
+        b2[it] = it ? (float)(1.0 / (1.0 - std::pow(o.adam_b2, (double)it))) : 1.f;
     }
     float *dlr, *db1, *db2;
     TRY(dalloc(c, &dlr, ntab));
