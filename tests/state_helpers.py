@@ -33,10 +33,11 @@ def split_hidden(vec, widths):
     return out
 
 
-def draw_state(Ps, ctx, opt_kw, it, nslots, seed, scale=0.3, adam=True):
+def draw_state(Ps, ctx, opt_kw, it, nslots, seed, scale=0.3, adam=True, subset=None):
     """Draw a state at global iteration `it` with `nslots` filled slots; install it on both sides.
 
-    Returns the list of oracle ActiveSet solvers (one per subproblem)."""
+    Returns the oracle ActiveSet solvers: a list over all subproblems, or a dict over `subset`
+    (the oracle side is then built for those subproblems only)."""
     rng = SplitMix64(seed)
     S, NH, NT, cap = ctx.S, ctx.NH, ctx.NT, ctx.cap
     widths = ctx.widths
@@ -72,9 +73,11 @@ def draw_state(Ps, ctx, opt_kw, it, nslots, seed, scale=0.3, adam=True):
     ctx.set_state(binding.ST_XSNAP, xsnap)
     ctx.set_state(binding.ST_ZSNAP, zsnap)
     ctx.set_state(binding.ST_SLOT_BETA, sb)
-    opt = AS.Options(**opt_kw)
-    solvers = []
+    opt = AS.Options(**{k: v for k, v in opt_kw.items() if hasattr(AS.Options, k)})
+    solvers = {} if subset is not None else []
     for s, P in enumerate(Ps):
+        if subset is not None and s not in subset:
+            continue
         st = du.DualState.zeros(P)
         st.alpha = [None] + split_hidden(alpha[s].astype(np.float64), widths)[1:]
         st.beta0 = [None] + split_hidden(beta0[s].astype(np.float64), widths)[1:]
@@ -96,7 +99,10 @@ def draw_state(Ps, ctx, opt_kw, it, nslots, seed, scale=0.3, adam=True):
         for q, key in enumerate(["a", "0", "1"]):
             solver.m[key] = [None] + [v.astype(np.float64) for v in split_hidden(m3[2 * q, s], widths)[1:]]
             solver.v[key] = [None] + [v.astype(np.float64) for v in split_hidden(m3[2 * q + 1, s], widths)[1:]]
-        solvers.append(solver)
+        if subset is not None:
+            solvers[s] = solver
+        else:
+            solvers.append(solver)
     return solvers
 
 

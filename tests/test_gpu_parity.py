@@ -410,3 +410,51 @@ def test_runs_are_deterministic():
         ctx.as_step(40)
         out.append((ctx.bound(), ctx.get_state(binding.ST_SLOT_BETA).tobytes()))
     assert (out[0][0] == out[1][0]).all() and out[0][1] == out[1][1]
+
+
+@pytest.mark.parametrize("it,nslots", [(236, 4), (240, 4)])
+def test_full_size_wide_conv_lockstep_on_sampled_subproblems(it, nslots):
+    """The bench workload at full size (Wide conv net, 9 properties), in the bench's launch
+    configuration: one Active Set iteration from a drawn state with 4 filled slots (omega 20:
+    iteration 236 is ordinary, 240 adds slot 4), every dual of two sampled subproblems against the
+    oracle (the oracle's dense conv operators are large)."""
+    prob = synth.problem("wide_conv", seed=0)
+    dense = nw.dense_layers(prob["net"])
+    Ps0 = nw.problems(prob, dense=dense)
+    lh, uh = oracle_bounds_f32(Ps0)
+    widths = Ps0[0].widths
+    Ps = nw.problems(prob, bounds=[(split_hidden(lh[s].astype(np.float64), widths)[1:],
+                                    split_hidden(uh[s].astype(np.float64), widths)[1:]) for s in range(9)],
+                     dense=dense)
+    kw = dict(bigm_iters=200, as_iters=800, omega=20, max_cuts=5)
+    ctx = binding.context_for(prob, binding.default_options(graph_chunk=25, **kw), bounds=(lh, uh))
+    sample = {0, 5}
+    solvers = draw_state(Ps, ctx, kw, it, nslots, seed=300 + it, subset=sample)
+    gb = ctx.bound()
+    for s, sv in solvers.items():
+        assert gb[s] == pytest.approx(du.evaluate(sv.P, sv.st)[0], abs=1e-4, rel=1e-5)
+    ctx.as_step(1)
+    S = 9
+    al = ctx.get_state(binding.ST_ALPHA).reshape(S, -1)
+    b1 = ctx.get_state(binding.ST_BETA1).reshape(S, -1)
+    sb = ctx.get_state(binding.ST_SLOT_BETA).reshape(S, ctx.cap, -1)
+    xstar = ctx.get_state(binding.ST_XSTAR).reshape(S, -1)
+    for s, sv in solvers.items():
+        P = sv.P
+        _, f, g, x, z = du.evaluate(P, sv.st)
+        grads = du.supergradient(P, sv.st, x, z)
+        fmin = min(np.abs(fk).min() for fk in f)
+        sv.step(1)
+        decided_f = np.concatenate([np.abs(fk) > 1e-5 for fk in f])
+        np.testing.assert_array_equal(xstar[s][decided_f], np.concatenate(x).astype(np.float32)[decided_f])
+        if fmin <= 1e-5:
+            continue   # a near-zero f: the minimiser, and so the step, is decided by rounding
+        for gpu, ref, gref in ((al[s], sv.st.alpha, grads["galpha"]), (b1[s], sv.st.beta1, grads["gbeta1"])):
+            ref, gref = hidden_concat(ref), hidden_concat(gref)
+            ok = (np.abs(gref) > 1e-4) | (gref == 0)
+            np.testing.assert_allclose(gpu[ok], ref[ok], rtol=1e-5, atol=1e-7)
+        for b in range(nslots):
+            ref = hidden_concat([None] + [sv.st.slots[k][b].beta for k in range(1, P.n)])
+            gref = hidden_concat([None] + [grads["gslots"][k][b] for k in range(1, P.n)])
+            ok = (np.abs(gref) > 1e-4) | (gref == 0)
+            np.testing.assert_allclose(sb[s, b][ok], ref[ok], rtol=1e-5, atol=1e-7)
