@@ -2,6 +2,7 @@
 // layout in device memory, the Big-M / Active Set and Saddle Point iteration loops (optionally
 // captured as CUDA graphs), bound evaluation and state access.
 #include <cmath>
+#include <cstdlib>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -259,8 +260,7 @@ struct Bump {
 
 // Team size for a pass with `units` reductions of about `fan` terms each: enough lanes to fill the
 // GPU (about 152 SMs x 1024 threads), at least 8 terms per lane, a power of two up to a warp.
-static int team_size(long long units, long long fan) {
-    const long long target = 152LL * 1024;
+static int team_size(long long units, long long fan, long long target) {
     int T = 1;
     while (T < 32 && units * T < target && fan / (2 * T) >= 8) T *= 2;
     return T;
@@ -269,6 +269,13 @@ static int team_size(long long units, long long fan) {
 static int make_team_segs(as_ctx* c) {
     DNet& D = c->net;
     const int n = D.n, S = D.S;
+    // threads a layer's segment aims for, row and col passes; measured on the Wide conv net with
+    // 9 subproblems (about a quarter of the threads the GPU holds at once does best: teams long
+    // enough to keep loads in flight, short enough not to replicate per-unit work);
+    // CB_TEAM_TARGET_ROW / CB_TEAM_TARGET_COL override them
+    long long target_row = 40000, target_col = 40000;
+    if (const char* e = getenv("CB_TEAM_TARGET_ROW")) target_row = atoll(e) > 0 ? atoll(e) : target_row;
+    if (const char* e = getenv("CB_TEAM_TARGET_COL")) target_col = atoll(e) > 0 ? atoll(e) : target_col;
     auto build = [&](TSegs& sg, int& blocks, bool col) -> int {
         const int nseg = col ? n : n - 1;
         sg.n = nseg;
@@ -280,7 +287,7 @@ static int make_team_segs(as_ctx* c) {
             if (L.kind == 0) fan = col ? L.n_out : L.n_in;
             else fan = col ? (long long)L.co * ((L.kh + L.st - 1) / L.st) * ((L.kw + L.st - 1) / L.st)
                            : (long long)L.ci * L.kh * L.kw;
-            int T = (col && k == n - 1) ? 1 : team_size(units, fan);
+            int T = (col && k == n - 1) ? 1 : team_size(units, fan, col ? target_col : target_row);
             // conv row-pass lanes split (channel, kernel row) pairs; col-pass lanes split channels
             const long long split = L.kind == 0 ? fan : (col ? L.co : (long long)L.ci * L.kh);
             while (T > 1 && T > split) T >>= 1;
