@@ -23,6 +23,8 @@
 
 namespace cb {
 
+#define CB_MAXTAP 9
+
 struct TSegs {
     int n;
     int layer[CB_MAXL];
@@ -76,15 +78,44 @@ __device__ __forceinline__ void col_walk_team(const DLayer& L, int j, int lane, 
     const int hw = L.hi * L.wi;
     const int c = j / hw, rem = j - c * hw;
     const int y = rem / L.wi, x = rem - y * L.wi;
-    // first kernel row (column) that reaches this input and its output row (column); further ones
-    // step by the stride in the kernel and by -1 in the output
+    // the taps of this input, found once: kernel rows (columns) step by the stride from the first
+    // one that reaches the input, output rows (columns) by -1; at most CB_MAXTAP taps are held in
+    // registers (kernels up to 3x3 at stride 1, 5x5 at stride 2, 7x7 at stride 3), else the walk
+    // falls back to the loops
     const int ky_s = (y + L.pd) % L.st, kx_s = (x + L.pd) % L.st;
     const int oy_s = (y + L.pd - ky_s) / L.st, ox_s = (x + L.pd - kx_s) / L.st;
     const size_t cstride = (size_t)L.ci * L.kh * L.kw;
     const float* Wb = L.W + (size_t)c * L.kh * L.kw;
+    const int plane = L.ho * L.wo;
+    int tw[CB_MAXTAP], ti[CB_MAXTAP], nt = 0;
+    bool fits = true;
+    for (int ky = ky_s, oy = oy_s; ky < L.kh && oy >= 0; ky += L.st, --oy) {
+        if (oy >= L.ho) continue;
+        for (int kx = kx_s, ox = ox_s; kx < L.kw && ox >= 0; kx += L.st, --ox) {
+            if (ox >= L.wo) continue;
+            if (nt < CB_MAXTAP) {
+#pragma unroll
+                for (int a = 0; a < CB_MAXTAP; ++a)
+                    if (a == nt) { tw[a] = ky * L.kw + kx; ti[a] = oy * L.wo + ox; }
+                ++nt;
+            } else {
+                fits = false;
+            }
+        }
+    }
+    if (fits) {
+        for (int co = lane; co < L.co; co += T) {
+            const float* Wco = Wb + co * cstride;
+            const int ib = co * plane;
+#pragma unroll
+            for (int a = 0; a < CB_MAXTAP; ++a)
+                if (a < nt) fn(ib + ti[a], __ldg(Wco + tw[a]));
+        }
+        return;
+    }
     for (int co = lane; co < L.co; co += T) {
         const float* Wco = Wb + co * cstride;
-        const int ib = co * L.ho * L.wo;
+        const int ib = co * plane;
         for (int ky = ky_s, oy = oy_s; ky < L.kh && oy >= 0; ky += L.st, --oy) {
             if (oy >= L.ho) continue;
             for (int kx = kx_s, ox = ox_s; kx < L.kw && ox >= 0; kx += L.st, --ox) {
@@ -518,14 +549,14 @@ __global__ void __launch_bounds__(CB_THREADS) k_sp_rowB_t(DNet net, DState st, D
             const float wx = w * r.x;
             a0 += wx;
             const bool I = w > 0.f ? (z >= r.y) : (w < 0.f ? (z >= r.z) : true);
-            if (I) {
-                A += wx;
-                Lam += w * (w >= 0.f ? r.w : uu);
-                any_in |= (w != 0.f) && (r.w != uu);
-            } else {
-                Mu += w * (w >= 0.f ? uu : r.w);
-                any_out = true;   // I = 0 only for a nonzero weight on a free input
-            }
+            const bool pos = w >= 0.f;
+            const float wL = w * (pos ? r.w : uu), wU = w * (pos ? uu : r.w);
+            // selects, not branches: the lanes of a warp disagree on I
+            A += I ? wx : 0.f;
+            Lam += I ? wL : 0.f;
+            Mu += I ? 0.f : wU;
+            any_in |= I && (w != 0.f) && (r.w != uu);
+            any_out |= !I;   // I = 0 only for a nonzero weight on a free input
         });
     }
     if (u.T > 1) {
