@@ -170,6 +170,23 @@ def slots_schedule(opt):
     return out
 
 
+def slowest_rank(values, dist, device):
+    """Element-wise maximum of per-rank timings over all ranks (the job is as slow as its slowest
+    replica); with one process the values themselves."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return list(values)
+    import torch
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def job_throughput(S_per_rank, world, ms_per_step):
+    """Whole-job subproblem-iterations per second: every rank bounds its own batch of S_per_rank
+    subproblems for iterations_per_step() iterations in ms_per_step (the slowest rank's)."""
+    return S_per_rank * iterations_per_step() * world / (ms_per_step / 1e3)
+
+
 def cpu_baseline(prob_name, seconds_budget=20.0):
     """Times the CPU oracle, single-threaded, on a bounded sample of the workload: one subproblem,
     a few Big-M then Active Set iterations (with the two first mask additions)."""
@@ -298,15 +315,9 @@ def main():
     bounds_as = out_h[0].numpy().copy()
     bounds_sp = out_h[1].numpy().copy()
 
-    ms = sum(times) / len(times)
-    ms_e2e = sum(e2e_times) / len(e2e_times)
-    if dist:
-        t = torch.tensor([ms, ms_e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, ms_e2e = t.tolist()
-    units = S * iterations_per_step() * world
-    value = units / (ms / 1e3)
-    e2e_value = units / (ms_e2e / 1e3)
+    ms, ms_e2e = slowest_rank([sum(times) / len(times), sum(e2e_times) / len(e2e_times)], dist, dev)
+    value = job_throughput(S, world, ms)
+    e2e_value = job_throughput(S, world, ms_e2e)
 
     # per-kernel device time for the roofline: one profiled step (CUDA events around each launch)
     as_p, sp_p = workload_options(binding, profile=1)
