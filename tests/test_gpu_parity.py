@@ -458,3 +458,76 @@ def test_full_size_wide_conv_lockstep_on_sampled_subproblems(it, nslots):
             gref = hidden_concat([None] + [grads["gslots"][k][b] for k in range(1, P.n)])
             ok = (np.abs(gref) > 1e-4) | (gref == 0)
             np.testing.assert_allclose(sb[s, b][ok], ref[ok], rtol=1e-5, atol=1e-7)
+
+
+def test_batched_subdomains_lockstep_with_splits_and_caps():
+    """BASELINE's batching form at full size: 4096 branch-and-bound subdomains of the Wide conv
+    net with random ReLU splits and per-subdomain caps of 1-5 masks, in the bench's graph launch
+    configuration. Interval bounds with the splits, and one Active Set iteration (an addition
+    iteration, so that capped subdomains must skip the new slot) from a drawn state, checked on
+    sampled subdomains of different caps."""
+    prob = synth.problem("wide_conv_bab", S=4096, seed=0)
+    caps = prob["caps"]
+    sample = sorted({int(np.argmax(caps == c)) for c in (1, 2, 3, 5)})
+    dense = nw.dense_layers(prob["net"])
+    sub = dict(prob)
+    for key in ("lo", "hi", "C", "splits"):
+        sub[key] = prob[key][sample]
+    Ps_s = nw.problems(sub, dense=dense)       # interval bounds with the splits, sampled only
+    kw = dict(bigm_iters=100, as_iters=400, omega=20, max_cuts=5)
+    ctx = binding.context_for(prob, binding.default_options(graph_chunk=25, **kw))
+    lh = ctx.get_state(binding.ST_LHAT).reshape(4096, -1)
+    uh = ctx.get_state(binding.ST_UHAT).reshape(4096, -1)
+    for q, s in enumerate(sample):
+        rl, ru = hidden_concat(Ps_s[q].lhat), hidden_concat(Ps_s[q].uhat)
+        assert (lh[s] <= rl + 1e-9 * (1 + np.abs(rl))).all() and (uh[s] >= ru - 1e-9 * (1 + np.abs(ru))).all()
+        assert (np.abs(lh[s] - rl) <= 4e-6 * (1 + np.abs(rl))).all()
+        assert (np.abs(uh[s] - ru) <= 4e-6 * (1 + np.abs(ru))).all()
+    # the oracle on the sampled subdomains, with the GPU's own interval bounds reproduced in FP64
+    # by the oracle above (rounded outward to float32 as both sides use them)
+    lh32, uh32 = oracle_bounds_f32(Ps_s)
+    widths = Ps_s[0].widths
+    Ps = [nw.Problem(prob["net"], prob["lo"][s], prob["hi"][s], prob["C"][s],
+                     bounds=(split_hidden(lh32[q].astype(np.float64), widths)[1:],
+                             split_hidden(uh32[q].astype(np.float64), widths)[1:]), dense=dense)
+          for q, s in enumerate(sample)]
+    it = 140   # t = 40: adds slot 4 (omega 20), which only caps of 5 accept
+    full_ps = [None] * 4096
+    for q, s in enumerate(sample):
+        full_ps[s] = Ps[q]
+    # install the same float32 bounds on the sampled subdomains of the GPU side
+    lh2, uh2 = lh.copy(), uh.copy()
+    lh2[sample], uh2[sample] = lh32, uh32
+    ctx = binding.context_for(prob, binding.default_options(graph_chunk=25, **kw), bounds=(lh2, uh2))
+    solvers = draw_state(full_ps, ctx, kw, it, 4, seed=41, subset=set(sample))
+    sbeta = ctx.get_state(binding.ST_SLOT_BETA).reshape(4096, ctx.cap, -1)
+    for s in range(4096):
+        sbeta[s, int(caps[s]):] = 0.0          # a subdomain never holds slots beyond its cap
+    ctx.set_state(binding.ST_SLOT_BETA, sbeta)
+    for s, sv in solvers.items():
+        sv.cap = int(caps[s])
+        # slots beyond a subdomain's cap were never added: drop them on the oracle side too
+        for k in range(1, sv.P.n):
+            del sv.st.slots[k][int(caps[s]):]
+    ctx.as_step(1)
+    al = ctx.get_state(binding.ST_ALPHA).reshape(4096, -1)
+    sb = ctx.get_state(binding.ST_SLOT_BETA).reshape(4096, ctx.cap, -1)
+    for s, sv in solvers.items():
+        P = sv.P
+        _, f, g, x, z = du.evaluate(P, sv.st)
+        grads = du.supergradient(P, sv.st, x, z)
+        if min(np.abs(fk).min() for fk in f) <= 1e-5:
+            continue
+        sv.step(1)
+        ref, gref = hidden_concat(sv.st.alpha), hidden_concat(grads["galpha"])
+        ok = (np.abs(gref) > 1e-4) | (gref == 0)
+        np.testing.assert_allclose(al[s][ok], ref[ok], rtol=1e-5, atol=1e-7)
+        nslots = len(sv.st.slots[1])
+        assert nslots == min(int(caps[s]), 5)
+        for b in range(min(nslots, 4)):
+            ref = hidden_concat([None] + [sv.st.slots[k][b].beta for k in range(1, P.n)])
+            gref = hidden_concat([None] + [grads["gslots"][k][b] for k in range(1, P.n)])
+            ok = (np.abs(gref) > 1e-4) | (gref == 0)
+            np.testing.assert_allclose(sb[s, b][ok], ref[ok], rtol=1e-5, atol=1e-7)
+        for b in range(nslots, ctx.cap):
+            assert (sb[s, b] == 0).all()      # capped: the slot stays empty
