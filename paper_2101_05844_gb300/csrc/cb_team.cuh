@@ -12,7 +12,7 @@
 // uses the per-row record the row pass leaves behind after its Adam step (one to three float4):
 //   rp[i]    = -(alpha_i - beta1_i) + sum_b z_b[i] beta_b[i]      (rows whose mask is all ones)
 //   bz[b][i] = (1 - z_b[i]) beta_b[i]
-// and the row pass reads one 8-byte record per input: x* and the snapshot bits with the fixed flag.
+// and the row pass reads one 8-byte record per input: x* and the slot masks for W > 0 and W < 0.
 // so that, with p_b = [x at its lower bound] or fixed, q_b = [x at its upper bound] or fixed,
 //   sum_i W_ij (-(alpha - beta1)_i + sum_b I_b(i,j) beta_b[i])
 //     = sum_i W_ij rp[i] + sum_b ( p_b sum_{W_ij > 0} W_ij bz[b][i] + q_b sum_{W_ij < 0} W_ij bz[b][i] ),
@@ -138,9 +138,21 @@ __device__ __forceinline__ void as_colA_body(const DNet& net, const DState& st, 
     const int m = k - 1;
     const Step sp = cb_step(st.ctr[0], sc, st.lr_tab);
     const size_t NT = net.NT, NH = net.NH, cap = net.cap;
-    float acc = 0.f, P[NS > 0 ? NS : 1], Q[NS > 0 ? NS : 1];
+    // the input's own slot bits select, per sign of W, which slots a pair feeds: W > 0 feeds the
+    // slots where x_j was at its lower bound (p), W < 0 those where it was at its upper bound (q);
+    // a fixed input feeds every slot
+    const int bo0 = sp.nadd_before & 1;
+    unsigned pm = 0u, qm = 0u;
+    if (valid) {
+        const size_t xo0 = (size_t)s * NT + L.in_off + j;
+        const unsigned xs0 = st.xsnap[bo0][xo0];
+        const unsigned fx = st.efix[xo0] ? 0xFFu : 0u;
+        pm = ((~xs0) & 0xFFu) | fx;
+        qm = xs0 | fx;
+    }
+    float acc = 0.f, P[NS > 0 ? NS : 1];
 #pragma unroll
-    for (int b = 0; b < NS; ++b) P[b] = Q[b] = 0.f;
+    for (int b = 0; b < NS; ++b) P[b] = 0.f;
     if (valid && k <= net.n - 1) {
         const int RS = net.RS;
         const float* ar = st.arec + ((size_t)s * NH + L.h_out) * RS;
@@ -152,21 +164,16 @@ __device__ __forceinline__ void as_colA_body(const DNet& net, const DState& st, 
             if (NS >= 4) { const float4 r1 = r[1]; v[4] = r1.x; v[5] = r1.y; v[6] = r1.z; v[7] = r1.w; }
             if (NS >= 8) { const float4 r2 = r[2]; v[8] = r2.x; v[9] = r2.y; v[10] = r2.z; v[11] = r2.w; }
             acc += w * v[0];
-            const float wp = fmaxf(w, 0.f), wn = fminf(w, 0.f);
+            const unsigned m = w > 0.f ? pm : qm;
 #pragma unroll
-            for (int b = 0; b < NS; ++b) {
-                P[b] += wp * v[1 + b];
-                Q[b] += wn * v[1 + b];
-            }
+            for (int b = 0; b < NS; ++b)
+                if (m & (1u << b)) P[b] += w * v[1 + b];
         });
     }
     if (T > 1) {
         acc = team_sum(acc, T);
 #pragma unroll
-        for (int b = 0; b < NS; ++b) {
-            P[b] = team_sum(P[b], T);
-            Q[b] = team_sum(Q[b], T);
-        }
+        for (int b = 0; b < NS; ++b) P[b] = team_sum(P[b], T);
     }
     if (!valid || lane != 0) return;
     const int cap_s = st.caps[s];
@@ -182,11 +189,7 @@ __device__ __forceinline__ void as_colA_body(const DNet& net, const DState& st, 
     if (k <= net.n - 1) {
         f = acc;
 #pragma unroll
-        for (int b = 0; b < NS; ++b) {
-            const bool up = (xs >> b) & 1u;
-            if (fixed || !up) f += P[b];
-            if (fixed || up) f += Q[b];
-        }
+        for (int b = 0; b < NS; ++b) f += P[b];
     } else {
         f = -net.Wout[(size_t)s * L.n_in + j];
     }
@@ -224,7 +227,10 @@ __device__ __forceinline__ void as_colA_body(const DNet& net, const DState& st, 
         xs_new = xs | ((add && up) ? (1u << sp.b_new) : 0u);
         st.xsnap[bo ^ 1][xo] = (uint8_t)xs_new;
     }
-    st.xrec[xo] = make_float2(xv, __uint_as_float(xs_new | (fixed ? 0x100u : 0u)));
+    // row-pass record: x* and the slot masks for W > 0 (bits 0-7) and W < 0 (bits 8-15)
+    const unsigned fxm = fixed ? 0xFFu : 0u;
+    const unsigned mpos = ((~xs_new) & 0xFFu) | fxm, mneg = (xs_new & 0xFFu) | fxm;
+    st.xrec[xo] = make_float2(xv, __uint_as_float(mpos | (mneg << 8)));
 }
 
 __device__ __forceinline__ int tseg_of(const TSegs& sg, int blk) {
@@ -291,13 +297,11 @@ __device__ __forceinline__ void as_rowB_body(const DNet& net, const DState& st, 
             const float wx = __fmul_rn(w, r.x);
             acc0 = __fadd_rn(acc0, wx);
             if (NS > 0) {
-                const unsigned fl = __float_as_uint(r.y);
-                const unsigned xs = fl & 0xFFu;
-                const unsigned f = (fl & 0x100u) ? 0xFFu : 0u;
-                const unsigned msk = w > 0.f ? ((~xs) | f) : (w < 0.f ? (xs | f) : 0xFFu);
+                // the input's mask for the sign of W (a zero weight adds a zero product either way)
+                const unsigned msk = (__float_as_uint(r.y) >> (w > 0.f ? 0 : 8)) & 0xFFu;
 #pragma unroll
                 for (int b = 0; b < NS; ++b)
-                    if ((msk >> b) & 1u) acc[b] = __fadd_rn(acc[b], wx);
+                    if (msk & (1u << b)) acc[b] = __fadd_rn(acc[b], wx);
                 if (ADD && newb >= 0) {
                     const float l = lo[j], u = hi[j];
                     if (((zs | msk) >> (newb & 7)) & 1u) lamN = __fadd_rn(lamN, __fmul_rn(w, w >= 0.f ? l : u));
