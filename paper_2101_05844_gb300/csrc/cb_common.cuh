@@ -21,12 +21,27 @@ struct DLayer {
     const float* b;        // per output neuron [n_out]
     int in_off, out_off;   // offsets of the input / output neuron layer in [NT] vectors
     int h_in, h_out;       // offsets in [NH] hidden vectors (-1 when not a hidden layer)
+    // Active Set walks (hidden-output layers). Tap lists {offset in floats, weight bits} per group,
+    // the group's positive weights first: taps [grp[2g], grp[2g+1]) have W > 0 and
+    // [grp[2g+1], grp[2g+2]) have W < 0 (zero weights are left out).
+    //  row pass: group = output row (linear) or output channel (conv); offsets index the input
+    //            records of this layer in positions (zero-padded input plane for conv)
+    //  col pass: group = input (linear) or (input channel, stride phase y, stride phase x) (conv);
+    //            offsets index the output records (output plane with a zero halo for conv)
+    const int2* rtap;
+    const int* rgrp;
+    const int2* ctap;
+    const int* cgrp;
+    int xo, ao;            // offsets (floats) of this layer's input / output records in a subproblem
+    int Hp, Wp;            // padded input plane (conv): in + 2 pad
+    int Hpo, Wpo, hl, wl;  // output plane with halo (conv): rows hl .. hl + ho - 1 are the outputs
 };
 
 struct DNet {
     int n;                 // affine layers; hidden layers k = 1..n-1
     int S, NT, NH, cap;    // subproblems, all neurons (layers 0..n-1), hidden neurons, max slots
-    int RS;                // floats per Active Set row record (1 + cap rounded up to 4)
+    int RS;                // floats per Active Set record chunk (1 + cap rounded up to 4)
+    int XT, AT;            // floats of input / output records per subproblem (all layers)
     DLayer L[CB_MAXL];
     const float* Wout;     // [S][n_{n-1}] property-folded output row
     const float* bout;     // [S]
@@ -50,9 +65,11 @@ struct DState {
     float *alpha, *beta0, *beta1;
     float *ma, *va, *m0, *v0, *m1, *v1;
     float *bs, *ms, *vs, *lam, *kap; // slots
-    float *arec;                     // [S][NH][RS] row record: -(alpha - beta1) + sum_b z_b beta_b,
-                                     // then (1 - z_b) beta_b per slot (RS = 1 + cap rounded to 4)
-    float2 *xrec;                    // [S][NT] input record: {x*, snapshot bits | fixed << 8}
+    float *arec;                     // [S][AT] output records of each layer (RS floats per position):
+                                     // -(alpha - beta1) + sum_b z_b beta_b, then (1 - z_b) beta_b
+    float *xin;                      // [S][XT] input records of each layer, one float2 per position:
+                                     // {x*, p_b bits | q_b bits << 8}
+    float *lz;                       // [S][NH] sum_j W_ij Lcheck_ij (the all-ones mask's lambda)
     uint8_t* efix;                   // [S][NT] l == u
     float *xval;                     // x* of the last evaluation [S][NT]
     float *fval;                     // f of the last evaluation [S][NT]

@@ -131,65 +131,138 @@ __device__ __forceinline__ float team_sum(float v, int T) {
     return v;
 }
 
+// ---------------------------------------------------------------- Active Set walks
+// Group and base position of row-pass unit i (output neuron i of layer L).
+__device__ __forceinline__ void row_group(const DLayer& L, int i, int& g, int& base) {
+    if (L.kind == 0) {
+        g = i;
+        base = 0;
+        return;
+    }
+    const int hw = L.ho * L.wo;
+    const int co = i / hw, rem = i - co * hw;
+    const int oy = rem / L.wo, ox = rem - oy * L.wo;
+    g = co;
+    base = oy * L.st * L.Wp + ox * L.st;
+}
+
+// Group and base position of col-pass unit j (input neuron j of layer L).
+__device__ __forceinline__ void col_group(const DLayer& L, int j, int& g, int& base) {
+    if (L.kind == 0) {
+        g = j;
+        base = 0;
+        return;
+    }
+    const int hw = L.hi * L.wi;
+    const int c = j / hw, rem = j - c * hw;
+    const int y = rem / L.wi, x = rem - y * L.wi;
+    const int ty = y + L.pd, tx = x + L.pd;
+    const int Y0 = ty / L.st, X0 = tx / L.st;
+    const int py = ty - Y0 * L.st, px = tx - X0 * L.st;
+    g = (c * L.st + py) * L.st + px;
+    base = (Y0 + L.hl) * L.Wpo + X0 + L.wl;
+}
+
+// Record position of input neuron j (row-pass input records) and output neuron i (col-pass
+// output records) of layer L.
+__device__ __forceinline__ int xin_pos(const DLayer& L, int j) {
+    if (L.kind == 0) return j;
+    const int hw = L.hi * L.wi;
+    const int c = j / hw, rem = j - c * hw;
+    const int y = rem / L.wi, x = rem - y * L.wi;
+    return (c * L.Hp + y + L.pd) * L.Wp + x + L.pd;
+}
+__device__ __forceinline__ int arec_pos(const DLayer& L, int i) {
+    if (L.kind == 0) return i;
+    const int hw = L.ho * L.wo;
+    const int co = i / hw, rem = i - co * hw;
+    const int oy = rem / L.wo, ox = rem - oy * L.wo;
+    return (co * L.Hpo + oy + L.hl) * L.Wpo + ox + L.wl;
+}
+
+// The first NV floats of a 16-byte aligned record.
+template <int NV>
+__device__ __forceinline__ void load_rec(const float* p, float (&v)[12]) {
+    const float4* q = reinterpret_cast<const float4*>(p);
+    const float4 a = q[0];
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    if (NV > 4) { const float4 b = q[1]; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w; }
+    if (NV > 8) { const float4 c = q[2]; v[8] = c.x; v[9] = c.y; v[10] = c.z; v[11] = c.w; }
+}
+
 // ---------------------------------------------------------------- Active Set col pass (phase A)
+// The masked backward product of eq. (6) for input j, regrouped by the sign of W: at binary
+// iterates eq. (3) gives I_b(i, j) = 1 on rows with z_b[i] = 1 (their beta is in the record's
+// first entry) and otherwise I_b(i, j) = p_b(j) where W_ij > 0, q_b(j) where W_ij < 0, with
+// p_b = [x_j at its lower bound when slot b was added] or fixed, q_b = [at its upper bound] or
+// fixed. Walking the positive taps, then the negative ones, the lanes accumulate, per slot,
+//   Pp_b = sum_{W_ij > 0} W_ij bz_b[i],  Pn_b = sum_{W_ij < 0} W_ij bz_b[i]
+// with no per-pair mask work; the input's own bits pick p_b Pp_b + q_b Pn_b at the end.
 template <int NS>
 __device__ __forceinline__ void as_colA_body(const DNet& net, const DState& st, const DSched& sc, const DLayer& L,
                                              int k, bool valid, int s, int j, int lane, int T, int mode) {
     const int m = k - 1;
     const Step sp = cb_step(st.ctr[0], sc, st.lr_tab);
     const size_t NT = net.NT, NH = net.NH, cap = net.cap;
-    // the input's own slot bits select, per sign of W, which slots a pair feeds: W > 0 feeds the
-    // slots where x_j was at its lower bound (p), W < 0 those where it was at its upper bound (q);
-    // a fixed input feeds every slot
-    const int bo0 = sp.nadd_before & 1;
-    unsigned pm = 0u, qm = 0u;
-    if (valid) {
-        const size_t xo0 = (size_t)s * NT + L.in_off + j;
-        const unsigned xs0 = st.xsnap[bo0][xo0];
-        const unsigned fx = st.efix[xo0] ? 0xFFu : 0u;
-        pm = ((~xs0) & 0xFFu) | fx;
-        qm = xs0 | fx;
-    }
-    float acc = 0.f, P[NS > 0 ? NS : 1];
+    const int RS = net.RS;
+    float acc = 0.f, Pp[NS > 0 ? NS : 1], Pn[NS > 0 ? NS : 1];
 #pragma unroll
-    for (int b = 0; b < NS; ++b) P[b] = 0.f;
+    for (int b = 0; b < NS; ++b) Pp[b] = Pn[b] = 0.f;
     if (valid && k <= net.n - 1) {
-        const int RS = net.RS;
-        const float* ar = st.arec + ((size_t)s * NH + L.h_out) * RS;
-        col_walk_team(L, j, lane, T, [&](int i, float w) {
-            const float4* r = reinterpret_cast<const float4*>(ar + (size_t)i * RS);
+        int g, base;
+        col_group(L, j, g, base);
+        const float* ar = st.arec + (size_t)s * net.AT + L.ao + (size_t)base * RS;
+        const int t0 = L.cgrp[2 * g], t1 = L.cgrp[2 * g + 1], t2 = L.cgrp[2 * g + 2];
+#pragma unroll 2
+        for (int t = t0 + lane; t < t1; t += T) {
+            const int2 e = L.ctap[t];
+            const float w = __int_as_float(e.y);
             float v[12];
-            const float4 r0 = r[0];
-            v[0] = r0.x; v[1] = r0.y; v[2] = r0.z; v[3] = r0.w;
-            if (NS >= 4) { const float4 r1 = r[1]; v[4] = r1.x; v[5] = r1.y; v[6] = r1.z; v[7] = r1.w; }
-            if (NS >= 8) { const float4 r2 = r[2]; v[8] = r2.x; v[9] = r2.y; v[10] = r2.z; v[11] = r2.w; }
-            acc += w * v[0];
-            const unsigned m = w > 0.f ? pm : qm;
+            load_rec<1 + NS>(ar + e.x, v);
+            acc = fmaf(w, v[0], acc);
 #pragma unroll
-            for (int b = 0; b < NS; ++b)
-                if (m & (1u << b)) P[b] += w * v[1 + b];
-        });
+            for (int b = 0; b < NS; ++b) Pp[b] = fmaf(w, v[1 + b], Pp[b]);
+        }
+#pragma unroll 2
+        for (int t = t1 + lane; t < t2; t += T) {
+            const int2 e = L.ctap[t];
+            const float w = __int_as_float(e.y);
+            float v[12];
+            load_rec<1 + NS>(ar + e.x, v);
+            acc = fmaf(w, v[0], acc);
+#pragma unroll
+            for (int b = 0; b < NS; ++b) Pn[b] = fmaf(w, v[1 + b], Pn[b]);
+        }
     }
     if (T > 1) {
         acc = team_sum(acc, T);
 #pragma unroll
-        for (int b = 0; b < NS; ++b) P[b] = team_sum(P[b], T);
+        for (int b = 0; b < NS; ++b) {
+            Pp[b] = team_sum(Pp[b], T);
+            Pn[b] = team_sum(Pn[b], T);
+        }
     }
     if (!valid || lane != 0) return;
+    const bool want_terms = mode != 2;
     const int cap_s = st.caps[s];
     const int nsl = min(sp.nadd_before, cap_s);
     const int bo = sp.nadd_before & 1;
-    const bool add_iter = (mode == 0) && sp.b_new >= 0;
+    const bool add_iter = (mode != 1) && sp.b_new >= 0;
     const bool add = add_iter && sp.b_new < cap_s;
     const size_t xo = (size_t)s * NT + L.in_off + j;
     const float lo = st.lo[xo], hi = st.hi[xo];
     const unsigned xs = st.xsnap[bo][xo];
     const bool fixed = st.efix[xo];
+    const unsigned fxm = fixed ? 0xFFu : 0u;
     float f;
     if (k <= net.n - 1) {
+        const unsigned pm = ((~xs) & 0xFFu) | fxm, qm = xs | fxm;
         f = acc;
 #pragma unroll
-        for (int b = 0; b < NS; ++b) f += P[b];
+        for (int b = 0; b < NS; ++b) {
+            if ((pm >> b) & 1u) f += Pp[b];
+            if ((qm >> b) & 1u) f += Pn[b];
+        }
     } else {
         f = -net.Wout[(size_t)s * L.n_in + j];
     }
@@ -203,14 +276,16 @@ __device__ __forceinline__ void as_colA_body(const DNet& net, const DState& st, 
             const float bb = st.bs[hs + (size_t)b * NH];
             sb += bb;
             gk += bb * st.kap[hs + (size_t)b * NH];
-            cterm += (double)bb * st.lam[hs + (size_t)b * NH];
+            if (want_terms) cterm += (double)bb * st.lam[hs + (size_t)b * NH];
         }
         f += st.alpha[h] - st.beta0[h] - st.beta1[h] - sb;
         const bool z = gk >= 0.f;
         st.zcur[h] = z;
-        const float bm = net.L[m - 1].b[j];
-        term = (double)bm * st.alpha[h] + (double)st.beta1[h] * ((double)st.lhat[h] - bm) + cterm -
-               (z ? (double)gk : 0.0);
+        if (want_terms) {
+            const float bm = net.L[m - 1].b[j];
+            term = (double)bm * st.alpha[h] + (double)st.beta1[h] * ((double)st.lhat[h] - bm) + cterm -
+                   (z ? (double)gk : 0.0);
+        }
         if (add_iter) {
             const unsigned zs_old = st.zsnap[bo][h];
             st.zsnap[bo ^ 1][h] = (uint8_t)(zs_old | ((add && z) ? (1u << sp.b_new) : 0u));
@@ -220,17 +295,18 @@ __device__ __forceinline__ void as_colA_body(const DNet& net, const DState& st, 
     const float xv = up ? hi : lo;
     st.xval[xo] = xv;
     st.fval[xo] = f;
-    term -= (double)f * xv;
-    st.terms[xo] = term;
+    if (want_terms) st.terms[xo] = term - (double)f * xv;
     unsigned xs_new = xs;
     if (add_iter) {
         xs_new = xs | ((add && up) ? (1u << sp.b_new) : 0u);
         st.xsnap[bo ^ 1][xo] = (uint8_t)xs_new;
     }
-    // row-pass record: x* and the slot masks for W > 0 (bits 0-7) and W < 0 (bits 8-15)
-    const unsigned fxm = fixed ? 0xFFu : 0u;
-    const unsigned mpos = ((~xs_new) & 0xFFu) | fxm, mneg = (xs_new & 0xFFu) | fxm;
-    st.xrec[xo] = make_float2(xv, __uint_as_float(mpos | (mneg << 8)));
+    if (k <= net.n - 1) {
+        // row-pass input record: x* and the slot masks p_b (bits 0-7) and q_b (bits 8-15)
+        const unsigned mpos = ((~xs_new) & 0xFFu) | fxm, mneg = (xs_new & 0xFFu) | fxm;
+        reinterpret_cast<float2*>(st.xin + (size_t)s * net.XT + L.xo)[xin_pos(L, j)] =
+            make_float2(xv, __uint_as_float(mpos | (mneg << 8)));
+    }
 }
 
 __device__ __forceinline__ int tseg_of(const TSegs& sg, int blk) {
@@ -268,56 +344,64 @@ __global__ void __launch_bounds__(CB_THREADS) k_as_colA_t(DNet net, DState st, D
 }
 
 // ---------------------------------------------------------------- Active Set row pass (phase B)
-// Row pass over hidden layers: W x*, the masked products (W o I_b) x* of every slot and, on
-// addition iterations, lambda and kappa of the new slot; the supergradient (eq. 9), Adam steps and
-// projection (Alg. 1); then the per-row sums rp and bz for the next col pass.
+// Row pass over hidden layers: W x* and the masked products (W o I_b) x* of every slot, walking
+// the positive taps, whose pairs feed the slots with p_b(j) set, then the negative taps (q_b(j));
+// the supergradient (eq. 9), Adam steps and projection (Alg. 1); then the per-row sums rp and bz
+// for the next col pass.
+//
+// A slot added at this iteration takes the oracle mask of the current point, where Lcheck_ij = x_j
+// on every selected pair of a row with z = 0 and Ucheck_ij = x_j on every other pair, so that
+// lambda = (W o I) x* and kappa = W x* + b there; on rows with z = 1 the mask is all ones and
+// lambda = sum_j W_ij Lcheck_ij (precomputed per batch). Taking lambda from the same float32 sum
+// as the masked product makes the two cancel exactly in the new slot's supergradient, as they do
+// in exact arithmetic.
 template <int NS, bool ADD>
 __device__ __forceinline__ void as_rowB_body(const DNet& net, const DState& st, const DSched& sc, const DLayer& L,
                                              bool valid, int s, int i, int lane, int T, const Step& sp, int it) {
     const size_t NT = net.NT, NH = net.NH, cap = net.cap;
+    const int RS = net.RS;
     const int cap_s = valid ? st.caps[s] : 0;
     const int newb = (ADD && sp.b_new < cap_s) ? sp.b_new : -1;
     const int bn = (sp.nadd_before + (sp.b_new >= 0 ? 1 : 0)) & 1;
     const size_t h = (size_t)s * NH + L.h_out + i;
     const unsigned zs = valid ? st.zsnap[bn][h] : 0u;
-    float acc0 = 0.f, lamN = 0.f, muN = 0.f;
+    float acc0 = 0.f;
     float acc[NS > 0 ? NS : 1];
 #pragma unroll
     for (int b = 0; b < NS; ++b) acc[b] = 0.f;
     if (valid) {
-        const size_t ib = (size_t)s * NT + L.in_off;
-        const float2* xr = st.xrec + ib;
-        const float* lo = st.lo + ib;
-        const float* hi = st.hi + ib;
-        // products rounded once and added without contraction: where the mask selects exactly the
-        // inputs at their interval end (Lcheck = x), the masked product and lambda of a new slot
-        // then cancel exactly in the supergradient, as they do in exact arithmetic
-        row_walk_team(L, i, lane, T, [&](int j, float w) {
-            const float2 r = xr[j];
-            const float wx = __fmul_rn(w, r.x);
-            acc0 = __fadd_rn(acc0, wx);
-            if (NS > 0) {
-                // the input's mask for the sign of W (a zero weight adds a zero product either way)
-                const unsigned msk = (__float_as_uint(r.y) >> (w > 0.f ? 0 : 8)) & 0xFFu;
+        int g, base;
+        row_group(L, i, g, base);
+        const float2* xb = reinterpret_cast<const float2*>(st.xin + (size_t)s * net.XT + L.xo) + base;
+        const int t0 = L.rgrp[2 * g], t1 = L.rgrp[2 * g + 1], t2 = L.rgrp[2 * g + 2];
+        // positive taps take the slot masks p_b (bits 0-7), negative taps q_b (bits 8-15)
+#pragma unroll 4
+        for (int t = t0 + lane; t < t1; t += T) {
+            const int2 e = L.rtap[t];
+            const float2 r = xb[e.x];
+            const float wx = __int_as_float(e.y) * r.x;
+            const unsigned msk = __float_as_uint(r.y);
+            acc0 += wx;
 #pragma unroll
-                for (int b = 0; b < NS; ++b)
-                    if (msk & (1u << b)) acc[b] = __fadd_rn(acc[b], wx);
-                if (ADD && newb >= 0) {
-                    const float l = lo[j], u = hi[j];
-                    if (((zs | msk) >> (newb & 7)) & 1u) lamN = __fadd_rn(lamN, __fmul_rn(w, w >= 0.f ? l : u));
-                    else muN = __fadd_rn(muN, __fmul_rn(w, w >= 0.f ? u : l));
-                }
-            }
-        });
+            for (int b = 0; b < NS; ++b)
+                if ((msk >> b) & 1u) acc[b] += wx;
+        }
+#pragma unroll 4
+        for (int t = t1 + lane; t < t2; t += T) {
+            const int2 e = L.rtap[t];
+            const float2 r = xb[e.x];
+            const float wx = __int_as_float(e.y) * r.x;
+            const unsigned msk = __float_as_uint(r.y);
+            acc0 += wx;
+#pragma unroll
+            for (int b = 0; b < NS; ++b)
+                if ((msk >> (8 + b)) & 1u) acc[b] += wx;
+        }
     }
     if (T > 1) {
         acc0 = team_sum(acc0, T);
 #pragma unroll
         for (int b = 0; b < NS; ++b) acc[b] = team_sum(acc[b], T);
-        if (ADD) {
-            lamN = team_sum(lamN, T);
-            muN = team_sum(muN, T);
-        }
     }
     // epilogue: the team's lanes share the Adam updates (variable v = alpha, beta_0, beta_1, then
     // the slots), each lane handling v = lane, lane + T, ...
@@ -329,7 +413,7 @@ __device__ __forceinline__ void as_rowB_body(const DNet& net, const DState& st, 
         const float z = st.zcur[h] ? 1.f : 0.f;
         const float xhat = acc0 + bi;
         const size_t hs0 = (size_t)s * cap * NH + L.h_out + i;
-        float* ar = st.arec + h * net.RS;
+        float* ar = st.arec + (size_t)s * net.AT + L.ao + (size_t)arec_pos(L, i) * RS;
         for (int v = lane; v < 3 + NS; v += T) {
             if (v < 3) {
                 float* th = v == 0 ? st.alpha : (v == 1 ? st.beta0 : st.beta1);
@@ -348,20 +432,21 @@ __device__ __forceinline__ void as_rowB_body(const DNet& net, const DState& st, 
                 if (b >= nsl) { ar[1 + b] = 0.f; continue; }
                 const size_t hs = hs0 + (size_t)b * NH;
                 float lam, kap;
+                float ab = 0.f;
+#pragma unroll
+                for (int bb = 0; bb < NS; ++bb)
+                    if (bb == b) ab = acc[bb];
+                const bool zb = (zs >> b) & 1u;
                 if (ADD && b == newb) {
-                    lam = lamN;
-                    kap = lamN + muN + bi;
+                    const float lzh = st.lz[h];
+                    lam = zb ? lzh : ab;
+                    kap = zb ? lzh + bi : xhat;
                     st.lam[hs] = lam;
                     st.kap[hs] = kap;
                 } else {
                     lam = st.lam[hs];
                     kap = st.kap[hs];
                 }
-                float ab = 0.f;
-#pragma unroll
-                for (int bb = 0; bb < NS; ++bb)
-                    if (bb == b) ab = acc[bb];
-                const bool zb = (zs >> b) & 1u;
                 const float prod = zb ? acc0 : ab;
                 const float gb = x - prod + lam * (1.f - z) - z * (kap - lam);
                 const int sstep = sp.t - cb_slot_added_at(b, sc) + 1;
@@ -375,7 +460,7 @@ __device__ __forceinline__ void as_rowB_body(const DNet& net, const DState& st, 
         }
     }
     if (T > 1) contrib = team_sum(contrib, T);
-    if (valid && lane == 0) st.arec[h * net.RS] = contrib;
+    if (valid && lane == 0) st.arec[(size_t)s * net.AT + L.ao + (size_t)arec_pos(L, i) * RS] = contrib;
 }
 
 __global__ void __launch_bounds__(CB_THREADS) k_as_rowB_t(DNet net, DState st, DSched sc, TSegs sg) {
@@ -426,9 +511,12 @@ __global__ void k_rowprep(DNet net, DState st, DSched sc) {
     const int bo = sp.nadd_before & 1;
     for (size_t u = blockIdx.x * (size_t)blockDim.x + threadIdx.x; u < n; u += (size_t)gridDim.x * blockDim.x) {
         const int s = (int)(u / net.NH), hh = (int)(u - (size_t)s * net.NH);
+        int li = 0;
+        while (li + 2 < net.n && hh >= net.L[li + 1].h_out) ++li;
+        const DLayer& L = net.L[li];
         const int nsl = min(sp.nadd_before, st.caps[s]);
         const unsigned zs = st.zsnap[bo][u];
-        float* rec = st.arec + u * net.RS;
+        float* rec = st.arec + (size_t)s * net.AT + L.ao + (size_t)arec_pos(L, hh - L.h_out) * net.RS;
         float r = -(st.alpha[u] - st.beta1[u]);
         for (int b = 0; b < net.RS - 1; ++b) {
             float bv = 0.f;
@@ -443,6 +531,22 @@ __global__ void k_rowprep(DNet net, DState st, DSched sc) {
         }
         rec[0] = r;
     }
+}
+
+// lz[s][i] = sum_j W_ij Lcheck_ij (Lcheck = l_j where W_ij >= 0, u_j where W_ij < 0): lambda of
+// the all-ones mask, taken by Active Set slots added on rows with z = 1. One warp per row;
+// FP64 accumulation rounded to nearest.
+__global__ void k_lz(DNet net, DState st, int li) {
+    const DLayer& L = net.L[li];
+    const int warp = (blockIdx.x * CB_THREADS + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= net.S * L.n_out) return;
+    const int s = warp / L.n_out, i = warp - s * L.n_out;
+    const float* lo = st.lo + (size_t)s * net.NT + L.in_off;
+    const float* hi = st.hi + (size_t)s * net.NT + L.in_off;
+    double a = 0.0;
+    row_walk(L, i, lane, [&](int j, float w) { a += (double)w * (w >= 0.f ? lo[j] : hi[j]); });
+    a = warp_sum(a);
+    if (lane == 0) st.lz[(size_t)s * net.NH + L.h_out + i] = (float)a;
 }
 
 // efix[s][j] = (l == u): fixed inputs, whose mask bit is 1 for every slot.

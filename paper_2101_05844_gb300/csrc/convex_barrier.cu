@@ -258,6 +258,109 @@ struct Bump {
     }
 };
 
+// Sign-partitioned tap lists and record layouts of the Active Set walks (DLayer fields) for the
+// hidden-output layers. Row-pass taps index the input records in positions (one float2 each),
+// col-pass taps the output records in floats (RS per position).
+static int build_walks(as_ctx* c, const std::vector<std::vector<float>>& Wh) {
+    DNet& D = c->net;
+    const int RS = D.RS;
+    int xo = 0, ao = 0;
+    for (int k = 0; k + 1 < D.n; ++k) {
+        DLayer& L = D.L[k];
+        const std::vector<float>& W = Wh[k];
+        std::vector<int2> rt, ct, pos, neg;
+        std::vector<int> rg, cg;
+        auto close_group = [&](std::vector<int2>& taps, std::vector<int>& grp) {
+            grp.push_back((int)taps.size());
+            taps.insert(taps.end(), pos.begin(), pos.end());
+            grp.push_back((int)taps.size());
+            taps.insert(taps.end(), neg.begin(), neg.end());
+            pos.clear();
+            neg.clear();
+        };
+        auto add = [&](int off, float w) {
+            int2 e;
+            e.x = off;
+            std::memcpy(&e.y, &w, sizeof w);
+            if (w > 0.f) pos.push_back(e);
+            else if (w < 0.f) neg.push_back(e);
+        };
+        int xpos, apos;
+        if (L.kind == 0) {
+            L.Hp = L.Wp = L.Hpo = L.Wpo = 1;
+            L.hl = L.wl = 0;
+            for (int i = 0; i < L.n_out; ++i) {
+                for (int j = 0; j < L.n_in; ++j) add(j, W[(size_t)i * L.n_in + j]);
+                close_group(rt, rg);
+            }
+            for (int j = 0; j < L.n_in; ++j) {
+                for (int i = 0; i < L.n_out; ++i) add(i * RS, W[(size_t)i * L.n_in + j]);
+                close_group(ct, cg);
+            }
+            xpos = L.n_in;
+            apos = L.n_out;
+        } else {
+            L.Hp = L.hi + 2 * L.pd;
+            L.Wp = L.wi + 2 * L.pd;
+            // col pass: input (y, x) of stride phase (py, px) reaches outputs (Y0 - dky, X0 - dkx),
+            // Y0 = (y + pad) / stride, kernel row py + stride dky; the halo holds the out-of-range ones
+            const int nky = (L.kh + L.st - 1) / L.st, nkx = (L.kw + L.st - 1) / L.st;
+            const int maxY0 = (L.hi - 1 + L.pd) / L.st, maxX0 = (L.wi - 1 + L.pd) / L.st;
+            L.hl = nky - 1;
+            L.wl = nkx - 1;
+            L.Hpo = L.hl + std::max(L.ho, maxY0 + 1);
+            L.Wpo = L.wl + std::max(L.wo, maxX0 + 1);
+            const size_t kk = (size_t)L.kh * L.kw;
+            for (int co = 0; co < L.co; ++co) {
+                for (int ci = 0; ci < L.ci; ++ci)
+                    for (int ky = 0; ky < L.kh; ++ky)
+                        for (int kx = 0; kx < L.kw; ++kx)
+                            add((ci * L.Hp + ky) * L.Wp + kx,
+                                W[((size_t)co * L.ci + ci) * kk + ky * L.kw + kx]);
+                close_group(rt, rg);
+            }
+            for (int ci = 0; ci < L.ci; ++ci)
+                for (int py = 0; py < L.st; ++py)
+                    for (int px = 0; px < L.st; ++px) {
+                        for (int co = 0; co < L.co; ++co)
+                            for (int ky = py, dky = 0; ky < L.kh; ky += L.st, ++dky)
+                                for (int kx = px, dkx = 0; kx < L.kw; kx += L.st, ++dkx)
+                                    add((co * L.Hpo * L.Wpo - dky * L.Wpo - dkx) * RS,
+                                        W[((size_t)co * L.ci + ci) * kk + ky * L.kw + kx]);
+                        close_group(ct, cg);
+                    }
+            xpos = L.ci * L.Hp * L.Wp;
+            apos = L.co * L.Hpo * L.Wpo;
+        }
+        rg.push_back((int)rt.size());
+        cg.push_back((int)ct.size());
+        int2 *drt, *dct;
+        int *drg, *dcg;
+        TRY(dalloc(c, &drt, rt.size()));
+        TRY(dalloc(c, &dct, ct.size()));
+        TRY(dalloc(c, &drg, rg.size()));
+        TRY(dalloc(c, &dcg, cg.size()));
+        CUDA_TRY(c, cudaMemcpy(drt, rt.data(), rt.size() * sizeof(int2), cudaMemcpyHostToDevice));
+        CUDA_TRY(c, cudaMemcpy(dct, ct.data(), ct.size() * sizeof(int2), cudaMemcpyHostToDevice));
+        CUDA_TRY(c, cudaMemcpy(drg, rg.data(), rg.size() * sizeof(int), cudaMemcpyHostToDevice));
+        CUDA_TRY(c, cudaMemcpy(dcg, cg.data(), cg.size() * sizeof(int), cudaMemcpyHostToDevice));
+        L.rtap = drt;
+        L.rgrp = drg;
+        L.ctap = dct;
+        L.cgrp = dcg;
+        L.xo = xo;
+        L.ao = ao;
+        const long long xn = (long long)xo + (long long)xpos * 2, an = (long long)ao + (long long)apos * RS;
+        if (xn > INT32_MAX / 2 || an > INT32_MAX / 2)
+            return fail(c, AS_ERR_SHAPE, "layer %d: record offsets exceed 32 bits", k + 1);
+        xo = (int)xn;
+        ao = (int)an;
+    }
+    D.XT = xo;
+    D.AT = ao;
+    return AS_OK;
+}
+
 // Team size for a pass with `units` reductions of about `fan` terms each: enough lanes to fill the
 // GPU (about 152 SMs x 1024 threads), at least 8 terms per lane, a power of two up to a warp.
 static int team_size(long long units, long long fan, long long target) {
@@ -333,7 +436,8 @@ static int alloc_state(as_ctx* c) {
         float** zs[] = {&st.bs, &st.ms, &st.vs, &st.lam, &st.kap};
         for (float** p : zs) *p = z.take<float>(SL);
         st.P = z.take<float>(NTS);
-        st.arec = z.take<float>(NHS * D.RS);
+        st.arec = z.take<float>(S * (size_t)D.AT);
+        st.xin = z.take<float>(S * (size_t)D.XT);
         for (int q = 0; q < 2; ++q) {
             st.xsnap[q] = z.take<uint8_t>(NTS);
             st.zsnap[q] = z.take<uint8_t>(NHS);
@@ -356,7 +460,7 @@ static int alloc_state(as_ctx* c) {
             st.spz[q] = o.take<float>(NHS);
         }
         st.zcur = o.take<uint8_t>(NHS);
-        st.xrec = o.take<float2>(NTS);
+        st.lz = o.take<float>(NHS);
         st.efix = o.take<uint8_t>(NTS);
         st.arow = o.take<float>(NHS);
         st.inrec = o.take<float4>(NTS);
@@ -463,7 +567,14 @@ static int load_batch(as_ctx* c, const float* x_lo, const float* x_hi, const flo
     }
     k_efix<<<grid_for((size_t)S * NT), CB_THREADS, 0, s>>>(D, st);
     c->launches++;
-    return check_launch(c, "k_efix");
+    TRY(check_launch(c, "k_efix"));
+    for (int k = 0; k < n - 1; ++k) {
+        const long long warps = (long long)S * D.L[k].n_out;
+        k_lz<<<(int)((warps + CB_WARPS - 1) / CB_WARPS), CB_THREADS, 0, s>>>(D, st, k);
+        c->launches++;
+        TRY(check_launch(c, "k_lz"));
+    }
+    return AS_OK;
 }
 
 extern "C" int as_reset(as_ctx* c, const float* x_lo, const float* x_hi, const float* C, const float* lhat,
@@ -498,6 +609,7 @@ static int init_impl(as_ctx* c, const as_net* net, int S, const float* x_lo, con
     }
     D.NT = NT;
     D.NH = NT - c->widths[0];
+    std::vector<std::vector<float>> Wh(n);
     // weights
     for (int k = 0; k < n; ++k) {
         const as_layer& A = c->layers[k];
@@ -520,6 +632,8 @@ static int init_impl(as_ctx* c, const as_net* net, int S, const float* x_lo, con
         float *W, *b;
         TRY(dalloc(c, &W, wcount));
         CUDA_TRY(c, cudaMemcpyAsync(W, A.W, wcount * sizeof(float), cudaMemcpyDefault, c->stream));
+        Wh[k].resize(wcount);
+        CUDA_TRY(c, cudaMemcpyAsync(Wh[k].data(), A.W, wcount * sizeof(float), cudaMemcpyDefault, c->stream));
         std::vector<float> hb(bcount), hbe(L.n_out);
         CUDA_TRY(c, cudaMemcpyAsync(hb.data(), A.b, bcount * sizeof(float), cudaMemcpyDefault, c->stream));
         CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -539,6 +653,7 @@ static int init_impl(as_ctx* c, const as_net* net, int S, const float* x_lo, con
             c->blast = b;
         }
     }
+    TRY(build_walks(c, Wh));
     // launch geometry
     {
         std::vector<int> ids;
@@ -634,7 +749,9 @@ static cudaEvent_t prof_event(as_ctx* c) {
     } while (0)
 
 static int launch_as_iter(as_ctx* c, cudaStream_t s) {
-    LAUNCH(c, s, CB_K_AS_COLA, (k_as_colA_t<<<c->blocksTA, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->tA, 0)));
+    // the per-neuron bound terms are only summed when the best bound is tracked
+    const int mode = c->opt.track_best ? 0 : 2;
+    LAUNCH(c, s, CB_K_AS_COLA, (k_as_colA_t<<<c->blocksTA, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->tA, mode)));
     if (c->opt.track_best)
         LAUNCH(c, s, CB_K_REDUCE, (k_reduce<<<c->net.S, CB_THREADS, 0, s>>>(c->net, c->st, 64, nullptr, 1)));
     LAUNCH(c, s, CB_K_AS_ROWB, (k_as_rowB_t<<<c->blocksTB, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->tB)));
