@@ -92,12 +92,11 @@ struct DState {
     float *mua, *mub;                // [S][NH]
     float* xbar;                     // [S][NT]
     uint8_t* zbar;                   // [S][NH]
-    float *taup, *taun;              // [S][NT] mask thresholds of every input
+    float4* spin;                    // [S][2 XT] Saddle Point input records (two float4 per position)
+    int* nfree;                      // [S][NH] nonzero weights of each row on free inputs
     uint8_t* sel;                    // [S][NH] selected beta of the conditional gradient (3 = none)
     float *ab, *b0i, *b1i;           // [S][NH] primal-init inner maximisers
     float* arow;                     // [S][NH] ab - b1i (primal-init row values for the col pass)
-    float4* inrec;                   // [S][NT] per input: {x, tau+, tau-, l} of the current iterate
-    float4* rowrec;                  // [S][NH] per row: {beta_bar on beta_1, on I*, z, 0}
     int* status;                     // device error word
 };
 

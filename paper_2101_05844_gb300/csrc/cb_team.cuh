@@ -533,9 +533,11 @@ __global__ void k_rowprep(DNet net, DState st, DSched sc) {
     }
 }
 
-// lz[s][i] = sum_j W_ij Lcheck_ij (Lcheck = l_j where W_ij >= 0, u_j where W_ij < 0): lambda of
-// the all-ones mask, taken by Active Set slots added on rows with z = 1. One warp per row;
-// FP64 accumulation rounded to nearest.
+// Per-batch row constants: lz[s][i] = sum_j W_ij Lcheck_ij (Lcheck = l_j where W_ij >= 0, u_j
+// where W_ij < 0), lambda of the all-ones mask, taken by Active Set slots added on rows with z = 1
+// (FP64 accumulation rounded to nearest); nfree[s][i] = the nonzero weights of row i on free
+// inputs (l < u), against which Saddle Point recognises a mask selecting all of them. One warp per
+// row.
 __global__ void k_lz(DNet net, DState st, int li) {
     const DLayer& L = net.L[li];
     const int warp = (blockIdx.x * CB_THREADS + threadIdx.x) >> 5, lane = threadIdx.x & 31;
@@ -544,9 +546,17 @@ __global__ void k_lz(DNet net, DState st, int li) {
     const float* lo = st.lo + (size_t)s * net.NT + L.in_off;
     const float* hi = st.hi + (size_t)s * net.NT + L.in_off;
     double a = 0.0;
-    row_walk(L, i, lane, [&](int j, float w) { a += (double)w * (w >= 0.f ? lo[j] : hi[j]); });
+    int nf = 0;
+    row_walk(L, i, lane, [&](int j, float w) {
+        a += (double)w * (w >= 0.f ? lo[j] : hi[j]);
+        nf += (w != 0.f && lo[j] != hi[j]) ? 1 : 0;
+    });
     a = warp_sum(a);
-    if (lane == 0) st.lz[(size_t)s * net.NH + L.h_out + i] = (float)a;
+    for (int o = 16; o > 0; o >>= 1) nf += __shfl_xor_sync(0xffffffffu, nf, o);
+    if (lane == 0) {
+        st.lz[(size_t)s * net.NH + L.h_out + i] = (float)a;
+        st.nfree[(size_t)s * net.NH + L.h_out + i] = nf;
+    }
 }
 
 // efix[s][j] = (l == u): fixed inputs, whose mask bit is 1 for every slot.
@@ -582,11 +592,36 @@ __device__ __forceinline__ Unit team_unit(const TSegs& sg, int q, int count, int
     return u;
 }
 
+// Saddle Point records, in the Active Set walks' layouts (Active Set and Saddle Point do not run on
+// one context at the same time, so the output records reuse the Active Set's array):
+//  per output position (first 4 floats of each RS-float record): {alpha, beta_bar on beta_1,
+//      beta_bar on I*, z} of the current iterate, written by the row pass (alpha also by k_sp_prep);
+//  per input position, two float4 (st.spin): {x, tau+, l, u} for W > 0 and {x, tau-, u, l} for
+//      W < 0, i.e. {x, threshold, Lcheck, Ucheck} for the sign of the taps that read it.
+__device__ __forceinline__ float4* sp_orec(const DNet& net, const DState& st, const DLayer& L, int s, int i) {
+    return reinterpret_cast<float4*>(st.arec + (size_t)s * net.AT + L.ao + (size_t)arec_pos(L, i) * net.RS);
+}
+__device__ __forceinline__ float4* sp_irec(const DNet& net, const DState& st, const DLayer& L, int s, int j) {
+    // in float4 units a position takes two, as it takes two floats in the Active Set records
+    return st.spin + (size_t)s * net.XT + (size_t)L.xo + (size_t)xin_pos(L, j) * 2;
+}
+
+// alpha into the output records (Saddle Point start, state import).
+__global__ void k_sp_prep(DNet net, DState st) {
+    const size_t n = (size_t)net.S * net.NH;
+    for (size_t u = blockIdx.x * (size_t)blockDim.x + threadIdx.x; u < n; u += (size_t)gridDim.x * blockDim.x) {
+        const int s = (int)(u / net.NH), hh = (int)(u - (size_t)s * net.NH);
+        int li = 0;
+        while (li + 2 < net.n && hh >= net.L[li + 1].h_out) ++li;
+        *sp_orec(net, st, net.L[li], s, hh - net.L[li].h_out) = make_float4(st.alpha[u], 0.f, 0.f, 0.f);
+    }
+}
+
 // Phase A (col pass over k = 1..n) at the current (alpha, zeta): f_m = alpha_m - Sb_m -
 // W_{m+1}^T alpha_{m+1} + P_{m+1} (Sec. 5.1), the primal conditional gradient (eqs. 7-8 with
-// B = E), the bound terms, and the record {x, tau+, tau-, l} of input j for the row pass: the
-// float32 thresholds of the oracle eq. (3) at the current primal iterate. init != 0 also starts
-// the primal iterate at the conditional gradient.
+// B = E), the bound terms, and the records of input j for the row pass: the float32 thresholds of
+// the oracle eq. (3) at the current primal iterate. init != 0 also starts the primal iterate at
+// the conditional gradient.
 __global__ void __launch_bounds__(CB_THREADS) k_sp_colA_t(DNet net, DState st, TSegs sg, int init) {
     const int q = tseg_of(sg, blockIdx.x);
     const int li = sg.layer[q];
@@ -596,8 +631,15 @@ __global__ void __launch_bounds__(CB_THREADS) k_sp_colA_t(DNet net, DState st, T
     const size_t NT = net.NT, NH = net.NH;
     float acc = 0.f;
     if (u.valid && k <= net.n - 1) {
-        const float* al = st.alpha + (size_t)u.s * NH + L.h_out;
-        col_walk_team(L, u.idx, u.lane, u.T, [&](int i, float w) { acc += w * al[i]; });
+        int g, base;
+        col_group(L, u.idx, g, base);
+        const float* ar = st.arec + (size_t)u.s * net.AT + L.ao + (size_t)base * net.RS;
+        const int t0 = L.cgrp[2 * g], t2 = L.cgrp[2 * g + 2];
+#pragma unroll 4
+        for (int t = t0 + u.lane; t < t2; t += u.T) {
+            const int2 e = L.ctap[t];
+            acc = fmaf(__int_as_float(e.y), ar[e.x], acc);
+        }
     }
     if (u.T > 1) acc = team_sum(acc, u.T);
     if (!u.valid || u.lane != 0) return;
@@ -622,19 +664,23 @@ __global__ void __launch_bounds__(CB_THREADS) k_sp_colA_t(DNet net, DState st, T
     st.terms[xo] = term;
     const float x = init ? xb : st.spx[cur][xo];
     if (init) st.spx[cur][xo] = xb;
-    float tp = -INFINITY, tn = -INFINITY;
-    if (lo != hi) {
-        const float den = __fsub_rn(hi, lo);
-        tp = __fdiv_rn(__fsub_rn(x, lo), den);
-        tn = __fdiv_rn(__fsub_rn(hi, x), den);
+    if (k <= net.n - 1) {
+        float tp = -INFINITY, tn = -INFINITY;
+        if (lo != hi) {
+            const float den = __fsub_rn(hi, lo);
+            tp = __fdiv_rn(__fsub_rn(x, lo), den);
+            tn = __fdiv_rn(__fsub_rn(hi, x), den);
+        }
+        float4* r = sp_irec(net, st, L, s, j);
+        r[0] = make_float4(x, tp, lo, hi);
+        r[1] = make_float4(x, tn, hi, lo);
     }
-    st.inrec[xo] = make_float4(x, tp, tn, lo);
 }
 
 // Phase B (row pass over hidden layers) at the current primal iterate: the oracle mask I*
 // (eq. 3), the gradients of beta_0, beta_1, beta_I* (eq. 9 with B = E), the conditional
 // gradients alpha_bar (eq. 11) and beta_bar (eq. 12), the convex combination of alpha, Sb, G, C
-// (Alg. 2), and the row record for phase C.
+// (Alg. 2), and the output record for phase C and the next phase A.
 __global__ void __launch_bounds__(CB_THREADS) k_sp_rowB_t(DNet net, DState st, DSched sc, TSegs sg) {
     const int q = tseg_of(sg, blockIdx.x);
     const DLayer& L = net.L[sg.layer[q]];
@@ -646,43 +692,51 @@ __global__ void __launch_bounds__(CB_THREADS) k_sp_rowB_t(DNet net, DState st, D
     const size_t h = (size_t)s * NH + L.h_out + i;
     const float z = u.valid ? st.spz[cur][h] : 0.f;
     float a0 = 0.f, A = 0.f, Lam = 0.f, Mu = 0.f;
-    bool any_in = false, any_out = false;
+    int nout = 0;   // pairs with I = 0 (a nonzero weight on a free input)
     if (u.valid) {
-        const size_t ib = (size_t)s * NT + L.in_off;
-        const float4* rec = st.inrec + ib;
-        const float* hiv = st.hi + ib;
-        row_walk_team(L, i, u.lane, u.T, [&](int j, float w) {
-            const float4 r = rec[j];
-            const float uu = hiv[j];
+        int g, base;
+        row_group(L, i, g, base);
+        const float4* rb = st.spin + (size_t)s * net.XT + (size_t)L.xo + (size_t)base * 2;
+        const int t0 = L.rgrp[2 * g], t1 = L.rgrp[2 * g + 1], t2 = L.rgrp[2 * g + 2];
+        // {x, threshold, Lcheck, Ucheck} of the tap's sign: the first record for W > 0, the second
+        // for W < 0; I = [z >= threshold] (fixed inputs and padding: always 1)
+        auto pair = [&](float w, const float4 r) {
             const float wx = w * r.x;
             a0 += wx;
-            const bool I = w > 0.f ? (z >= r.y) : (w < 0.f ? (z >= r.z) : true);
-            const bool pos = w >= 0.f;
-            const float wL = w * (pos ? r.w : uu), wU = w * (pos ? uu : r.w);
-            // selects, not branches: the lanes of a warp disagree on I
-            A += I ? wx : 0.f;
-            Lam += I ? wL : 0.f;
-            Mu += I ? 0.f : wU;
-            any_in |= I && (w != 0.f) && (r.w != uu);
-            any_out |= !I;   // I = 0 only for a nonzero weight on a free input
-        });
+            if (z >= r.y) {
+                A += wx;
+                Lam += w * r.z;
+            } else {
+                Mu += w * r.w;
+                ++nout;
+            }
+        };
+#pragma unroll 4
+        for (int tt = t0 + u.lane; tt < t1; tt += u.T) {
+            const int2 e = L.rtap[tt];
+            pair(__int_as_float(e.y), rb[2 * e.x]);
+        }
+#pragma unroll 4
+        for (int tt = t1 + u.lane; tt < t2; tt += u.T) {
+            const int2 e = L.rtap[tt];
+            pair(__int_as_float(e.y), rb[2 * e.x + 1]);
+        }
     }
     if (u.T > 1) {
         a0 = team_sum(a0, u.T);
         A = team_sum(A, u.T);
         Lam = team_sum(Lam, u.T);
         Mu = team_sum(Mu, u.T);
+        for (int o = u.T >> 1; o > 0; o >>= 1) nout += __shfl_xor_sync(0xffffffffu, nout, o);
     }
+    if (!u.valid || u.lane != 0) return;
     // a row selecting none or all of its free inputs is the all-zero / all-ones constraint, a
     // looser copy of beta_0 / beta_1: it does not compete in the choice of eq. (12)
-    any_in = team_any(any_in, u.T);
-    any_out = team_any(any_out, u.T);
-    if (!u.valid || u.lane != 0) return;
-    const bool degenerate = !any_in || !any_out;
+    const bool degenerate = nout == 0 || nout == st.nfree[h];
     const float gamma = 1.f / ((float)t + sc.gamma0);
     const float bi = L.b[i];
     const float xhat = a0 + bi;
-    const float x = st.inrec[(size_t)s * NT + L.out_off + i].x;
+    const float x = st.spx[cur][(size_t)s * NT + L.out_off + i];
     const float uh = st.uhat[h], lh = st.lhat[h];
     const float abar = (xhat - x >= 0.f) ? st.mua[h] : 0.f;
     const float v0 = x - z * uh;
@@ -697,12 +751,13 @@ __global__ void __launch_bounds__(CB_THREADS) k_sp_rowB_t(DNet net, DState st, D
     const float gsel = sel == 0 ? uh : (sel == 1 ? lh : Lam + Mu + bi);
     const float csel = sel == 0 ? 0.f : (sel == 1 ? lh - bi : Lam);
     const float om = 1.f - gamma;
-    st.alpha[h] = om * st.alpha[h] + gamma * abar;
+    const float an = om * st.alpha[h] + gamma * abar;
+    st.alpha[h] = an;
     st.Sb[h] = om * st.Sb[h] + gamma * bb;
     st.G[h] = om * st.G[h] + gamma * (bb * gsel);
     st.C[h] = om * st.C[h] + gamma * (bb * csel);
     st.sel[h] = on ? (uint8_t)sel : (uint8_t)3;
-    st.rowrec[h] = make_float4(sel == 1 ? bb : 0.f, sel == 2 ? bb : 0.f, z, 0.f);
+    *sp_orec(net, st, L, s, i) = make_float4(an, sel == 1 ? bb : 0.f, sel == 2 ? bb : 0.f, z);
 }
 
 // Phase C (col pass over k = 1..n): P_bar_k = (W_k o I_dagger)^T beta_bar for input j (the masked
@@ -719,13 +774,24 @@ __global__ void __launch_bounds__(CB_THREADS) k_sp_colC_t(DNet net, DState st, D
     const size_t xo = (size_t)u.s * NT + L.in_off + u.idx;
     float acc = 0.f;
     if (u.valid && k <= net.n - 1) {
-        const float4 r = st.inrec[xo];
-        const float4* rr = st.rowrec + (size_t)u.s * NH + L.h_out;
-        col_walk_team(L, u.idx, u.lane, u.T, [&](int i, float w) {
-            const float4 v = rr[i];
-            const bool I = w > 0.f ? (v.z >= r.y) : (w < 0.f ? (v.z >= r.z) : true);
-            acc += w * (v.x + (I ? v.y : 0.f));
-        });
+        const float4* own = sp_irec(net, st, L, u.s, u.idx);
+        const float tp = own[0].y, tn = own[1].y;
+        int g, base;
+        col_group(L, u.idx, g, base);
+        const float* ar = st.arec + (size_t)u.s * net.AT + L.ao + (size_t)base * net.RS;
+        const int t0 = L.cgrp[2 * g], t1 = L.cgrp[2 * g + 1], t2 = L.cgrp[2 * g + 2];
+#pragma unroll 4
+        for (int tt = t0 + u.lane; tt < t1; tt += u.T) {
+            const int2 e = L.ctap[tt];
+            const float4 v = *reinterpret_cast<const float4*>(ar + e.x);
+            acc = fmaf(__int_as_float(e.y), v.y + (v.w >= tp ? v.z : 0.f), acc);
+        }
+#pragma unroll 4
+        for (int tt = t1 + u.lane; tt < t2; tt += u.T) {
+            const int2 e = L.ctap[tt];
+            const float4 v = *reinterpret_cast<const float4*>(ar + e.x);
+            acc = fmaf(__int_as_float(e.y), v.y + (v.w >= tn ? v.z : 0.f), acc);
+        }
     }
     if (u.T > 1) acc = team_sum(acc, u.T);
     if (u.valid && u.lane == 0) {

@@ -438,6 +438,7 @@ static int alloc_state(as_ctx* c) {
         st.P = z.take<float>(NTS);
         st.arec = z.take<float>(S * (size_t)D.AT);
         st.xin = z.take<float>(S * (size_t)D.XT);
+        st.spin = z.take<float4>(S * (size_t)D.XT);
         for (int q = 0; q < 2; ++q) {
             st.xsnap[q] = z.take<uint8_t>(NTS);
             st.zsnap[q] = z.take<uint8_t>(NHS);
@@ -453,8 +454,6 @@ static int alloc_state(as_ctx* c) {
         st.xval = o.take<float>(NTS);
         st.fval = o.take<float>(NTS);
         st.xbar = o.take<float>(NTS);
-        st.taup = o.take<float>(NTS);
-        st.taun = o.take<float>(NTS);
         for (int q = 0; q < 2; ++q) {
             st.spx[q] = o.take<float>(NTS);
             st.spz[q] = o.take<float>(NHS);
@@ -463,8 +462,7 @@ static int alloc_state(as_ctx* c) {
         st.lz = o.take<float>(NHS);
         st.efix = o.take<uint8_t>(NTS);
         st.arow = o.take<float>(NHS);
-        st.inrec = o.take<float4>(NTS);
-        st.rowrec = o.take<float4>(NHS);
+        st.nfree = o.take<int>(NHS);
         st.zbar = o.take<uint8_t>(NHS);
         st.sel = o.take<uint8_t>(NHS);
         st.terms = o.take<double>(NTS);
@@ -829,8 +827,9 @@ static int sp_start(as_ctx* c) {
     k_sp_convert_elem<<<grid_for(NHS), CB_THREADS, 0, s>>>(c->net, c->st, c->sc, (float)c->opt.sp_c_alpha,
                                                            (float)c->opt.sp_c_beta);
     k_sp_convert_P<<<c->blocksP, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->segP);
+    k_sp_prep<<<grid_for(NHS), CB_THREADS, 0, s>>>(c->net, c->st);
     k_sp_colA_t<<<c->blocksTA, CB_THREADS, 0, s>>>(c->net, c->st, c->tA, 1);
-    c->launches += 3;
+    c->launches += 4;
     TRY(check_launch(c, "Saddle Point conversion"));
     for (int t = 0; t < c->opt.sp_init_steps; ++t) {
         LAUNCH(c, s, CB_K_SPI_ROW, (k_spi_row_t<<<c->blocksTB, CB_THREADS, 0, s>>>(c->net, c->st, c->tB)));
