@@ -27,12 +27,14 @@ struct DLayer {
     //  row pass: group = output row (linear) or output channel (conv); offsets index the input
     //            records of this layer in positions (zero-padded input plane for conv)
     //  col pass: group = input (linear) or (input channel, stride phase y, stride phase x) (conv);
-    //            offsets index the output records (output plane with a zero halo for conv)
+    //            offsets index the output records in positions (output plane with a zero halo
+    //            for conv)
     const int2* rtap;
     const int* rgrp;
     const int2* ctap;
     const int* cgrp;
     int xo, ao;            // offsets (floats) of this layer's input / output records in a subproblem
+    int xpos, apos;        // input / output record positions (padded planes for conv)
     int Hp, Wp;            // padded input plane (conv): in + 2 pad
     int Hpo, Wpo, hl, wl;  // output plane with halo (conv): rows hl .. hl + ho - 1 are the outputs
 };
@@ -65,7 +67,8 @@ struct DState {
     float *alpha, *beta0, *beta1;
     float *ma, *va, *m0, *v0, *m1, *v1;
     float *bs, *ms, *vs, *lam, *kap; // slots
-    float *arec;                     // [S][AT] output records of each layer (RS floats per position):
+    float *arec;                     // [S][AT] output records of each layer, RS floats per position
+                                     // stored as RS / 4 planes of float4 over the positions:
                                      // -(alpha - beta1) + sum_b z_b beta_b, then (1 - z_b) beta_b
     float *xin;                      // [S][XT] input records of each layer, one float2 per position:
                                      // {x*, p_b bits | q_b bits << 8}
@@ -92,7 +95,7 @@ struct DState {
     float *mua, *mub;                // [S][NH]
     float* xbar;                     // [S][NT]
     uint8_t* zbar;                   // [S][NH]
-    float4* spin;                    // [S][2 XT] Saddle Point input records (two float4 per position)
+    float4* spin;                    // [S][XT] Saddle Point input records: two float4 planes per layer
     int* nfree;                      // [S][NH] nonzero weights of each row on free inputs
     uint8_t* sel;                    // [S][NH] selected beta of the conditional gradient (3 = none)
     float *ab, *b0i, *b1i;           // [S][NH] primal-init inner maximisers

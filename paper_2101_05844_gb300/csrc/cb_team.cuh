@@ -180,14 +180,23 @@ __device__ __forceinline__ int arec_pos(const DLayer& L, int i) {
     return (co * L.Hpo + oy + L.hl) * L.Wpo + ox + L.wl;
 }
 
-// The first NV floats of a 16-byte aligned record.
+// Output records of layer L for subproblem s: RS / 4 planes of float4, plane q holding entries
+// 4q .. 4q + 3 of every position, so that lanes reading neighbouring positions read one
+// contiguous run per plane.
+__device__ __forceinline__ float4* arec_planes(const DNet& net, const DState& st, const DLayer& L, int s) {
+    return reinterpret_cast<float4*>(st.arec + (size_t)s * net.AT + L.ao);
+}
+__device__ __forceinline__ float* arec_entry(const DNet& net, const DState& st, const DLayer& L, int s, int p, int e) {
+    return reinterpret_cast<float*>(arec_planes(net, st, L, s) + (size_t)(e >> 2) * L.apos + p) + (e & 3);
+}
+
+// The first NV entries of the record at q (planes apos apart).
 template <int NV>
-__device__ __forceinline__ void load_rec(const float* p, float (&v)[12]) {
-    const float4* q = reinterpret_cast<const float4*>(p);
+__device__ __forceinline__ void load_rec(const float4* q, int apos, float (&v)[12]) {
     const float4 a = q[0];
     v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-    if (NV > 4) { const float4 b = q[1]; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w; }
-    if (NV > 8) { const float4 c = q[2]; v[8] = c.x; v[9] = c.y; v[10] = c.z; v[11] = c.w; }
+    if (NV > 4) { const float4 b = q[apos]; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w; }
+    if (NV > 8) { const float4 c = q[2 * apos]; v[8] = c.x; v[9] = c.y; v[10] = c.z; v[11] = c.w; }
 }
 
 // ---------------------------------------------------------------- Active Set col pass (phase A)
@@ -211,14 +220,15 @@ __device__ __forceinline__ void as_colA_body(const DNet& net, const DState& st, 
     if (valid && k <= net.n - 1) {
         int g, base;
         col_group(L, j, g, base);
-        const float* ar = st.arec + (size_t)s * net.AT + L.ao + (size_t)base * RS;
+        const float4* ar = arec_planes(net, st, L, s) + base;
+        const int apos = L.apos;
         const int t0 = L.cgrp[2 * g], t1 = L.cgrp[2 * g + 1], t2 = L.cgrp[2 * g + 2];
 #pragma unroll 2
         for (int t = t0 + lane; t < t1; t += T) {
             const int2 e = L.ctap[t];
             const float w = __int_as_float(e.y);
             float v[12];
-            load_rec<1 + NS>(ar + e.x, v);
+            load_rec<1 + NS>(ar + e.x, apos, v);
             acc = fmaf(w, v[0], acc);
 #pragma unroll
             for (int b = 0; b < NS; ++b) Pp[b] = fmaf(w, v[1 + b], Pp[b]);
@@ -228,7 +238,7 @@ __device__ __forceinline__ void as_colA_body(const DNet& net, const DState& st, 
             const int2 e = L.ctap[t];
             const float w = __int_as_float(e.y);
             float v[12];
-            load_rec<1 + NS>(ar + e.x, v);
+            load_rec<1 + NS>(ar + e.x, apos, v);
             acc = fmaf(w, v[0], acc);
 #pragma unroll
             for (int b = 0; b < NS; ++b) Pn[b] = fmaf(w, v[1 + b], Pn[b]);
@@ -413,7 +423,7 @@ __device__ __forceinline__ void as_rowB_body(const DNet& net, const DState& st, 
         const float z = st.zcur[h] ? 1.f : 0.f;
         const float xhat = acc0 + bi;
         const size_t hs0 = (size_t)s * cap * NH + L.h_out + i;
-        float* ar = st.arec + (size_t)s * net.AT + L.ao + (size_t)arec_pos(L, i) * RS;
+        const int ap = arec_pos(L, i);
         for (int v = lane; v < 3 + NS; v += T) {
             if (v < 3) {
                 float* th = v == 0 ? st.alpha : (v == 1 ? st.beta0 : st.beta1);
@@ -429,7 +439,7 @@ __device__ __forceinline__ void as_rowB_body(const DNet& net, const DState& st, 
                 if (v == 2) contrib += nv;
             } else {
                 const int b = v - 3;
-                if (b >= nsl) { ar[1 + b] = 0.f; continue; }
+                if (b >= nsl) { *arec_entry(net, st, L, s, ap, 1 + b) = 0.f; continue; }
                 const size_t hs = hs0 + (size_t)b * NH;
                 float lam, kap;
                 float ab = 0.f;
@@ -455,12 +465,12 @@ __device__ __forceinline__ void as_rowB_body(const DNet& net, const DState& st, 
                                            inv_bias_corr(st.bc2_tab, sc.ntab, sstep, sc.b2), sc);
                 st.bs[hs] = nv; st.ms[hs] = m; st.vs[hs] = w2;
                 if (zb) contrib += nv;
-                ar[1 + b] = zb ? 0.f : nv;
+                *arec_entry(net, st, L, s, ap, 1 + b) = zb ? 0.f : nv;
             }
         }
     }
     if (T > 1) contrib = team_sum(contrib, T);
-    if (valid && lane == 0) st.arec[(size_t)s * net.AT + L.ao + (size_t)arec_pos(L, i) * RS] = contrib;
+    if (valid && lane == 0) *arec_entry(net, st, L, s, arec_pos(L, i), 0) = contrib;
 }
 
 __global__ void __launch_bounds__(CB_THREADS) k_as_rowB_t(DNet net, DState st, DSched sc, TSegs sg) {
@@ -516,7 +526,7 @@ __global__ void k_rowprep(DNet net, DState st, DSched sc) {
         const DLayer& L = net.L[li];
         const int nsl = min(sp.nadd_before, st.caps[s]);
         const unsigned zs = st.zsnap[bo][u];
-        float* rec = st.arec + (size_t)s * net.AT + L.ao + (size_t)arec_pos(L, hh - L.h_out) * net.RS;
+        const int ap = arec_pos(L, hh - L.h_out);
         float r = -(st.alpha[u] - st.beta1[u]);
         for (int b = 0; b < net.RS - 1; ++b) {
             float bv = 0.f;
@@ -527,9 +537,9 @@ __global__ void k_rowprep(DNet net, DState st, DSched sc) {
                 zb = (zs >> b) & 1u;
             }
             if (zb) r += bv;
-            rec[1 + b] = zb ? 0.f : bv;
+            *arec_entry(net, st, L, s, ap, 1 + b) = zb ? 0.f : bv;
         }
-        rec[0] = r;
+        *arec_entry(net, st, L, s, ap, 0) = r;
     }
 }
 
@@ -594,16 +604,17 @@ __device__ __forceinline__ Unit team_unit(const TSegs& sg, int q, int count, int
 
 // Saddle Point records, in the Active Set walks' layouts (Active Set and Saddle Point do not run on
 // one context at the same time, so the output records reuse the Active Set's array):
-//  per output position (first 4 floats of each RS-float record): {alpha, beta_bar on beta_1,
+//  per output position (the first float4 plane of the output records): {alpha, beta_bar on beta_1,
 //      beta_bar on I*, z} of the current iterate, written by the row pass (alpha also by k_sp_prep);
-//  per input position, two float4 (st.spin): {x, tau+, l, u} for W > 0 and {x, tau-, u, l} for
-//      W < 0, i.e. {x, threshold, Lcheck, Ucheck} for the sign of the taps that read it.
+//  per input position, two float4 planes (st.spin): {x, tau+, l, u} for W > 0 and {x, tau-, u, l}
+//      for W < 0, i.e. {x, threshold, Lcheck, Ucheck} for the sign of the taps that read it.
 __device__ __forceinline__ float4* sp_orec(const DNet& net, const DState& st, const DLayer& L, int s, int i) {
-    return reinterpret_cast<float4*>(st.arec + (size_t)s * net.AT + L.ao + (size_t)arec_pos(L, i) * net.RS);
+    return arec_planes(net, st, L, s) + arec_pos(L, i);
 }
-__device__ __forceinline__ float4* sp_irec(const DNet& net, const DState& st, const DLayer& L, int s, int j) {
-    // in float4 units a position takes two, as it takes two floats in the Active Set records
-    return st.spin + (size_t)s * net.XT + (size_t)L.xo + (size_t)xin_pos(L, j) * 2;
+// the W > 0 plane of layer L (the W < 0 plane follows, xpos float4 later): in float4 units a
+// layer takes 2 xpos, as it takes 2 xpos floats in the Active Set input records
+__device__ __forceinline__ float4* sp_iplane(const DNet& net, const DState& st, const DLayer& L, int s) {
+    return st.spin + (size_t)s * net.XT + (size_t)L.xo;
 }
 
 // alpha into the output records (Saddle Point start, state import).
@@ -633,12 +644,12 @@ __global__ void __launch_bounds__(CB_THREADS) k_sp_colA_t(DNet net, DState st, T
     if (u.valid && k <= net.n - 1) {
         int g, base;
         col_group(L, u.idx, g, base);
-        const float* ar = st.arec + (size_t)u.s * net.AT + L.ao + (size_t)base * net.RS;
+        const float4* ar = arec_planes(net, st, L, u.s) + base;
         const int t0 = L.cgrp[2 * g], t2 = L.cgrp[2 * g + 2];
 #pragma unroll 4
         for (int t = t0 + u.lane; t < t2; t += u.T) {
             const int2 e = L.ctap[t];
-            acc = fmaf(__int_as_float(e.y), ar[e.x], acc);
+            acc = fmaf(__int_as_float(e.y), ar[e.x].x, acc);
         }
     }
     if (u.T > 1) acc = team_sum(acc, u.T);
@@ -671,9 +682,9 @@ __global__ void __launch_bounds__(CB_THREADS) k_sp_colA_t(DNet net, DState st, T
             tp = __fdiv_rn(__fsub_rn(x, lo), den);
             tn = __fdiv_rn(__fsub_rn(hi, x), den);
         }
-        float4* r = sp_irec(net, st, L, s, j);
+        float4* r = sp_iplane(net, st, L, s) + xin_pos(L, j);
         r[0] = make_float4(x, tp, lo, hi);
-        r[1] = make_float4(x, tn, hi, lo);
+        r[L.xpos] = make_float4(x, tn, hi, lo);
     }
 }
 
@@ -696,9 +707,10 @@ __global__ void __launch_bounds__(CB_THREADS) k_sp_rowB_t(DNet net, DState st, D
     if (u.valid) {
         int g, base;
         row_group(L, i, g, base);
-        const float4* rb = st.spin + (size_t)s * net.XT + (size_t)L.xo + (size_t)base * 2;
+        const float4* rb = sp_iplane(net, st, L, s) + base;
+        const float4* rn = rb + L.xpos;
         const int t0 = L.rgrp[2 * g], t1 = L.rgrp[2 * g + 1], t2 = L.rgrp[2 * g + 2];
-        // {x, threshold, Lcheck, Ucheck} of the tap's sign: the first record for W > 0, the second
+        // {x, threshold, Lcheck, Ucheck} of the tap's sign: the first plane for W > 0, the second
         // for W < 0; I = [z >= threshold] (fixed inputs and padding: always 1)
         auto pair = [&](float w, const float4 r) {
             const float wx = w * r.x;
@@ -714,12 +726,12 @@ __global__ void __launch_bounds__(CB_THREADS) k_sp_rowB_t(DNet net, DState st, D
 #pragma unroll 4
         for (int tt = t0 + u.lane; tt < t1; tt += u.T) {
             const int2 e = L.rtap[tt];
-            pair(__int_as_float(e.y), rb[2 * e.x]);
+            pair(__int_as_float(e.y), rb[e.x]);
         }
 #pragma unroll 4
         for (int tt = t1 + u.lane; tt < t2; tt += u.T) {
             const int2 e = L.rtap[tt];
-            pair(__int_as_float(e.y), rb[2 * e.x + 1]);
+            pair(__int_as_float(e.y), rn[e.x]);
         }
     }
     if (u.T > 1) {
@@ -774,22 +786,22 @@ __global__ void __launch_bounds__(CB_THREADS) k_sp_colC_t(DNet net, DState st, D
     const size_t xo = (size_t)u.s * NT + L.in_off + u.idx;
     float acc = 0.f;
     if (u.valid && k <= net.n - 1) {
-        const float4* own = sp_irec(net, st, L, u.s, u.idx);
-        const float tp = own[0].y, tn = own[1].y;
+        const float4* own = sp_iplane(net, st, L, u.s) + xin_pos(L, u.idx);
+        const float tp = own[0].y, tn = own[L.xpos].y;
         int g, base;
         col_group(L, u.idx, g, base);
-        const float* ar = st.arec + (size_t)u.s * net.AT + L.ao + (size_t)base * net.RS;
+        const float4* ar = arec_planes(net, st, L, u.s) + base;
         const int t0 = L.cgrp[2 * g], t1 = L.cgrp[2 * g + 1], t2 = L.cgrp[2 * g + 2];
 #pragma unroll 4
         for (int tt = t0 + u.lane; tt < t1; tt += u.T) {
             const int2 e = L.ctap[tt];
-            const float4 v = *reinterpret_cast<const float4*>(ar + e.x);
+            const float4 v = ar[e.x];
             acc = fmaf(__int_as_float(e.y), v.y + (v.w >= tp ? v.z : 0.f), acc);
         }
 #pragma unroll 4
         for (int tt = t1 + u.lane; tt < t2; tt += u.T) {
             const int2 e = L.ctap[tt];
-            const float4 v = *reinterpret_cast<const float4*>(ar + e.x);
+            const float4 v = ar[e.x];
             acc = fmaf(__int_as_float(e.y), v.y + (v.w >= tn ? v.z : 0.f), acc);
         }
     }

@@ -259,8 +259,8 @@ struct Bump {
 };
 
 // Sign-partitioned tap lists and record layouts of the Active Set walks (DLayer fields) for the
-// hidden-output layers. Row-pass taps index the input records in positions (one float2 each),
-// col-pass taps the output records in floats (RS per position).
+// hidden-output layers. Taps index record positions: the input records (one float2 each) for the
+// row pass, the output records (RS / 4 float4 planes) for the col pass.
 static int build_walks(as_ctx* c, const std::vector<std::vector<float>>& Wh) {
     DNet& D = c->net;
     const int RS = D.RS;
@@ -294,7 +294,7 @@ static int build_walks(as_ctx* c, const std::vector<std::vector<float>>& Wh) {
                 close_group(rt, rg);
             }
             for (int j = 0; j < L.n_in; ++j) {
-                for (int i = 0; i < L.n_out; ++i) add(i * RS, W[(size_t)i * L.n_in + j]);
+                for (int i = 0; i < L.n_out; ++i) add(i, W[(size_t)i * L.n_in + j]);
                 close_group(ct, cg);
             }
             xpos = L.n_in;
@@ -325,7 +325,7 @@ static int build_walks(as_ctx* c, const std::vector<std::vector<float>>& Wh) {
                         for (int co = 0; co < L.co; ++co)
                             for (int ky = py, dky = 0; ky < L.kh; ky += L.st, ++dky)
                                 for (int kx = px, dkx = 0; kx < L.kw; kx += L.st, ++dkx)
-                                    add((co * L.Hpo * L.Wpo - dky * L.Wpo - dkx) * RS,
+                                    add(co * L.Hpo * L.Wpo - dky * L.Wpo - dkx,
                                         W[((size_t)co * L.ci + ci) * kk + ky * L.kw + kx]);
                         close_group(ct, cg);
                     }
@@ -350,6 +350,8 @@ static int build_walks(as_ctx* c, const std::vector<std::vector<float>>& Wh) {
         L.cgrp = dcg;
         L.xo = xo;
         L.ao = ao;
+        L.xpos = xpos;
+        L.apos = apos;
         const long long xn = (long long)xo + (long long)xpos * 2, an = (long long)ao + (long long)apos * RS;
         if (xn > INT32_MAX / 2 || an > INT32_MAX / 2)
             return fail(c, AS_ERR_SHAPE, "layer %d: record offsets exceed 32 bits", k + 1);
