@@ -213,7 +213,6 @@ __device__ __forceinline__ void as_colA_body(const DNet& net, const DState& st, 
     const int m = k - 1;
     const Step sp = cb_step(st.ctr[0], sc, st.lr_tab);
     const size_t NT = net.NT, NH = net.NH, cap = net.cap;
-    const int RS = net.RS;
     float acc = 0.f, Pp[NS > 0 ? NS : 1], Pn[NS > 0 ? NS : 1];
 #pragma unroll
     for (int b = 0; b < NS; ++b) Pp[b] = Pn[b] = 0.f;
@@ -328,7 +327,7 @@ __device__ __forceinline__ int tseg_of(const TSegs& sg, int blk) {
 // Col pass over layers k = 1..n (phase A of an iteration, or the bound evaluation with mode 1):
 // f_m for every neuron j of layer m = k-1 (Sec. 4.1), x*, z* (eqs. 7-8), per-neuron bound terms
 // (eq. 6) and, on addition iterations, the new slot's snapshot bits (Alg. 1, Prop. 1).
-__global__ void __launch_bounds__(CB_THREADS) k_as_colA_t(DNet net, DState st, DSched sc, TSegs sg, int mode) {
+__global__ void __launch_bounds__(CB_THREADS, 4) k_as_colA_t(DNet net, DState st, DSched sc, TSegs sg, int mode) {
     const int q = tseg_of(sg, blockIdx.x);
     const int li = sg.layer[q];
     const DLayer& L = net.L[li];
@@ -369,7 +368,6 @@ template <int NS, bool ADD>
 __device__ __forceinline__ void as_rowB_body(const DNet& net, const DState& st, const DSched& sc, const DLayer& L,
                                              bool valid, int s, int i, int lane, int T, const Step& sp, int it) {
     const size_t NT = net.NT, NH = net.NH, cap = net.cap;
-    const int RS = net.RS;
     const int cap_s = valid ? st.caps[s] : 0;
     const int newb = (ADD && sp.b_new < cap_s) ? sp.b_new : -1;
     const int bn = (sp.nadd_before + (sp.b_new >= 0 ? 1 : 0)) & 1;
@@ -473,7 +471,7 @@ __device__ __forceinline__ void as_rowB_body(const DNet& net, const DState& st, 
     if (valid && lane == 0) *arec_entry(net, st, L, s, arec_pos(L, i), 0) = contrib;
 }
 
-__global__ void __launch_bounds__(CB_THREADS) k_as_rowB_t(DNet net, DState st, DSched sc, TSegs sg) {
+__global__ void __launch_bounds__(CB_THREADS, 4) k_as_rowB_t(DNet net, DState st, DSched sc, TSegs sg) {
     const int q = tseg_of(sg, blockIdx.x);
     const DLayer& L = net.L[sg.layer[q]];
     const int T = sg.T[q];
@@ -628,34 +626,14 @@ __global__ void k_sp_prep(DNet net, DState st) {
     }
 }
 
-// Phase A (col pass over k = 1..n) at the current (alpha, zeta): f_m = alpha_m - Sb_m -
-// W_{m+1}^T alpha_{m+1} + P_{m+1} (Sec. 5.1), the primal conditional gradient (eqs. 7-8 with
-// B = E), the bound terms, and the records of input j for the row pass: the float32 thresholds of
-// the oracle eq. (3) at the current primal iterate. init != 0 also starts the primal iterate at
-// the conditional gradient.
-__global__ void __launch_bounds__(CB_THREADS) k_sp_colA_t(DNet net, DState st, TSegs sg, int init) {
-    const int q = tseg_of(sg, blockIdx.x);
-    const int li = sg.layer[q];
-    const DLayer& L = net.L[li];
-    const int k = li + 1, m = k - 1;
-    const Unit u = team_unit(sg, q, L.n_in, net.S);
+// Phase A epilogue for input j of layer L (k = li + 1, m = k - 1): f_m from acc = (W_k^T alpha_k)[j]
+// (Sec. 5.1), the primal conditional gradient (eqs. 7-8 with B = E), the bound terms, and the
+// records of input j for the row pass: the float32 thresholds of the oracle eq. (3) at the primal
+// iterate x (buffer cur). init != 0 also starts the primal iterate at the conditional gradient.
+__device__ __forceinline__ void sp_phaseA_epilogue(const DNet& net, const DState& st, const DLayer& L, int k,
+                                                   int s, int j, float acc, int cur, int init) {
+    const int m = k - 1;
     const size_t NT = net.NT, NH = net.NH;
-    float acc = 0.f;
-    if (u.valid && k <= net.n - 1) {
-        int g, base;
-        col_group(L, u.idx, g, base);
-        const float4* ar = arec_planes(net, st, L, u.s) + base;
-        const int t0 = L.cgrp[2 * g], t2 = L.cgrp[2 * g + 2];
-#pragma unroll 4
-        for (int t = t0 + u.lane; t < t2; t += u.T) {
-            const int2 e = L.ctap[t];
-            acc = fmaf(__int_as_float(e.y), ar[e.x].x, acc);
-        }
-    }
-    if (u.T > 1) acc = team_sum(acc, u.T);
-    if (!u.valid || u.lane != 0) return;
-    const int s = u.s, j = u.idx;
-    const int cur = st.ctr[1] & 1;
     const size_t xo = (size_t)s * NT + L.in_off + j;
     float f = k <= net.n - 1 ? st.P[xo] - acc : -net.Wout[(size_t)s * L.n_in + j];
     const float lo = st.lo[xo], hi = st.hi[xo];
@@ -688,6 +666,32 @@ __global__ void __launch_bounds__(CB_THREADS) k_sp_colA_t(DNet net, DState st, T
     }
 }
 
+// Phase A (col pass over k = 1..n) at the current (alpha, zeta): the walk for W_k^T alpha_k, then
+// the epilogue above. Runs alone at the start of Saddle Point, after a state import and for the
+// bound; within the iteration loop it is fused with phase C (k_sp_colCA_t).
+__global__ void __launch_bounds__(CB_THREADS) k_sp_colA_t(DNet net, DState st, TSegs sg, int init) {
+    const int q = tseg_of(sg, blockIdx.x);
+    const int li = sg.layer[q];
+    const DLayer& L = net.L[li];
+    const int k = li + 1;
+    const Unit u = team_unit(sg, q, L.n_in, net.S);
+    float acc = 0.f;
+    if (u.valid && k <= net.n - 1) {
+        int g, base;
+        col_group(L, u.idx, g, base);
+        const float4* ar = arec_planes(net, st, L, u.s) + base;
+        const int t0 = L.cgrp[2 * g], t2 = L.cgrp[2 * g + 2];
+#pragma unroll 4
+        for (int t = t0 + u.lane; t < t2; t += u.T) {
+            const int2 e = L.ctap[t];
+            acc = fmaf(__int_as_float(e.y), ar[e.x].x, acc);
+        }
+    }
+    if (u.T > 1) acc = team_sum(acc, u.T);
+    if (!u.valid || u.lane != 0) return;
+    sp_phaseA_epilogue(net, st, L, k, u.s, u.idx, acc, st.ctr[1] & 1, init);
+}
+
 // Phase B (row pass over hidden layers) at the current primal iterate: the oracle mask I*
 // (eq. 3), the gradients of beta_0, beta_1, beta_I* (eq. 9 with B = E), the conditional
 // gradients alpha_bar (eq. 11) and beta_bar (eq. 12), the convex combination of alpha, Sb, G, C
@@ -712,26 +716,22 @@ __global__ void __launch_bounds__(CB_THREADS) k_sp_rowB_t(DNet net, DState st, D
         const int t0 = L.rgrp[2 * g], t1 = L.rgrp[2 * g + 1], t2 = L.rgrp[2 * g + 2];
         // {x, threshold, Lcheck, Ucheck} of the tap's sign: the first plane for W > 0, the second
         // for W < 0; I = [z >= threshold] (fixed inputs and padding: always 1)
-        auto pair = [&](float w, const float4 r) {
-            const float wx = w * r.x;
-            a0 += wx;
-            if (z >= r.y) {
-                A += wx;
-                Lam += w * r.z;
-            } else {
-                Mu += w * r.w;
-                ++nout;
+        for (int ph = 0; ph < 2; ++ph) {
+            const float4* rp = ph ? rn : rb;
+            const int ta = ph ? t1 : t0, tb = ph ? t2 : t1;
+#pragma unroll 4
+            for (int tt = ta + u.lane; tt < tb; tt += u.T) {
+                const int2 e = L.rtap[tt];
+                const float w = __int_as_float(e.y);
+                const float4 r = rp[e.x];
+                const float wx = w * r.x;
+                a0 += wx;
+                const bool I = z >= r.y;
+                A += I ? wx : 0.f;
+                Lam += I ? w * r.z : 0.f;
+                Mu += I ? 0.f : w * r.w;
+                nout += I ? 0 : 1;
             }
-        };
-#pragma unroll 4
-        for (int tt = t0 + u.lane; tt < t1; tt += u.T) {
-            const int2 e = L.rtap[tt];
-            pair(__int_as_float(e.y), rb[e.x]);
-        }
-#pragma unroll 4
-        for (int tt = t1 + u.lane; tt < t2; tt += u.T) {
-            const int2 e = L.rtap[tt];
-            pair(__int_as_float(e.y), rn[e.x]);
         }
     }
     if (u.T > 1) {
@@ -772,10 +772,13 @@ __global__ void __launch_bounds__(CB_THREADS) k_sp_rowB_t(DNet net, DState st, D
     *sp_orec(net, st, L, s, i) = make_float4(an, sel == 1 ? bb : 0.f, sel == 2 ? bb : 0.f, z);
 }
 
-// Phase C (col pass over k = 1..n): P_bar_k = (W_k o I_dagger)^T beta_bar for input j (the masked
-// backward product of the chosen masks), the convex combination of P_k and of the primal iterate
-// (x_m, z_m) into the other buffer. The last block advances the iteration counter.
-__global__ void __launch_bounds__(CB_THREADS) k_sp_colC_t(DNet net, DState st, DSched sc, TSegs sg) {
+// Phase C of iteration t fused with phase A of iteration t + 1 (col pass over k = 1..n): one walk
+// over the output records {alpha, beta_bar on beta_1, beta_bar on I*, z} gives both
+// P_bar_k = (W_k o I_dagger)^T beta_bar for input j (the masked backward product of the chosen
+// masks) and (W_k^T alpha_k)[j] at the updated alpha. The epilogue takes the convex combination of
+// P_k and of the primal iterate (x_m, z_m) into the other buffer (Alg. 2), then runs phase A at
+// the new iterate. The last block advances the iteration counter.
+__global__ void __launch_bounds__(CB_THREADS) k_sp_colCA_t(DNet net, DState st, DSched sc, TSegs sg) {
     const int q = tseg_of(sg, blockIdx.x);
     const int li = sg.layer[q];
     const DLayer& L = net.L[li];
@@ -784,7 +787,7 @@ __global__ void __launch_bounds__(CB_THREADS) k_sp_colC_t(DNet net, DState st, D
     const int t = st.ctr[1];
     const size_t NT = net.NT, NH = net.NH;
     const size_t xo = (size_t)u.s * NT + L.in_off + u.idx;
-    float acc = 0.f;
+    float accC = 0.f, accA = 0.f;
     if (u.valid && k <= net.n - 1) {
         const float4* own = sp_iplane(net, st, L, u.s) + xin_pos(L, u.idx);
         const float tp = own[0].y, tn = own[L.xpos].y;
@@ -795,27 +798,35 @@ __global__ void __launch_bounds__(CB_THREADS) k_sp_colC_t(DNet net, DState st, D
 #pragma unroll 4
         for (int tt = t0 + u.lane; tt < t1; tt += u.T) {
             const int2 e = L.ctap[tt];
+            const float w = __int_as_float(e.y);
             const float4 v = ar[e.x];
-            acc = fmaf(__int_as_float(e.y), v.y + (v.w >= tp ? v.z : 0.f), acc);
+            accC = fmaf(w, v.y + (v.w >= tp ? v.z : 0.f), accC);
+            accA = fmaf(w, v.x, accA);
         }
 #pragma unroll 4
         for (int tt = t1 + u.lane; tt < t2; tt += u.T) {
             const int2 e = L.ctap[tt];
+            const float w = __int_as_float(e.y);
             const float4 v = ar[e.x];
-            acc = fmaf(__int_as_float(e.y), v.y + (v.w >= tn ? v.z : 0.f), acc);
+            accC = fmaf(w, v.y + (v.w >= tn ? v.z : 0.f), accC);
+            accA = fmaf(w, v.x, accA);
         }
     }
-    if (u.T > 1) acc = team_sum(acc, u.T);
+    if (u.T > 1) {
+        accC = team_sum(accC, u.T);
+        accA = team_sum(accA, u.T);
+    }
     if (u.valid && u.lane == 0) {
         const int cur = t & 1, nxt = cur ^ 1;
         const float gamma = 1.f / ((float)t + sc.gamma0);
         const float om = 1.f - gamma;
-        if (k <= net.n - 1) st.P[xo] = om * st.P[xo] + gamma * acc;
+        if (k <= net.n - 1) st.P[xo] = om * st.P[xo] + gamma * accC;
         st.spx[nxt][xo] = om * st.spx[cur][xo] + gamma * st.xbar[xo];
         if (m >= 1) {
             const size_t hh = (size_t)u.s * NH + L.h_in + u.idx;
             st.spz[nxt][hh] = om * st.spz[cur][hh] + gamma * (st.zbar[hh] ? 1.f : 0.f);
         }
+        sp_phaseA_epilogue(net, st, L, k, u.s, u.idx, accA, nxt, 0);
     }
     if (last_block(&st.done[1]) && threadIdx.x == 0) {
         st.ctr[1] = t + 1;

@@ -29,6 +29,7 @@ struct as_ctx {
     std::vector<as_layer> layers;  // shapes (pointers not kept)
     std::vector<int> widths;       // neuron layers 0..n-1
     bool sp_started = false;
+    bool sp_need_phaseA = true;    // the next Saddle Point iteration starts with a separate phase A
     long long launches = 0;
     Segs segA{}, segB{}, segP{};
     int blocksA = 0, blocksB = 0, blocksP = 0;
@@ -758,12 +759,13 @@ static int launch_as_iter(as_ctx* c, cudaStream_t s) {
     return check_launch(c, "Active Set iteration");
 }
 
+// One Saddle Point iteration t: phase B, then phase C fused with phase A of iteration t + 1 (the
+// loop's first phase A runs before it, k_sp_colA_t, whenever the state is new).
 static int launch_sp_iter(as_ctx* c, cudaStream_t s) {
-    LAUNCH(c, s, CB_K_SP_COLA, (k_sp_colA_t<<<c->blocksTA, CB_THREADS, 0, s>>>(c->net, c->st, c->tA, 0)));
+    LAUNCH(c, s, CB_K_SP_ROWB, (k_sp_rowB_t<<<c->blocksTB, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->tB)));
+    LAUNCH(c, s, CB_K_SP_COLC, (k_sp_colCA_t<<<c->blocksTA, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->tA)));
     if (c->opt.track_best)
         LAUNCH(c, s, CB_K_REDUCE, (k_reduce<<<c->net.S, CB_THREADS, 0, s>>>(c->net, c->st, 64, nullptr, 1)));
-    LAUNCH(c, s, CB_K_SP_ROWB, (k_sp_rowB_t<<<c->blocksTB, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->tB)));
-    LAUNCH(c, s, CB_K_SP_COLC, (k_sp_colC_t<<<c->blocksTA, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->tA)));
     return check_launch(c, "Saddle Point iteration");
 }
 
@@ -839,6 +841,7 @@ static int sp_start(as_ctx* c) {
     }
     TRY(check_launch(c, "Saddle Point primal initialisation"));
     c->sp_started = true;
+    c->sp_need_phaseA = true;
     return AS_OK;
 }
 
@@ -846,6 +849,13 @@ extern "C" int sp_step(as_ctx* c, int n_iters) {
     if (!c) return AS_ERR_ARG;
     if (n_iters < 0) return fail(c, AS_ERR_ARG, "n_iters < 0");
     if (!c->sp_started) TRY(sp_start(c));
+    if (n_iters == 0) return AS_OK;
+    if (c->sp_need_phaseA) {
+        cudaStream_t s = c->stream;
+        LAUNCH(c, s, CB_K_SP_COLA, (k_sp_colA_t<<<c->blocksTA, CB_THREADS, 0, s>>>(c->net, c->st, c->tA, 0)));
+        TRY(check_launch(c, "Saddle Point phase A"));
+        c->sp_need_phaseA = false;
+    }
     return run_iters(c, n_iters, launch_sp_iter, &c->g_sp, &c->g_sp_len, &c->g_sp_nodes);
 }
 
@@ -1013,6 +1023,7 @@ static int recompute_slot_sums(as_ctx* c);
 
 extern "C" int as_set_state(as_ctx* c, int which, const void* src) {
     if (!c || !src) return AS_ERR_ARG;
+    c->sp_need_phaseA = true;
     if (which < 0 || which >= AS_ST_COUNT) return fail(c, AS_ERR_ARG, "unknown state buffer %d", which);
     if (which == AS_ST_XSTAR || which == AS_ST_ZSTAR || which == AS_ST_LAMBDA || which == AS_ST_KAPPA ||
         which == AS_ST_LO || which == AS_ST_HI || which == AS_ST_LHAT || which == AS_ST_UHAT ||
