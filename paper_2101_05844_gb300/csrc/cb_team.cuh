@@ -199,6 +199,18 @@ __device__ __forceinline__ void load_rec(const float4* q, int apos, float (&v)[1
     if (NV > 8) { const float4 c = q[2 * apos]; v[8] = c.x; v[9] = c.y; v[10] = c.z; v[11] = c.w; }
 }
 
+// B taps of a lane's stride T starting at t (taps at or past tb read as {0, +0.f}: a zero weight
+// at the unit's base position, which adds nothing). Loading a whole batch of taps, then all of their
+// records, keeps B independent loads in flight per lane instead of one dependent pair at a time.
+template <int B>
+__device__ __forceinline__ void load_taps(const int2* tap, int t, int tb, int T, int2 (&e)[B]) {
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        const int tt = t + b * T;
+        e[b] = tt < tb ? tap[tt] : make_int2(0, 0);
+    }
+}
+
 // ---------------------------------------------------------------- Active Set col pass (phase A)
 // The masked backward product of eq. (6) for input j, regrouped by the sign of W: at binary
 // iterates eq. (3) gives I_b(i, j) = 1 on rows with z_b[i] = 1 (their beta is in the record's
@@ -222,25 +234,26 @@ __device__ __forceinline__ void as_colA_body(const DNet& net, const DState& st, 
         const float4* ar = arec_planes(net, st, L, s) + base;
         const int apos = L.apos;
         const int t0 = L.cgrp[2 * g], t1 = L.cgrp[2 * g + 1], t2 = L.cgrp[2 * g + 2];
-#pragma unroll 2
-        for (int t = t0 + lane; t < t1; t += T) {
-            const int2 e = L.ctap[t];
-            const float w = __int_as_float(e.y);
-            float v[12];
-            load_rec<1 + NS>(ar + e.x, apos, v);
-            acc = fmaf(w, v[0], acc);
+        constexpr int B = 2;   // records of up to 12 floats: two in flight fit 64 registers
+        for (int ph = 0; ph < 2; ++ph) {
+            const int ta = ph ? t1 : t0, tb = ph ? t2 : t1;
+            for (int t = ta + lane; t < tb; t += B * T) {
+                int2 e[B];
+                load_taps<B>(L.ctap, t, tb, T, e);
+                float v[B][12];
 #pragma unroll
-            for (int b = 0; b < NS; ++b) Pp[b] = fmaf(w, v[1 + b], Pp[b]);
-        }
-#pragma unroll 2
-        for (int t = t1 + lane; t < t2; t += T) {
-            const int2 e = L.ctap[t];
-            const float w = __int_as_float(e.y);
-            float v[12];
-            load_rec<1 + NS>(ar + e.x, apos, v);
-            acc = fmaf(w, v[0], acc);
+                for (int q = 0; q < B; ++q) load_rec<1 + NS>(ar + e[q].x, apos, v[q]);
 #pragma unroll
-            for (int b = 0; b < NS; ++b) Pn[b] = fmaf(w, v[1 + b], Pn[b]);
+                for (int q = 0; q < B; ++q) {
+                    const float w = __int_as_float(e[q].y);
+                    acc = fmaf(w, v[q][0], acc);
+#pragma unroll
+                    for (int b = 0; b < NS; ++b) {
+                        if (ph) Pn[b] = fmaf(w, v[q][1 + b], Pn[b]);
+                        else Pp[b] = fmaf(w, v[q][1 + b], Pp[b]);
+                    }
+                }
+            }
         }
     }
     if (T > 1) {
@@ -383,27 +396,26 @@ __device__ __forceinline__ void as_rowB_body(const DNet& net, const DState& st, 
         const float2* xb = reinterpret_cast<const float2*>(st.xin + (size_t)s * net.XT + L.xo) + base;
         const int t0 = L.rgrp[2 * g], t1 = L.rgrp[2 * g + 1], t2 = L.rgrp[2 * g + 2];
         // positive taps take the slot masks p_b (bits 0-7), negative taps q_b (bits 8-15)
-#pragma unroll 4
-        for (int t = t0 + lane; t < t1; t += T) {
-            const int2 e = L.rtap[t];
-            const float2 r = xb[e.x];
-            const float wx = __int_as_float(e.y) * r.x;
-            const unsigned msk = __float_as_uint(r.y);
-            acc0 += wx;
+        constexpr int B = 6;   // six taps and records in flight fit 64 registers
+        for (int ph = 0; ph < 2; ++ph) {
+            const int ta = ph ? t1 : t0, tb = ph ? t2 : t1;
+            const int sh = ph ? 8 : 0;
+            for (int t = ta + lane; t < tb; t += B * T) {
+                int2 e[B];
+                load_taps<B>(L.rtap, t, tb, T, e);
+                float2 r[B];
 #pragma unroll
-            for (int b = 0; b < NS; ++b)
-                if ((msk >> b) & 1u) acc[b] += wx;
-        }
-#pragma unroll 4
-        for (int t = t1 + lane; t < t2; t += T) {
-            const int2 e = L.rtap[t];
-            const float2 r = xb[e.x];
-            const float wx = __int_as_float(e.y) * r.x;
-            const unsigned msk = __float_as_uint(r.y);
-            acc0 += wx;
+                for (int q = 0; q < B; ++q) r[q] = xb[e[q].x];
 #pragma unroll
-            for (int b = 0; b < NS; ++b)
-                if ((msk >> (8 + b)) & 1u) acc[b] += wx;
+                for (int q = 0; q < B; ++q) {
+                    const float wx = __int_as_float(e[q].y) * r[q].x;
+                    const unsigned msk = __float_as_uint(r[q].y) >> sh;
+                    acc0 += wx;
+#pragma unroll
+                    for (int b = 0; b < NS; ++b)
+                        if ((msk >> b) & 1u) acc[b] += wx;
+                }
+            }
         }
     }
     if (T > 1) {
@@ -681,10 +693,15 @@ __global__ void __launch_bounds__(CB_THREADS) k_sp_colA_t(DNet net, DState st, T
         col_group(L, u.idx, g, base);
         const float4* ar = arec_planes(net, st, L, u.s) + base;
         const int t0 = L.cgrp[2 * g], t2 = L.cgrp[2 * g + 2];
-#pragma unroll 4
-        for (int t = t0 + u.lane; t < t2; t += u.T) {
-            const int2 e = L.ctap[t];
-            acc = fmaf(__int_as_float(e.y), ar[e.x].x, acc);
+        constexpr int B = 8;
+        for (int t = t0 + u.lane; t < t2; t += B * u.T) {
+            int2 e[B];
+            load_taps<B>(L.ctap, t, t2, u.T, e);
+            float a[B];
+#pragma unroll
+            for (int q = 0; q < B; ++q) a[q] = ar[e[q].x].x;
+#pragma unroll
+            for (int q = 0; q < B; ++q) acc = fmaf(__int_as_float(e[q].y), a[q], acc);
         }
     }
     if (u.T > 1) acc = team_sum(acc, u.T);
@@ -716,21 +733,28 @@ __global__ void __launch_bounds__(CB_THREADS) k_sp_rowB_t(DNet net, DState st, D
         const int t0 = L.rgrp[2 * g], t1 = L.rgrp[2 * g + 1], t2 = L.rgrp[2 * g + 2];
         // {x, threshold, Lcheck, Ucheck} of the tap's sign: the first plane for W > 0, the second
         // for W < 0; I = [z >= threshold] (fixed inputs and padding: always 1)
+        constexpr int B = 8;
         for (int ph = 0; ph < 2; ++ph) {
             const float4* rp = ph ? rn : rb;
             const int ta = ph ? t1 : t0, tb = ph ? t2 : t1;
-#pragma unroll 4
-            for (int tt = ta + u.lane; tt < tb; tt += u.T) {
-                const int2 e = L.rtap[tt];
-                const float w = __int_as_float(e.y);
-                const float4 r = rp[e.x];
-                const float wx = w * r.x;
-                a0 += wx;
-                const bool I = z >= r.y;
-                A += I ? wx : 0.f;
-                Lam += I ? w * r.z : 0.f;
-                Mu += I ? 0.f : w * r.w;
-                nout += I ? 0 : 1;
+            for (int tt = ta + u.lane; tt < tb; tt += B * u.T) {
+                int2 e[B];
+                load_taps<B>(L.rtap, tt, tb, u.T, e);
+                float4 r[B];
+#pragma unroll
+                for (int q = 0; q < B; ++q) r[q] = rp[e[q].x];
+#pragma unroll
+                for (int q = 0; q < B; ++q) {
+                    const float w = __int_as_float(e[q].y);
+                    const float wx = w * r[q].x;
+                    a0 += wx;
+                    // a padding tap (w = 0) adds nothing and counts as selected
+                    const bool I = z >= r[q].y || w == 0.f;
+                    A += I ? wx : 0.f;
+                    Lam += I ? w * r[q].z : 0.f;
+                    Mu += I ? 0.f : w * r[q].w;
+                    nout += I ? 0 : 1;
+                }
             }
         }
     }
@@ -795,21 +819,23 @@ __global__ void __launch_bounds__(CB_THREADS) k_sp_colCA_t(DNet net, DState st, 
         col_group(L, u.idx, g, base);
         const float4* ar = arec_planes(net, st, L, u.s) + base;
         const int t0 = L.cgrp[2 * g], t1 = L.cgrp[2 * g + 1], t2 = L.cgrp[2 * g + 2];
-#pragma unroll 4
-        for (int tt = t0 + u.lane; tt < t1; tt += u.T) {
-            const int2 e = L.ctap[tt];
-            const float w = __int_as_float(e.y);
-            const float4 v = ar[e.x];
-            accC = fmaf(w, v.y + (v.w >= tp ? v.z : 0.f), accC);
-            accA = fmaf(w, v.x, accA);
-        }
-#pragma unroll 4
-        for (int tt = t1 + u.lane; tt < t2; tt += u.T) {
-            const int2 e = L.ctap[tt];
-            const float w = __int_as_float(e.y);
-            const float4 v = ar[e.x];
-            accC = fmaf(w, v.y + (v.w >= tn ? v.z : 0.f), accC);
-            accA = fmaf(w, v.x, accA);
+        constexpr int B = 8;
+        for (int ph = 0; ph < 2; ++ph) {
+            const int ta = ph ? t1 : t0, tb = ph ? t2 : t1;
+            const float tau = ph ? tn : tp;
+            for (int tt = ta + u.lane; tt < tb; tt += B * u.T) {
+                int2 e[B];
+                load_taps<B>(L.ctap, tt, tb, u.T, e);
+                float4 v[B];
+#pragma unroll
+                for (int q = 0; q < B; ++q) v[q] = ar[e[q].x];
+#pragma unroll
+                for (int q = 0; q < B; ++q) {
+                    const float w = __int_as_float(e[q].y);
+                    accC = fmaf(w, v[q].y + (v[q].w >= tau ? v[q].z : 0.f), accC);
+                    accA = fmaf(w, v[q].x, accA);
+                }
+            }
         }
     }
     if (u.T > 1) {
