@@ -52,13 +52,16 @@ def iterations_per_step():
 
 
 def run_step(ctx_as, ctx_sp, batch, out_as, out_sp):
+    """One step: the Active Set solve and the Saddle Point solve of the batch. The two contexts are
+    independent; when they sit on different streams their launches overlap on the GPU (all work
+    is enqueued before the first bound evaluation, which waits for its own stream)."""
     lo, hi, C = batch
     ctx_as.reset(lo, hi, C)
     ctx_as.as_step(AS_BIGM + AS_ITERS)
-    ctx_as.bound_into(64, out_as)
     ctx_sp.reset(lo, hi, C)
     ctx_sp.as_step(SP_BIGM)
     ctx_sp.sp_step(SP_ITERS)
+    ctx_as.bound_into(64, out_as)
     ctx_sp.bound_into(64, out_sp)
 
 
@@ -331,8 +334,12 @@ def main():
     out_h = [torch.zeros(S, dtype=torch.float64).pin_memory() for _ in range(2)]
     as_opt, sp_opt = workload_options(binding)
     stream = torch.cuda.current_stream().cuda_stream
-    ctx_as = binding.Context(prob["net"], prob["lo"], prob["hi"], prob["C"], options=as_opt, stream=stream)
-    ctx_sp = binding.Context(prob["net"], prob["lo"], prob["hi"], prob["C"], options=sp_opt, stream=stream)
+    # the step's two solves on streams of their own (joined to the timing stream by events)
+    s_as, s_sp = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    ctx_as = binding.Context(prob["net"], prob["lo"], prob["hi"], prob["C"], options=as_opt,
+                             stream=s_as.cuda_stream)
+    ctx_sp = binding.Context(prob["net"], prob["lo"], prob["hi"], prob["C"], options=sp_opt,
+                             stream=s_sp.cuda_stream)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
 
     def barrier():
@@ -342,17 +349,23 @@ def main():
 
     def timed(batch, outs, k):
         times = []
+        main = torch.cuda.current_stream(dev)
         for _ in range(k):
             flush.fill_(1.0)                      # evict L2 between steps
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
+            e0.record(main)
+            s_as.wait_event(e0)
+            s_sp.wait_event(e0)
             run_step(ctx_as, ctx_sp, batch, outs[0], outs[1])
-            e1.record()
+            main.wait_stream(s_as)
+            main.wait_stream(s_sp)
+            e1.record(main)
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
         return times
 
+    torch.cuda.synchronize()
     for _ in range(args.warmup):
         run_step(ctx_as, ctx_sp, (lo_d, hi_d, C_d), out_d[0], out_d[1])
     barrier()
