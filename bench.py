@@ -227,6 +227,23 @@ def batched_run(binding, torch, dev, stream, rank):
             "kernel_ms": {k: v[0] for k, v in kt.items() if v[1]}}
 
 
+def captured_traffic(workload, kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture of this workload, or None
+    when there is none or the kernel source has changed since it was taken."""
+    import hashlib
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles", f"dram_traffic_{workload}.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        src = os.path.join(os.path.dirname(os.path.abspath(__file__)), rec["source"])
+        with open(src, "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != rec["source_sha256"]:
+                return None
+        return rec["dram_bytes_per_launch"].get(kernel)
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def slowest_rank(values, dist, device):
     """Element-wise maximum of per-rank timings over all ranks (the job is as slow as its slowest
     replica); with one process the values themselves."""
@@ -421,7 +438,7 @@ def main():
         "roofline": {"bound": "alu", "kernel": top, "achieved": achieved, "peak": peak_tflops,
                      "unit": "TFLOP/s", "frac": (achieved / peak_tflops) if achieved else None,
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (derived)",
-                     "traffic": None, "launches": n, "kernel_ms": tms,
+                     "traffic": captured_traffic(args.workload, top), "launches": n, "kernel_ms": tms,
                      "share_of_kernel_time": tms / step_kernel_ms if step_kernel_ms else None},
         "kernel_ms_per_step": {k: v[0] for k, v in kt.items() if v[1]},
         "clocks": clk.summary(),
