@@ -32,7 +32,7 @@ extern "C" {
 #define AS_ERR_CUDA 3     /* a CUDA call failed (message in as_last_error)                   */
 #define AS_ERR_OOM 4      /* device allocation failed                                        */
 #define AS_ERR_NUMERIC 5  /* a bound came out NaN or infinite                                */
-#define AS_ERR_TIMEOUT 6  /* a bounded device wait expired (reserved; no kernel waits today) */
+#define AS_ERR_TIMEOUT 6  /* a bounded device wait expired (tensor-core kernels only)          */
 #define AS_ERR_STATE 7    /* call not valid in the context's current mode                    */
 #define AS_ERR_SCRATCH 8  /* the problem does not fit the fixed scratch of as_ibp_noalloc      */
 
@@ -224,6 +224,20 @@ const char* as_last_error(as_ctx* ctx);
 #define AS_NOALLOC_SCRATCH_FLOATS (1u << 22)
 int as_ibp_noalloc(const as_net* net, int S, const float* x_lo, const float* x_hi,
                    const signed char* splits, float* lhat, float* uhat, void* stream);
+
+/* BF16 tensor-core GEMM, D = A . B^T (the building block of the BF16 form of the masked
+ * products of Sec. 4.1 / eq. 6 and eq. 9: at Active Set iterates every masked product is a dense
+ * product with W+ and W-, and the transposed one with their transposes).
+ *  A: [M][K] bf16 (raw 16-bit), row stride lda elements; B: [N][K] bf16, row stride ldb; both
+ *     device memory, 16-byte aligned, K, lda and ldb multiples of 8.
+ *  D: [M][N] float32 device memory, row stride ldd (>= N); every entry is overwritten.
+ *  bn: N tile of a CTA, 32, 64, 128 or 256 (tensor-memory columns it allocates).
+ * Products are exact in float32; the sum over K accumulates in float32 in the tensor cores'
+ * order. The call synchronises `stream`. Returns AS_ERR_ARG for bad sizes, strides or
+ * alignment, AS_ERR_CUDA for a failed launch, AS_ERR_TIMEOUT if a bounded wait of the kernel on
+ * its own tensor-core work ran out (D is then unspecified). */
+int as_gemm_bf16(const void* A, int lda, const void* B, int ldb, float* D, int ldd, int M, int N, int K, int bn,
+                 void* stream);
 
 #ifdef __cplusplus
 }

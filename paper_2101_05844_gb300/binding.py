@@ -26,7 +26,7 @@ MAX_LAYERS, MAX_CUTS = 10, 8
 
 EXPORTS = ["as_default_options", "as_init", "as_reset", "as_step", "sp_step", "as_bound",
            "as_bound_backward", "as_state_size", "as_get_state", "as_set_state", "as_launch_count",
-           "as_kernel_times", "as_destroy", "as_last_error", "as_ibp_noalloc"]
+           "as_kernel_times", "as_destroy", "as_last_error", "as_ibp_noalloc", "as_gemm_bf16"]
 KERNELS = ["as_colA", "as_rowB", "reduce", "sp_colA", "sp_rowB", "sp_colC", "spi_row", "spi_col"]
 
 
@@ -85,6 +85,9 @@ def lib() -> ct.CDLL:
         L.as_last_error.restype = ct.c_char_p
         L.as_ibp_noalloc.argtypes = [ct.POINTER(Net), ct.c_int] + [ct.c_void_p] * 6
         L.as_ibp_noalloc.restype = ct.c_int
+        L.as_gemm_bf16.argtypes = [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_int, ct.c_int,
+                                   ct.c_int, ct.c_int, ct.c_int, ct.c_void_p]
+        L.as_gemm_bf16.restype = ct.c_int
         _lib = L
     return _lib
 
@@ -257,6 +260,19 @@ def ibp_noalloc(net: list, lo, hi, lhat_out, uhat_out, splits=None, stream: int 
     n = Net(len(net), layers)
     return lib().as_ibp_noalloc(ct.byref(n), int(lo.shape[0]), _ptr(lo), _ptr(hi), _ptr(splits),
                                 _ptr(lhat_out), _ptr(uhat_out), ct.c_void_p(stream))
+
+
+def gemm_bf16(A, B, D, bn: int = 128, stream: int = 0) -> int:
+    """as_gemm_bf16: D = A . B^T for CUDA tensors A [M][K], B [N][K] (torch.bfloat16) and D [M][N]
+    (float32), each with contiguous rows (row strides may exceed the row length); returns the
+    status code."""
+    M, K = A.shape
+    N = B.shape[0]
+    for t in (A, B, D):
+        if t.stride(1) != 1:
+            raise ValueError("rows must be contiguous")
+    return lib().as_gemm_bf16(ct.c_void_p(A.data_ptr()), A.stride(0), ct.c_void_p(B.data_ptr()), B.stride(0),
+                              ct.c_void_p(D.data_ptr()), D.stride(0), M, N, K, bn, ct.c_void_p(stream))
 
 
 def context_for(prob: dict, options: Options | None = None, bounds=None, stream: int = 0, **kw) -> Context:

@@ -6,14 +6,16 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SRCS = [os.path.join(HERE, "csrc", "convex_barrier.cu"), os.path.join(HERE, "csrc", "noalloc.cu")]
+SRCS = [os.path.join(HERE, "csrc", f) for f in ("convex_barrier.cu", "noalloc.cu", "tc_gemm.cu")]
 LIB = os.path.join(HERE, "libconvex_barrier.so")
+OBJDIR = os.path.join(HERE, "_build")
 DEPS = [os.path.join(HERE, "csrc", f) for f in
         ("convex_barrier.cu", "cb_common.cuh", "cb_kernels.cuh", "cb_backward.cuh", "cb_team.cuh",
-         "cb_host_extra.inc", "noalloc.cu", "cb_walk.cuh")] + [os.path.join(HERE, "..", "include", "convex_barrier.h")]
+         "cb_host_extra.inc", "noalloc.cu", "cb_walk.cuh", "cb_tc.cuh", "tc_gemm.cu")] + \
+    [os.path.join(HERE, "..", "include", "convex_barrier.h")]
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
-              "-shared", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
+              "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 
 
 def nvcc() -> str:
@@ -31,9 +33,23 @@ def up_to_date() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
+    """Compiles the translation units in parallel (nvcc -c), then links the shared library."""
     if not force and up_to_date():
         return LIB
-    cmd = [nvcc(), *NVCC_FLAGS, "-o", LIB + ".tmp", *SRCS]
+    os.makedirs(OBJDIR, exist_ok=True)
+    procs = []
+    for src in SRCS:
+        obj = os.path.join(OBJDIR, os.path.basename(src) + ".o")
+        cmd = [nvcc(), *NVCC_FLAGS, "-c", "-o", obj, src]
+        if verbose:
+            print(" ".join(cmd), file=sys.stderr)
+        procs.append((subprocess.Popen(cmd), obj, cmd))
+    objs = []
+    for p, obj, cmd in procs:
+        if p.wait() != 0:
+            raise subprocess.CalledProcessError(p.returncode, cmd)
+        objs.append(obj)
+    cmd = [nvcc(), "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-o", LIB + ".tmp", *objs]
     if verbose:
         print(" ".join(cmd), file=sys.stderr)
     subprocess.run(cmd, check=True)

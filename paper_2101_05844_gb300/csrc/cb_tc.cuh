@@ -1,0 +1,242 @@
+// BF16 tensor-core GEMM on the 5th-generation tensor cores of sm_103a (tcgen05):
+//   D[M][N] (float32) = A[M][K] (bf16) . B[N][K]^T (bf16)
+// Both operands are K-major (rows of K contiguous elements), as the masked products of the
+// Active Set iteration present them: rows of A are (subproblem, slot) inputs, rows of B are the
+// sign-split weights [W+ | W-] (row pass) or their transposes (col pass).
+//
+// A CTA of 128 threads owns a 128 x BN tile of D, accumulated in tensor memory (TMEM: lane = row,
+// column = output column, float32). K advances in tiles of 64: every thread stages 16-byte pieces
+// of the A and B tiles into shared memory with cp.async, in the canonical no-swizzle K-major layout
+// (8-row x 16-byte core matrices; core (r8, k8) at byte ((r8 * 8) + k8) * 128 of the tile, so that
+// core matrices adjacent in K are 128 bytes apart and those adjacent in M/N 1024 bytes apart), two
+// stages deep. One thread issues four tcgen05.mma (K = 16 each) per tile and commits them to the
+// stage's mbarrier; the stage is refilled once that barrier completes. The epilogue reads the
+// accumulator back with tcgen05.ld (each warp its 32 TMEM lanes) and stores it to global memory.
+//
+// Every wait is bounded: a barrier that does not complete within the limit sets *status and the
+// CTA stops issuing work, waits (bounded) for its last commit, frees its TMEM and returns.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace cb {
+namespace tc {
+
+constexpr int TC_BM = 128, TC_BK = 64, TC_THREADS = 128, TC_STAGES = 2;
+constexpr uint32_t TC_WAIT_LIMIT = 1u << 24;   // try_wait rounds before a barrier counts as lost
+constexpr int TC_ERR_TIMEOUT = 6;             // value written to *status (AS_ERR_TIMEOUT)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0u;
+}
+
+// Bounded wait for the completion of phase `parity`; false if the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    for (uint32_t i = 0; i < TC_WAIT_LIMIT; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// TMEM allocation of `ncols` columns (a power of two, >= 32) by one whole warp; the address is
+// written to shared memory at dst.
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_free(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// Shared-memory matrix descriptor: start address, leading-dimension byte offset (between core
+// matrices adjacent in K), stride-dimension byte offset (adjacent in M/N), descriptor version 1,
+// no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= static_cast<uint64_t>((addr >> 4) & 0x3FFFu);
+    d |= static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16;
+    d |= static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32;
+    d |= static_cast<uint64_t>(1u) << 46;
+    return d;
+}
+
+// Instruction descriptor of kind::f16 with bf16 A and B, float32 D, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+           (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// 16 consecutive float32 columns of this warp's 32 TMEM lanes.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// Stage `rows` rows x 64 K of a K-major bf16 matrix (row stride ld elements) into the canonical
+// layout at smem byte address dst; rows >= nrows and K >= k_end are zero-filled.
+__device__ __forceinline__ void stage_tile(uint32_t dst, const uint16_t* src, int ld, int row0, int nrows, int k0,
+                                           int k_end, int rows) {
+    for (int c = threadIdx.x; c < rows * 8; c += TC_THREADS) {
+        const int r = c >> 3, k8 = c & 7;
+        const int gr = row0 + r, gk = k0 + k8 * 8;
+        const bool in = gr < nrows && gk < k_end;
+        const uint16_t* p = in ? src + (size_t)gr * ld + gk : src;
+        cp_async16(dst + static_cast<uint32_t>((((r >> 3) * 8) + k8) * 128 + (r & 7) * 16), p, in ? 16u : 0u);
+    }
+}
+
+template <int BN>
+constexpr int tc_smem_bytes() {
+    return TC_STAGES * (TC_BM * TC_BK * 2 + BN * TC_BK * 2) + 64;
+}
+
+// D = A . B^T with A [M][K] (row stride lda), B [N][K] (ldb), D [M][N] (ldd); K, lda, ldb
+// multiples of 8 (16-byte rows pieces). Grid (ceil(M / 128), ceil(N / BN)).
+template <int BN>
+__global__ void __launch_bounds__(TC_THREADS) k_gemm_bf16(const uint16_t* __restrict__ A, int lda,
+                                                          const uint16_t* __restrict__ B, int ldb, float* __restrict__ D,
+                                                          int ldd, int M, int N, int K, int* status) {
+    static_assert(BN == 32 || BN == 64 || BN == 128 || BN == 256, "BN");
+    extern __shared__ __align__(1024) uint8_t smem[];
+    constexpr int A_BYTES = TC_BM * TC_BK * 2, B_BYTES = BN * TC_BK * 2, STAGE = A_BYTES + B_BYTES;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + TC_STAGES * STAGE);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + TC_STAGES);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * BN;
+    if (warp == 0) tmem_alloc(tslot, BN);
+    if (tid == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) mbar_init(&bars[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    const uint32_t sbase = smem_u32(smem);
+    constexpr uint32_t idesc = idesc_bf16(TC_BM, BN);
+    const int KT = (K + TC_BK - 1) / TC_BK;
+    bool ok = true;
+
+    stage_tile(sbase, A, lda, m0, M, 0, K, TC_BM);
+    stage_tile(sbase + A_BYTES, B, ldb, n0, N, 0, K, BN);
+    cp_async_commit();
+    int issued = 0;   // commits issued by thread 0 (stage of commit c: c % TC_STAGES)
+    for (int kt = 0; kt < KT; ++kt) {
+        const int s = kt % TC_STAGES;
+        bool w_ok = true;
+        // stage (kt + 1) % TC_STAGES was last read by the MMAs of tile kt + 1 - TC_STAGES
+        if (kt + 1 < KT && kt + 1 >= TC_STAGES)
+            w_ok = mbar_wait(&bars[(kt + 1) % TC_STAGES], ((kt + 1 - TC_STAGES) / TC_STAGES) & 1u);
+        if (!__syncthreads_and(w_ok)) {   // the decision is the CTA's, so every thread leaves together
+            ok = false;
+            break;
+        }
+        if (kt + 1 < KT) {
+            const uint32_t st = sbase + ((kt + 1) % TC_STAGES) * STAGE;
+            stage_tile(st, A, lda, m0, M, (kt + 1) * TC_BK, K, TC_BM);
+            stage_tile(st + A_BYTES, B, ldb, n0, N, (kt + 1) * TC_BK, K, BN);
+            cp_async_commit();
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t a = sbase + s * STAGE, b = a + A_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < TC_BK / 16; ++kk)
+                mma_bf16(tmem, smem_desc(a + kk * 256, 128, 1024), smem_desc(b + kk * 256, 128, 1024), idesc,
+                         (kt > 0 || kk > 0) ? 1u : 0u);
+            mma_commit(&bars[s]);
+        }
+        ++issued;
+    }
+    cp_async_wait<0>();
+    // every thread waits for the last commit (all MMAs issued before it are then complete)
+    bool f_ok = true;
+    if (issued > 0) {
+        const int last = issued - 1;
+        f_ok = mbar_wait(&bars[last % TC_STAGES], (last / TC_STAGES) & 1u);
+    }
+    ok = __syncthreads_and(ok && f_ok);
+    if (!ok && tid == 0 && status) atomicExch(status, TC_ERR_TIMEOUT);
+    tc_fence_after();
+    if (ok) {
+        const int row = m0 + warp * 32 + lane;
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            float v[16];
+            tmem_ld16(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0, v);
+            if (row < M) {
+                float* dr = D + (size_t)row * ldd + n0 + c0;
+                if (n0 + c0 + 16 <= N && (ldd & 3) == 0) {
+#pragma unroll
+                    for (int j = 0; j < 16; j += 4)
+                        *reinterpret_cast<float4*>(dr + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (n0 + c0 + j < N) dr[j] = v[j];
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_free(tmem, BN);
+}
+
+}  // namespace tc
+}  // namespace cb
