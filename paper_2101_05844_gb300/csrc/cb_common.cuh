@@ -10,7 +10,7 @@
 
 // Kernel ids for per-kernel timing (as_kernel_times).
 enum { CB_K_AS_COLA = 0, CB_K_AS_ROWB, CB_K_REDUCE, CB_K_SP_COLA, CB_K_SP_ROWB, CB_K_SP_COLC,
-       CB_K_SPI_ROW, CB_K_SPI_COL, CB_NPROF };
+       CB_K_SPI_ROW, CB_K_SPI_COL, CB_K_TC_COL, CB_K_TC_ROW, CB_K_SLOT_SUMS, CB_NPROF };
 
 // One affine layer k (1-based in the paper; stored at index k-1).
 struct DLayer {
@@ -39,6 +39,22 @@ struct DLayer {
     int Hpo, Wpo, hl, wl;  // output plane with halo (conv): rows hl .. hl + ho - 1 are the outputs
 };
 
+#define CB_MAXPH 9   // stride phases of a conv layer in the BF16 form (stride <= 3)
+
+// BF16 form of the Active Set passes, per hidden-output layer: the tensor-core operands
+// (channels-last planes, channels padded to a multiple of 8, zero padding and halo) and products.
+// Slot 0 carries the unmasked operand (x*, resp. rp), slot 1 + b the operand of active-set slot b.
+struct BfLayer {
+    int Cip, Cop;             // input / output channels rounded up to 8
+    long long PX, PR;         // elements of an input plane [Hp][Wp][Cip], of an output plane [Hpo][Wpo][Cop]
+    uint16_t* X;              // [1 + cap][S][2][Hp][Wp][Cip] bf16: x* (slot 0), x* p_b (sign 0) and x* q_b (sign 1)
+    uint16_t* R;              // [1 + cap][S][Hpo][Wpo][Cop] bf16: rp (slot 0), bz_b
+    float* Drow;              // [(1 + cap) S Ho Wo][co]: W x* (slot 0) and (W o I_b) x* per output neuron
+    int nph;                  // stride phases (stride^2); input j = (c, y, x) is in phase (y + pad) % st, (x + pad) % st
+    float* Dcol[CB_MAXPH];    // per phase [(1 + cap) S nY nX][2 ci]: W+^T and W-^T products per input
+    int Y0a[CB_MAXPH], X0a[CB_MAXPH], nY[CB_MAXPH], nX[CB_MAXPH];   // (y + pad) / st spans nY values from Y0a
+};
+
 struct DNet {
     int n;                 // affine layers; hidden layers k = 1..n-1
     int S, NT, NH, cap;    // subproblems, all neurons (layers 0..n-1), hidden neurons, max slots
@@ -47,6 +63,7 @@ struct DNet {
     DLayer L[CB_MAXL];
     const float* Wout;     // [S][n_{n-1}] property-folded output row
     const float* bout;     // [S]
+    const BfLayer* bf;     // [n - 1] device array, BF16 form only (else null)
 };
 
 // Solver schedule constants (float32 copies prepared on the host from the double options).

@@ -1,8 +1,9 @@
 // BF16 tensor-core GEMM on the 5th-generation tensor cores of sm_103a (tcgen05):
 //   D[M][N] (float32) = A[M][K] (bf16) . B[N][K]^T (bf16)
 // Both operands are K-major (rows of K contiguous elements), as the masked products of the
-// Active Set iteration present them: rows of A are (subproblem, slot) inputs, rows of B are the
-// sign-split weights [W+ | W-] (row pass) or their transposes (col pass).
+// Active Set iteration present them: rows of A are (slot, subproblem, position) inputs gathered
+// from channels-last planes (an implicit-GEMM convolution, see Gather), rows of B the sign-split
+// weights per output channel (row pass) or input channel (col pass).
 //
 // A CTA of 128 threads owns a 128 x BN tile of D, accumulated in tensor memory (TMEM: lane = row,
 // column = output column, float32). K advances in tiles of 64: every thread stages 16-byte pieces
@@ -19,12 +20,15 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "cb_common.cuh"
+
 namespace cb {
 namespace tc {
 
 constexpr int TC_BM = 128, TC_BK = 64, TC_THREADS = 128, TC_STAGES = 2;
 constexpr uint32_t TC_WAIT_LIMIT = 1u << 24;   // try_wait rounds before a barrier counts as lost
 constexpr int TC_ERR_TIMEOUT = 6;             // value written to *status (AS_ERR_TIMEOUT)
+constexpr int TC_ZERO_CHUNK = -2147483647 - 1; // K-offset marking a chunk of zeros
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -135,22 +139,58 @@ __device__ __forceinline__ void stage_tile(uint32_t dst, const uint16_t* src, in
     }
 }
 
-template <int BN>
-constexpr int tc_smem_bytes() {
-    return TC_STAGES * (TC_BM * TC_BK * 2 + BN * TC_BK * 2) + 64;
+// Rows of the A operand gathered from a bf16 array: row m of A starts at element
+//   rowbase(m) = (m / P) * plane + ((m % P) / Wq) * ry + ((m % P) % Wq) * rx + r0
+// and its K-chunk c (8 consecutive K elements, 16 bytes) at rowbase(m) + kofs[c] (kofs == null:
+// 8 c, a dense row-major matrix; kofs[c] == TC_ZERO_CHUNK: a chunk of zeros; offsets may be
+// negative, relative to the row base). With channels-last planes padded to a multiple of 8
+// channels this is an implicit-GEMM convolution: (m / P) picks the plane of a (slot, subproblem),
+// (m % P) the output position, kofs the kernel tap and the channel octet.
+struct Gather {
+    const uint16_t* base;
+    long long plane;
+    int P, Wq;
+    int ry, rx, r0;
+    const int* kofs;
+};
+
+__device__ __forceinline__ long long gather_rowbase(const Gather& g, int m) {
+    const int q = m / g.P, p = m - q * g.P;
+    const int y = p / g.Wq, x = p - y * g.Wq;
+    return (long long)q * g.plane + (long long)y * g.ry + (long long)x * g.rx + g.r0;
 }
 
-// D = A . B^T with A [M][K] (row stride lda), B [N][K] (ldb), D [M][N] (ldd); K, lda, ldb
-// multiples of 8 (16-byte rows pieces). Grid (ceil(M / 128), ceil(N / BN)).
+// Stage 128 rows x 64 K of the gathered A operand (row bases of the tile in rb[]).
+__device__ __forceinline__ void stage_gather(uint32_t dst, const Gather& g, const long long* rb, int row0, int nrows,
+                                             int k0, int k_end) {
+    for (int c = threadIdx.x; c < TC_BM * 8; c += TC_THREADS) {
+        const int r = c >> 3, k8 = c & 7;
+        const int gk = k0 + k8 * 8;
+        int ko = TC_ZERO_CHUNK;
+        if (row0 + r < nrows && gk < k_end) ko = g.kofs ? __ldg(g.kofs + (gk >> 3)) : gk;
+        const bool in = ko != TC_ZERO_CHUNK;
+        const uint16_t* p = in ? g.base + rb[r] + ko : g.base;
+        cp_async16(dst + static_cast<uint32_t>((((r >> 3) * 8) + k8) * 128 + (r & 7) * 16), p, in ? 16u : 0u);
+    }
+}
+
 template <int BN>
-__global__ void __launch_bounds__(TC_THREADS) k_gemm_bf16(const uint16_t* __restrict__ A, int lda,
-                                                          const uint16_t* __restrict__ B, int ldb, float* __restrict__ D,
-                                                          int ldd, int M, int N, int K, int* status) {
+constexpr int tc_smem_bytes() {
+    return TC_STAGES * (TC_BM * TC_BK * 2 + BN * TC_BK * 2) + 64 + TC_BM * 8;
+}
+
+// One CTA's 128 x BN tile (blockIdx.x, blockIdx.y) of D = A . B^T with A [M][K] gathered as
+// described by ga, B [N][K] (row stride ldb), D [M][N] (row stride ldd); K and ldb multiples of 8
+// (16-byte row pieces).
+template <int BN>
+__device__ __forceinline__ void gemm_tile(const Gather& ga, const uint16_t* __restrict__ B, int ldb,
+                                          float* __restrict__ D, int ldd, int M, int N, int K, int* status) {
     static_assert(BN == 32 || BN == 64 || BN == 128 || BN == 256, "BN");
-    extern __shared__ __align__(1024) uint8_t smem[];
+    extern __shared__ __align__(128) uint8_t smem[];
     constexpr int A_BYTES = TC_BM * TC_BK * 2, B_BYTES = BN * TC_BK * 2, STAGE = A_BYTES + B_BYTES;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + TC_STAGES * STAGE);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + TC_STAGES);
+    long long* rb = reinterpret_cast<long long*>(smem + TC_STAGES * STAGE + 64);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * BN;
     if (warp == 0) tmem_alloc(tslot, BN);
@@ -158,6 +198,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_bf16(const uint16_t* __rest
         for (int s = 0; s < TC_STAGES; ++s) mbar_init(&bars[s], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    for (int r = tid; r < TC_BM; r += TC_THREADS) rb[r] = m0 + r < M ? gather_rowbase(ga, m0 + r) : 0;
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -167,7 +208,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_bf16(const uint16_t* __rest
     const int KT = (K + TC_BK - 1) / TC_BK;
     bool ok = true;
 
-    stage_tile(sbase, A, lda, m0, M, 0, K, TC_BM);
+    stage_gather(sbase, ga, rb, m0, M, 0, K);
     stage_tile(sbase + A_BYTES, B, ldb, n0, N, 0, K, BN);
     cp_async_commit();
     int issued = 0;   // commits issued by thread 0 (stage of commit c: c % TC_STAGES)
@@ -183,7 +224,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_bf16(const uint16_t* __rest
         }
         if (kt + 1 < KT) {
             const uint32_t st = sbase + ((kt + 1) % TC_STAGES) * STAGE;
-            stage_tile(st, A, lda, m0, M, (kt + 1) * TC_BK, K, TC_BM);
+            stage_gather(st, ga, rb, m0, M, (kt + 1) * TC_BK, K);
             stage_tile(st + A_BYTES, B, ldb, n0, N, (kt + 1) * TC_BK, K, BN);
             cp_async_commit();
             cp_async_wait<1>();
@@ -236,6 +277,49 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_bf16(const uint16_t* __rest
     tc_fence_before();
     __syncthreads();
     if (warp == 0) tmem_free(tmem, BN);
+}
+
+template <int BN>
+__global__ void __launch_bounds__(TC_THREADS) k_gemm_bf16(Gather ga, const uint16_t* __restrict__ B, int ldb,
+                                                          float* __restrict__ D, int ldd, int M, int N, int K,
+                                                          int* status) {
+    gemm_tile<BN>(ga, B, ldb, D, ldd, M, N, K, status);
+}
+
+// Up to CB_MAXPH GEMMs of one shape class in one launch (blockIdx.z picks one): the stride phases
+// of a transposed convolution, or a single row-pass GEMM. The rows in use follow the Active Set
+// schedule read from the device iteration counter: (1 + slots) x rows_per_slot, where slots is
+// the number of active-set slots the pass consumes (row pass: those added up to and including
+// the current iteration; col pass: before it). CTAs past the rows in use return at once.
+struct GemmGroup {
+    Gather ga[CB_MAXPH];
+    const uint16_t* B[CB_MAXPH];
+    float* D[CB_MAXPH];
+    int M[CB_MAXPH];              // rows for all 1 + cap slots
+    int K[CB_MAXPH];
+    int rows_per_slot[CB_MAXPH];
+    int ldb[CB_MAXPH];
+    int N, ldd;
+    const int* ctr;               // device iteration counter
+    DSched sc;
+    int row_pass;
+};
+
+template <int BN>
+__global__ void __launch_bounds__(TC_THREADS) k_gemm_group_bf16(GemmGroup gg, int* status) {
+    const int g = blockIdx.z;
+    const int it = *gg.ctr;
+    int ns = 0;
+    if (it >= gg.sc.TM) {
+        const int t = it - gg.sc.TM;
+        ns = cb_additions_before(t, gg.sc);
+        if (gg.row_pass && cb_slot_at(t, gg.sc) >= 0) ++ns;
+        ns = ns < gg.sc.maxcut ? ns : gg.sc.maxcut;
+    }
+    const long long want = (long long)(1 + ns) * gg.rows_per_slot[g];
+    const int M = want < gg.M[g] ? (int)want : gg.M[g];
+    if ((int)blockIdx.x * TC_BM >= M) return;   // the whole CTA leaves together, before any barrier
+    gemm_tile<BN>(gg.ga[g], gg.B[g], gg.ldb[g], gg.D[g], gg.ldd, M, gg.N, gg.K[g], status);
 }
 
 }  // namespace tc

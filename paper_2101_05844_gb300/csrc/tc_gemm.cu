@@ -18,7 +18,8 @@ cudaError_t launch(const uint16_t* A, int lda, const uint16_t* B, int ldb, float
     cudaError_t e = cudaFuncSetAttribute(k_gemm_bf16<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((M + TC_BM - 1) / TC_BM, (N + BN - 1) / BN);
-    k_gemm_bf16<BN><<<grid, TC_THREADS, smem, s>>>(A, lda, B, ldb, D, ldd, M, N, K, status);
+    Gather ga{A, (long long)lda, 1, 1, 0, 0, 0, nullptr};   // dense: row m at m * lda
+    k_gemm_bf16<BN><<<grid, TC_THREADS, smem, s>>>(ga, B, ldb, D, ldd, M, N, K, status);
     return cudaGetLastError();
 }
 }  // namespace
