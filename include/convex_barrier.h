@@ -80,6 +80,14 @@ typedef struct as_options {
     int track_best;      /* 1: evaluate the bound at every iteration and keep the best        */
     int graph_chunk;     /* iterations per captured CUDA graph (0: plain launches)           */
     int profile;         /* 1: time every kernel with CUDA events (disables graphs)           */
+    int precision;       /* products of the Big-M / Active Set passes: 32 (float32, default) or
+                          * 16 (the BF16 form: W x* and every masked product (W o I_b) x*, W^T and
+                          * every masked W^T product run on the tensor cores with bf16 operands
+                          * (W, x*, the dual row sums) and float32 accumulation; duals, Adam and
+                          * the mask decisions stay float32; lambda, kappa of every slot are
+                          * recomputed in float32 after each addition; as_bound re-evaluates the
+                          * bound in float32 with float64 summation). Saddle Point runs in
+                          * float32 on any context.                                        */
 } as_options;
 
 typedef struct as_ctx as_ctx;
@@ -185,10 +193,14 @@ long long as_launch_count(as_ctx* ctx);
 #define AS_K_REDUCE 2  /* bound reduction                                              */
 #define AS_K_SP_COLA 3 /* Saddle Point col pass: f, primal conditional gradient        */
 #define AS_K_SP_ROWB 4 /* Saddle Point row pass: oracle, dual conditional gradient     */
-#define AS_K_SP_COLC 5 /* Saddle Point col pass: masked backward, convex combination   */
+#define AS_K_SP_COLC 5 /* Saddle Point col pass: masked backward and convex combination,
+                          fused with the next iteration's phase A                      */
 #define AS_K_SPI_ROW 6 /* Saddle Point primal initialisation, row pass                 */
 #define AS_K_SPI_COL 7 /* Saddle Point primal initialisation, col pass                 */
-#define AS_K_COUNT 8
+#define AS_K_TC_COL 8  /* BF16 form: tensor-core products of the col pass              */
+#define AS_K_TC_ROW 9  /* BF16 form: tensor-core products of the row pass              */
+#define AS_K_SLOT_SUMS 10 /* BF16 form: float32 lambda, kappa after an addition        */
+#define AS_K_COUNT 11
 
 /* With as_options.profile set: total device time (CUDA events on the context's stream) and
  * launch count of one kernel over the context's life so far. Synchronises the stream. */

@@ -27,7 +27,8 @@ MAX_LAYERS, MAX_CUTS = 10, 8
 EXPORTS = ["as_default_options", "as_init", "as_reset", "as_step", "sp_step", "as_bound",
            "as_bound_backward", "as_state_size", "as_get_state", "as_set_state", "as_launch_count",
            "as_kernel_times", "as_destroy", "as_last_error", "as_ibp_noalloc", "as_gemm_bf16"]
-KERNELS = ["as_colA", "as_rowB", "reduce", "sp_colA", "sp_rowB", "sp_colC", "spi_row", "spi_col"]
+KERNELS = ["as_colA", "as_rowB", "reduce", "sp_colA", "sp_rowB", "sp_colC", "spi_row", "spi_col", "tc_col",
+           "tc_row", "slot_sums"]
 
 
 class Layer(ct.Structure):
@@ -49,7 +50,8 @@ class Options(ct.Structure):
                 ("adam_b1", ct.c_double), ("adam_b2", ct.c_double), ("adam_eps", ct.c_double),
                 ("sp_gamma0", ct.c_double), ("sp_c_alpha", ct.c_double), ("sp_c_beta", ct.c_double),
                 ("sp_init_steps", ct.c_int), ("sp_init_lr0", ct.c_double), ("sp_init_lr1", ct.c_double),
-                ("track_best", ct.c_int), ("graph_chunk", ct.c_int), ("profile", ct.c_int)]
+                ("track_best", ct.c_int), ("graph_chunk", ct.c_int), ("profile", ct.c_int),
+                ("precision", ct.c_int)]
 
 
 _lib = None

@@ -181,8 +181,23 @@ __global__ void k_grad_box(DNet net, DState st, GradCtx gc, float* dlo, float* d
     if (dhi) dhi[u] += (float)(gc.gb[s] * (double)ah);
 }
 
+__device__ __forceinline__ void slot_sums_body(const DNet& net, const DState& st, const Segs& sg, int nadd, int bo);
+
 // lambda, kappa of every filled slot from the snapshot bits (after the caller replaced them).
 __global__ void __launch_bounds__(CB_THREADS) k_slot_sums(DNet net, DState st, Segs sg, int nadd, int bo) {
+    slot_sums_body(net, st, sg, nadd, bo);
+}
+
+// The same in float32 after an Active Set iteration that added a slot (BF16 form: the iteration
+// took the new slot's lambda from its bf16 products); returns at once after other iterations.
+__global__ void __launch_bounds__(CB_THREADS) k_slot_sums_after_add(DNet net, DState st, DSched sc, Segs sg) {
+    const int it = st.ctr[0] - 1;   // the iteration that just ended
+    if (it < sc.TM || cb_slot_at(it - sc.TM, sc) < 0) return;
+    const int nadd = cb_additions_before(it - sc.TM + 1, sc);
+    slot_sums_body(net, st, sg, nadd, nadd & 1);
+}
+
+__device__ __forceinline__ void slot_sums_body(const DNet& net, const DState& st, const Segs& sg, int nadd, int bo) {
     const int q = seg_of(sg, blockIdx.x);
     const DLayer& L = net.L[sg.layer[q]];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;

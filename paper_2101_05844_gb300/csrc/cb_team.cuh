@@ -19,6 +19,8 @@
 // the masked backward product of eq. (6) regrouped by the sign of W (exact: eq. 3 at binary iterates
 // sets I_b(i, j) from z_b[i], the sign of W_ij and p_b / q_b only).
 #pragma once
+#include <cuda_bf16.h>
+
 #include "cb_kernels.cuh"
 
 namespace cb {
@@ -221,14 +223,36 @@ __device__ __forceinline__ void load_taps(const int2* tap, int t, int tb, int T,
 // with no per-pair mask work; the input's own bits pick p_b Pp_b + q_b Pn_b at the end.
 template <int NS>
 __device__ __forceinline__ void as_colA_body(const DNet& net, const DState& st, const DSched& sc, const DLayer& L,
-                                             int k, bool valid, int s, int j, int lane, int T, int mode) {
+                                             int k, bool valid, int s, int j, int lane, int T, int mode, bool tc) {
     const int m = k - 1;
     const Step sp = cb_step(st.ctr[0], sc, st.lr_tab);
     const size_t NT = net.NT, NH = net.NH, cap = net.cap;
     float acc = 0.f, Pp[NS > 0 ? NS : 1], Pn[NS > 0 ? NS : 1];
 #pragma unroll
     for (int b = 0; b < NS; ++b) Pp[b] = Pn[b] = 0.f;
-    if (valid && k <= net.n - 1) {
+    if (valid && k <= net.n - 1 && tc) {
+        // BF16 form: the sums come from the tensor-core products of this input's stride phase
+        const BfLayer& B = net.bf[k - 1];
+        int c = j, ph = 0, q = 0;
+        if (L.kind == 1) {
+            const int hw = L.hi * L.wi;
+            c = j / hw;
+            const int rem = j - c * hw, y = rem / L.wi, x = rem - y * L.wi;
+            const int ty = y + L.pd, tx = x + L.pd;
+            const int Y0 = ty / L.st, X0 = tx / L.st;
+            ph = (ty - Y0 * L.st) * L.st + (tx - X0 * L.st);
+            q = (Y0 - B.Y0a[ph]) * B.nX[ph] + (X0 - B.X0a[ph]);
+        }
+        const int P = B.nY[ph] * B.nX[ph], ld = 2 * L.ci;
+        const size_t slot = (size_t)net.S * P * ld;
+        const float* d = B.Dcol[ph] + ((size_t)s * P + q) * ld + c;
+        acc = d[0] + d[L.ci];
+#pragma unroll
+        for (int b = 0; b < NS; ++b) {
+            Pp[b] = d[(b + 1) * slot];
+            Pn[b] = d[(b + 1) * slot + L.ci];
+        }
+    } else if (valid && k <= net.n - 1) {
         int g, base;
         col_group(L, j, g, base);
         const float4* ar = arec_planes(net, st, L, s) + base;
@@ -324,10 +348,32 @@ __device__ __forceinline__ void as_colA_body(const DNet& net, const DState& st, 
         st.xsnap[bo ^ 1][xo] = (uint8_t)xs_new;
     }
     if (k <= net.n - 1) {
-        // row-pass input record: x* and the slot masks p_b (bits 0-7) and q_b (bits 8-15)
         const unsigned mpos = ((~xs_new) & 0xFFu) | fxm, mneg = (xs_new & 0xFFu) | fxm;
-        reinterpret_cast<float2*>(st.xin + (size_t)s * net.XT + L.xo)[xin_pos(L, j)] =
-            make_float2(xv, __uint_as_float(mpos | (mneg << 8)));
+        if (tc) {
+            // BF16 form: the row pass's tensor-core operand, x* (slot 0) and x* p_b / x* q_b
+            const BfLayer& B = net.bf[k - 1];
+            int c = j, y = 0, x = 0;
+            if (L.kind == 1) {
+                const int hw = L.hi * L.wi;
+                c = j / hw;
+                const int rem = j - c * hw;
+                y = rem / L.wi;
+                x = rem - y * L.wi;
+            }
+            const long long off = ((long long)(y + L.pd) * L.Wp + (x + L.pd)) * B.Cip + c;
+            const __nv_bfloat16 xb = __float2bfloat16_rn(xv), zero = __float2bfloat16_rn(0.f);
+            __nv_bfloat16* X = reinterpret_cast<__nv_bfloat16*>(B.X);
+            for (int t = 0; t <= net.cap; ++t) {
+                const long long pl = ((long long)t * net.S + s) * 2;
+                const bool p = t == 0 || ((mpos >> (t - 1)) & 1u), qq = t == 0 || ((mneg >> (t - 1)) & 1u);
+                X[pl * B.PX + off] = p ? xb : zero;
+                X[(pl + 1) * B.PX + off] = qq ? xb : zero;
+            }
+        } else {
+            // row-pass input record: x* and the slot masks p_b (bits 0-7) and q_b (bits 8-15)
+            reinterpret_cast<float2*>(st.xin + (size_t)s * net.XT + L.xo)[xin_pos(L, j)] =
+                make_float2(xv, __uint_as_float(mpos | (mneg << 8)));
+        }
     }
 }
 
@@ -340,7 +386,8 @@ __device__ __forceinline__ int tseg_of(const TSegs& sg, int blk) {
 // Col pass over layers k = 1..n (phase A of an iteration, or the bound evaluation with mode 1):
 // f_m for every neuron j of layer m = k-1 (Sec. 4.1), x*, z* (eqs. 7-8), per-neuron bound terms
 // (eq. 6) and, on addition iterations, the new slot's snapshot bits (Alg. 1, Prop. 1).
-__global__ void __launch_bounds__(CB_THREADS, 4) k_as_colA_t(DNet net, DState st, DSched sc, TSegs sg, int mode) {
+__global__ void __launch_bounds__(CB_THREADS, 4) k_as_colA_t(DNet net, DState st, DSched sc, TSegs sg, int mode,
+                                                              int tc) {
     const int q = tseg_of(sg, blockIdx.x);
     const int li = sg.layer[q];
     const DLayer& L = net.L[li];
@@ -353,15 +400,15 @@ __global__ void __launch_bounds__(CB_THREADS, 4) k_as_colA_t(DNet net, DState st
     const Step sp = cb_step(st.ctr[0], sc, st.lr_tab);
     const int ns = min(sp.nadd_before, sc.maxcut);
     switch (ns) {
-        case 0: as_colA_body<0>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode); break;
-        case 1: as_colA_body<1>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode); break;
-        case 2: as_colA_body<2>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode); break;
-        case 3: as_colA_body<3>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode); break;
-        case 4: as_colA_body<4>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode); break;
-        case 5: as_colA_body<5>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode); break;
-        case 6: as_colA_body<6>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode); break;
-        case 7: as_colA_body<7>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode); break;
-        default: as_colA_body<8>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode); break;
+        case 0: as_colA_body<0>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, tc != 0); break;
+        case 1: as_colA_body<1>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, tc != 0); break;
+        case 2: as_colA_body<2>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, tc != 0); break;
+        case 3: as_colA_body<3>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, tc != 0); break;
+        case 4: as_colA_body<4>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, tc != 0); break;
+        case 5: as_colA_body<5>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, tc != 0); break;
+        case 6: as_colA_body<6>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, tc != 0); break;
+        case 7: as_colA_body<7>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, tc != 0); break;
+        default: as_colA_body<8>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, tc != 0); break;
     }
 }
 
@@ -379,7 +426,8 @@ __global__ void __launch_bounds__(CB_THREADS, 4) k_as_colA_t(DNet net, DState st
 // in exact arithmetic.
 template <int NS, bool ADD>
 __device__ __forceinline__ void as_rowB_body(const DNet& net, const DState& st, const DSched& sc, const DLayer& L,
-                                             bool valid, int s, int i, int lane, int T, const Step& sp, int it) {
+                                             int li, bool valid, int s, int i, int lane, int T, const Step& sp, int it,
+                                             bool tc) {
     const size_t NT = net.NT, NH = net.NH, cap = net.cap;
     const int cap_s = valid ? st.caps[s] : 0;
     const int newb = (ADD && sp.b_new < cap_s) ? sp.b_new : -1;
@@ -390,7 +438,21 @@ __device__ __forceinline__ void as_rowB_body(const DNet& net, const DState& st, 
     float acc[NS > 0 ? NS : 1];
 #pragma unroll
     for (int b = 0; b < NS; ++b) acc[b] = 0.f;
-    if (valid) {
+    // BF16 form: output channel and position of this row
+    int co = i, p = 0;
+    if (L.kind == 1) {
+        const int hw = L.ho * L.wo;
+        co = i / hw;
+        p = i - co * hw;
+    }
+    if (valid && tc) {
+        const int P = L.ho * L.wo;
+        const size_t slot = (size_t)net.S * P * L.co;
+        const float* d = net.bf[li].Drow + ((size_t)s * P + p) * L.co + co;
+        acc0 = d[0];
+#pragma unroll
+        for (int b = 0; b < NS; ++b) acc[b] = d[(b + 1) * slot];
+    } else if (valid) {
         int g, base;
         row_group(L, i, g, base);
         const float2* xb = reinterpret_cast<const float2*>(st.xin + (size_t)s * net.XT + L.xo) + base;
@@ -434,6 +496,19 @@ __device__ __forceinline__ void as_rowB_body(const DNet& net, const DState& st, 
         const float xhat = acc0 + bi;
         const size_t hs0 = (size_t)s * cap * NH + L.h_out + i;
         const int ap = arec_pos(L, i);
+        // the col pass's record entry e of this row: float32 plane, or (BF16 form) bf16 operand
+        long long roff = 0;
+        if (tc) {
+            const int oy = p / L.wo, ox = p - (p / L.wo) * L.wo;
+            roff = ((long long)(oy + L.hl) * L.Wpo + (ox + L.wl)) * net.bf[li].Cop + co;
+        }
+        auto put = [&](int e, float v) {
+            if (tc)
+                reinterpret_cast<__nv_bfloat16*>(net.bf[li].R)[((long long)e * net.S + s) * net.bf[li].PR + roff] =
+                    __float2bfloat16_rn(v);
+            else
+                *arec_entry(net, st, L, s, ap, e) = v;
+        };
         for (int v = lane; v < 3 + NS; v += T) {
             if (v < 3) {
                 float* th = v == 0 ? st.alpha : (v == 1 ? st.beta0 : st.beta1);
@@ -449,7 +524,7 @@ __device__ __forceinline__ void as_rowB_body(const DNet& net, const DState& st, 
                 if (v == 2) contrib += nv;
             } else {
                 const int b = v - 3;
-                if (b >= nsl) { *arec_entry(net, st, L, s, ap, 1 + b) = 0.f; continue; }
+                if (b >= nsl) { put(1 + b, 0.f); continue; }
                 const size_t hs = hs0 + (size_t)b * NH;
                 float lam, kap;
                 float ab = 0.f;
@@ -475,15 +550,24 @@ __device__ __forceinline__ void as_rowB_body(const DNet& net, const DState& st, 
                                            inv_bias_corr(st.bc2_tab, sc.ntab, sstep, sc.b2), sc);
                 st.bs[hs] = nv; st.ms[hs] = m; st.vs[hs] = w2;
                 if (zb) contrib += nv;
-                *arec_entry(net, st, L, s, ap, 1 + b) = zb ? 0.f : nv;
+                put(1 + b, zb ? 0.f : nv);
             }
         }
     }
     if (T > 1) contrib = team_sum(contrib, T);
-    if (valid && lane == 0) *arec_entry(net, st, L, s, arec_pos(L, i), 0) = contrib;
+    if (valid && lane == 0) {
+        if (tc) {
+            const BfLayer& B = net.bf[li];
+            const int oy = p / L.wo, ox = p - (p / L.wo) * L.wo;
+            const long long roff = ((long long)(oy + L.hl) * L.Wpo + (ox + L.wl)) * B.Cop + co;
+            reinterpret_cast<__nv_bfloat16*>(B.R)[(long long)s * B.PR + roff] = __float2bfloat16_rn(contrib);
+        } else {
+            *arec_entry(net, st, L, s, arec_pos(L, i), 0) = contrib;
+        }
+    }
 }
 
-__global__ void __launch_bounds__(CB_THREADS, 4) k_as_rowB_t(DNet net, DState st, DSched sc, TSegs sg) {
+__global__ void __launch_bounds__(CB_THREADS, 4) k_as_rowB_t(DNet net, DState st, DSched sc, TSegs sg, int tc) {
     const int q = tseg_of(sg, blockIdx.x);
     const DLayer& L = net.L[sg.layer[q]];
     const int T = sg.T[q];
@@ -496,26 +580,26 @@ __global__ void __launch_bounds__(CB_THREADS, 4) k_as_rowB_t(DNet net, DState st
     const int ns = min(sp.nadd_before + (sp.b_new >= 0 ? 1 : 0), sc.maxcut);
     if (sp.b_new >= 0) {
         switch (ns) {
-            case 1: as_rowB_body<1, true>(net, st, sc, L, valid, s, i, lane, T, sp, it); break;
-            case 2: as_rowB_body<2, true>(net, st, sc, L, valid, s, i, lane, T, sp, it); break;
-            case 3: as_rowB_body<3, true>(net, st, sc, L, valid, s, i, lane, T, sp, it); break;
-            case 4: as_rowB_body<4, true>(net, st, sc, L, valid, s, i, lane, T, sp, it); break;
-            case 5: as_rowB_body<5, true>(net, st, sc, L, valid, s, i, lane, T, sp, it); break;
-            case 6: as_rowB_body<6, true>(net, st, sc, L, valid, s, i, lane, T, sp, it); break;
-            case 7: as_rowB_body<7, true>(net, st, sc, L, valid, s, i, lane, T, sp, it); break;
-            default: as_rowB_body<8, true>(net, st, sc, L, valid, s, i, lane, T, sp, it); break;
+            case 1: as_rowB_body<1, true>(net, st, sc, L, sg.layer[q], valid, s, i, lane, T, sp, it, tc != 0); break;
+            case 2: as_rowB_body<2, true>(net, st, sc, L, sg.layer[q], valid, s, i, lane, T, sp, it, tc != 0); break;
+            case 3: as_rowB_body<3, true>(net, st, sc, L, sg.layer[q], valid, s, i, lane, T, sp, it, tc != 0); break;
+            case 4: as_rowB_body<4, true>(net, st, sc, L, sg.layer[q], valid, s, i, lane, T, sp, it, tc != 0); break;
+            case 5: as_rowB_body<5, true>(net, st, sc, L, sg.layer[q], valid, s, i, lane, T, sp, it, tc != 0); break;
+            case 6: as_rowB_body<6, true>(net, st, sc, L, sg.layer[q], valid, s, i, lane, T, sp, it, tc != 0); break;
+            case 7: as_rowB_body<7, true>(net, st, sc, L, sg.layer[q], valid, s, i, lane, T, sp, it, tc != 0); break;
+            default: as_rowB_body<8, true>(net, st, sc, L, sg.layer[q], valid, s, i, lane, T, sp, it, tc != 0); break;
         }
     } else {
         switch (ns) {
-            case 0: as_rowB_body<0, false>(net, st, sc, L, valid, s, i, lane, T, sp, it); break;
-            case 1: as_rowB_body<1, false>(net, st, sc, L, valid, s, i, lane, T, sp, it); break;
-            case 2: as_rowB_body<2, false>(net, st, sc, L, valid, s, i, lane, T, sp, it); break;
-            case 3: as_rowB_body<3, false>(net, st, sc, L, valid, s, i, lane, T, sp, it); break;
-            case 4: as_rowB_body<4, false>(net, st, sc, L, valid, s, i, lane, T, sp, it); break;
-            case 5: as_rowB_body<5, false>(net, st, sc, L, valid, s, i, lane, T, sp, it); break;
-            case 6: as_rowB_body<6, false>(net, st, sc, L, valid, s, i, lane, T, sp, it); break;
-            case 7: as_rowB_body<7, false>(net, st, sc, L, valid, s, i, lane, T, sp, it); break;
-            default: as_rowB_body<8, false>(net, st, sc, L, valid, s, i, lane, T, sp, it); break;
+            case 0: as_rowB_body<0, false>(net, st, sc, L, sg.layer[q], valid, s, i, lane, T, sp, it, tc != 0); break;
+            case 1: as_rowB_body<1, false>(net, st, sc, L, sg.layer[q], valid, s, i, lane, T, sp, it, tc != 0); break;
+            case 2: as_rowB_body<2, false>(net, st, sc, L, sg.layer[q], valid, s, i, lane, T, sp, it, tc != 0); break;
+            case 3: as_rowB_body<3, false>(net, st, sc, L, sg.layer[q], valid, s, i, lane, T, sp, it, tc != 0); break;
+            case 4: as_rowB_body<4, false>(net, st, sc, L, sg.layer[q], valid, s, i, lane, T, sp, it, tc != 0); break;
+            case 5: as_rowB_body<5, false>(net, st, sc, L, sg.layer[q], valid, s, i, lane, T, sp, it, tc != 0); break;
+            case 6: as_rowB_body<6, false>(net, st, sc, L, sg.layer[q], valid, s, i, lane, T, sp, it, tc != 0); break;
+            case 7: as_rowB_body<7, false>(net, st, sc, L, sg.layer[q], valid, s, i, lane, T, sp, it, tc != 0); break;
+            default: as_rowB_body<8, false>(net, st, sc, L, sg.layer[q], valid, s, i, lane, T, sp, it, tc != 0); break;
         }
     }
     if (last_block(&st.done[0]) && threadIdx.x == 0) {
@@ -524,8 +608,9 @@ __global__ void __launch_bounds__(CB_THREADS, 4) k_as_rowB_t(DNet net, DState st
     }
 }
 
-// rp and bz from the current duals and snapshots (after a state import).
-__global__ void k_rowprep(DNet net, DState st, DSched sc) {
+// rp and bz from the current duals and snapshots (after a state import): the float32 output
+// records, or with tc the BF16 form's bf16 operand planes.
+__global__ void k_rowprep(DNet net, DState st, DSched sc, int tc) {
     const size_t n = (size_t)net.S * net.NH;
     const Step sp = cb_step(st.ctr[0], sc, st.lr_tab);
     const int bo = sp.nadd_before & 1;
@@ -536,9 +621,28 @@ __global__ void k_rowprep(DNet net, DState st, DSched sc) {
         const DLayer& L = net.L[li];
         const int nsl = min(sp.nadd_before, st.caps[s]);
         const unsigned zs = st.zsnap[bo][u];
-        const int ap = arec_pos(L, hh - L.h_out);
+        const int i = hh - L.h_out;
+        const int ap = arec_pos(L, i);
+        long long roff = 0;
+        if (tc) {
+            int co = i, oy = 0, ox = 0;
+            if (L.kind == 1) {
+                const int hw = L.ho * L.wo;
+                co = i / hw;
+                oy = (i - co * hw) / L.wo;
+                ox = i - co * hw - oy * L.wo;
+            }
+            roff = ((long long)(oy + L.hl) * L.Wpo + (ox + L.wl)) * net.bf[li].Cop + co;
+        }
+        auto put = [&](int e, float v) {
+            if (tc)
+                reinterpret_cast<__nv_bfloat16*>(net.bf[li].R)[((long long)e * net.S + s) * net.bf[li].PR + roff] =
+                    __float2bfloat16_rn(v);
+            else
+                *arec_entry(net, st, L, s, ap, e) = v;
+        };
         float r = -(st.alpha[u] - st.beta1[u]);
-        for (int b = 0; b < net.RS - 1; ++b) {
+        for (int b = 0; b < (tc ? net.cap : net.RS - 1); ++b) {
             float bv = 0.f;
             bool zb = false;
             if (b < net.cap) {
@@ -547,9 +651,9 @@ __global__ void k_rowprep(DNet net, DState st, DSched sc) {
                 zb = (zs >> b) & 1u;
             }
             if (zb) r += bv;
-            *arec_entry(net, st, L, s, ap, 1 + b) = zb ? 0.f : bv;
+            put(1 + b, zb ? 0.f : bv);
         }
-        *arec_entry(net, st, L, s, ap, 0) = r;
+        put(0, r);
     }
 }
 

@@ -13,6 +13,7 @@
 #include "cb_kernels.cuh"
 #include "cb_backward.cuh"
 #include "cb_team.cuh"
+#include "cb_tc.cuh"
 
 using namespace cb;
 
@@ -52,6 +53,16 @@ struct as_ctx {
     std::vector<cudaEvent_t> pool;
     double prof_ms[CB_NPROF] = {};
     long long prof_n[CB_NPROF] = {};
+    // BF16 form (as_options.precision = 16)
+    struct TcGemm {
+        tc::GemmGroup g;
+        int ng, maxM, bn;
+    };
+    std::vector<TcGemm> tc_row, tc_col;           // per hidden-output layer
+    std::vector<std::pair<void*, size_t>> planes; // bf16 operand planes, cleared with each batch
+    int* tc_status = nullptr;                     // set by a tensor-core kernel whose wait ran out
+    TSegs tA1{}, tB1{};                           // one lane per unit
+    int blocksTA1 = 0, blocksTB1 = 0;
 };
 
 static int fail(as_ctx* c, int code, const char* fmt, ...) {
@@ -94,6 +105,11 @@ static int dalloc(as_ctx* c, T** p, size_t count) {
         if (r_ != AS_OK) return r_; \
     } while (0)
 
+// defined further down (cb_bf16.inc, cb_host_extra.inc)
+static int clear_planes(as_ctx* c);
+static int build_bf16(as_ctx* c, const std::vector<std::vector<float>>& Wh);
+static int recompute_slot_sums(as_ctx* c);
+
 extern "C" void as_default_options(as_options* o) {
     if (!o) return;
     std::memset(o, 0, sizeof *o);
@@ -117,6 +133,7 @@ extern "C" void as_default_options(as_options* o) {
     o->sp_init_lr1 = 1e-5;
     o->track_best = 0;
     o->graph_chunk = 16;
+    o->precision = 32;
 }
 
 extern "C" const char* as_last_error(as_ctx* c) { return c ? c->err.c_str() : "null context"; }
@@ -191,6 +208,7 @@ static int validate_opt(as_ctx* c, const as_options& o) {
     if (!(o.sp_gamma0 >= 1)) return fail(c, AS_ERR_ARG, "sp_gamma0 < 1");
     if (!(o.sp_c_alpha > 0 && o.sp_c_beta > 0)) return fail(c, AS_ERR_ARG, "price-cap constants must be > 0");
     if (o.sp_init_steps < 0 || o.graph_chunk < 0) return fail(c, AS_ERR_ARG, "negative step counts");
+    if (o.precision != 32 && o.precision != 16) return fail(c, AS_ERR_ARG, "precision must be 32 or 16");
     return AS_OK;
 }
 
@@ -499,6 +517,7 @@ static int load_batch(as_ctx* c, const float* x_lo, const float* x_hi, const flo
     const size_t NT = D.NT, NHS = (size_t)S * D.NH;
     cudaStream_t s = c->stream;
     CUDA_TRY(c, cudaMemsetAsync(c->zero_arena, 0, c->zero_bytes, s));
+    TRY(clear_planes(c));
     k_fill<<<grid_for(S), CB_THREADS, 0, s>>>(st.best, (size_t)S, -INFINITY);
     c->launches++;
     c->sp_started = false;
@@ -682,6 +701,7 @@ static int init_impl(as_ctx* c, const as_net* net, int S, const float* x_lo, con
     TRY(make_team_segs(c));
     TRY(alloc_state(c));
     TRY(build_tables(c));
+    if (c->opt.precision == 16) TRY(build_bf16(c, Wh));
     TRY(load_batch(c, x_lo, x_hi, C, lhat, uhat, splits, caps, true));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     return AS_OK;
@@ -752,10 +772,10 @@ static cudaEvent_t prof_event(as_ctx* c) {
 static int launch_as_iter(as_ctx* c, cudaStream_t s) {
     // the per-neuron bound terms are only summed when the best bound is tracked
     const int mode = c->opt.track_best ? 0 : 2;
-    LAUNCH(c, s, CB_K_AS_COLA, (k_as_colA_t<<<c->blocksTA, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->tA, mode)));
+    LAUNCH(c, s, CB_K_AS_COLA, (k_as_colA_t<<<c->blocksTA, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->tA, mode, 0)));
     if (c->opt.track_best)
         LAUNCH(c, s, CB_K_REDUCE, (k_reduce<<<c->net.S, CB_THREADS, 0, s>>>(c->net, c->st, 64, nullptr, 1)));
-    LAUNCH(c, s, CB_K_AS_ROWB, (k_as_rowB_t<<<c->blocksTB, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->tB)));
+    LAUNCH(c, s, CB_K_AS_ROWB, (k_as_rowB_t<<<c->blocksTB, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->tB, 0)));
     return check_launch(c, "Active Set iteration");
 }
 
@@ -786,6 +806,8 @@ extern "C" int as_kernel_times(as_ctx* c, int kernel, double* total_ms, long lon
     if (launches) *launches = c->prof_n[kernel];
     return AS_OK;
 }
+
+#include "cb_bf16.inc"
 
 typedef int (*iter_fn)(as_ctx*, cudaStream_t);
 
@@ -822,11 +844,13 @@ extern "C" int as_step(as_ctx* c, int n_iters) {
     if (!c) return AS_ERR_ARG;
     if (n_iters < 0) return fail(c, AS_ERR_ARG, "n_iters < 0");
     if (c->sp_started) return fail(c, AS_ERR_STATE, "Saddle Point has started on this context");
-    return run_iters(c, n_iters, launch_as_iter, &c->g_as, &c->g_as_len, &c->g_as_nodes);
+    return run_iters(c, n_iters, c->opt.precision == 16 ? launch_as_iter_bf16 : launch_as_iter, &c->g_as,
+                     &c->g_as_len, &c->g_as_nodes);
 }
 
 static int sp_start(as_ctx* c) {
     cudaStream_t s = c->stream;
+    if (c->opt.precision == 16) TRY(recompute_slot_sums(c));   // float32 lambda, kappa for the conversion
     const size_t NHS = (size_t)c->net.S * c->net.NH;
     k_sp_convert_elem<<<grid_for(NHS), CB_THREADS, 0, s>>>(c->net, c->st, c->sc, (float)c->opt.sp_c_alpha,
                                                            (float)c->opt.sp_c_beta);
@@ -865,7 +889,11 @@ extern "C" int as_bound(as_ctx* c, int precision, double* out, double* best) {
     const int S = c->net.S;
     cudaStream_t s = c->stream;
     if (c->sp_started) LAUNCH(c, s, CB_K_SP_COLA, (k_sp_colA_t<<<c->blocksTA, CB_THREADS, 0, s>>>(c->net, c->st, c->tA, 0)));
-    else LAUNCH(c, s, CB_K_AS_COLA, (k_as_colA_t<<<c->blocksTA, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->tA, 1)));
+    else {
+        // the BF16 form's iterates give a bound through float32 lambda, kappa and records
+        if (c->opt.precision == 16) TRY(recompute_slot_sums(c));
+        LAUNCH(c, s, CB_K_AS_COLA, (k_as_colA_t<<<c->blocksTA, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->tA, 1, 0)));
+    }
     double* dout = c->bound_out;
     LAUNCH(c, s, CB_K_REDUCE, (k_reduce<<<S, CB_THREADS, 0, s>>>(c->net, c->st, precision, dout, 1)));
     TRY(check_launch(c, "bound evaluation"));
@@ -877,6 +905,11 @@ extern "C" int as_bound(as_ctx* c, int precision, double* out, double* best) {
     if (best) CUDA_TRY(c, cudaMemcpyAsync(best, c->st.best, S * sizeof(double), cudaMemcpyDefault, s));
     CUDA_TRY(c, cudaStreamSynchronize(s));
     if (status) return fail(c, AS_ERR_ARG, "the batch's input box has lo > hi or a non-finite entry");
+    if (c->tc_status) {
+        int ts = 0;
+        CUDA_TRY(c, cudaMemcpy(&ts, c->tc_status, sizeof(int), cudaMemcpyDeviceToHost));
+        if (ts) return fail(c, AS_ERR_TIMEOUT, "a tensor-core kernel's bounded wait ran out");
+    }
     for (int q = 0; q < S; ++q)
         if (!std::isfinite(h[q])) return fail(c, AS_ERR_NUMERIC, "bound of subproblem %d is %g", q, h[q]);
     return AS_OK;
