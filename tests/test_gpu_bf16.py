@@ -1,0 +1,180 @@
+"""The BF16 form of the Active Set passes (as_options.precision = 16) against the FP64 oracle.
+
+The BF16 form rounds the operands of every product to bf16 (W, x*, and the dual row sums) and
+accumulates in float32 on the tensor cores. A bf16 rounding moves an operand by at most 2^-9 of
+itself, so a product moves by at most (2^-9 + 2^-9 + 2^-18) of |w| |v|, and a sum of products by at
+most 2^-8 of sum |w| |v| plus float32 accumulation. The tests use the bound
+    e = 2^-7 sum |w| |v|
+(twice that, which also covers float32 accumulation at these sizes) for every sum the form takes on
+the tensor cores, and check:
+  * one iteration from a drawn state (installed on both sides, nothing taken from the GPU): z* is
+    exact (its coefficients need no products), x* equals the oracle's wherever the oracle's |f|
+    clears e, and every dual lies in the range of the oracle's own Adam step over gradients
+    within e of the oracle's (1e-7 + 1e-6 relative slack);
+  * free-running solves: every bound, which as_bound re-evaluates in float32 with float32 lambda,
+    kappa, is valid (below the network's minimum over sampled inputs and box vertices, and, on the
+    tiny net, below the exact LP over the tighter relaxation), and stays within the stated gap of
+    the oracle's own FP64 run with the same schedule.
+"""
+import numpy as np
+import pytest
+
+from oracle import active_set as AS
+from oracle import dual as du
+from oracle import network as nw
+from oracle import relaxation as rx
+from paper_2101_05844_gb300 import binding, synth
+from tests.helpers import netlp_for, sample_min_output
+from tests.state_helpers import draw_state, hidden_concat, oracle_bounds_f32, split_hidden
+
+pytestmark = pytest.mark.gpu
+E_REL = 2.0 ** -7
+# stated gap of the BF16 form's final bound to the oracle's FP64 run (absolute, per unit of |bound|)
+GAP = 2e-2
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    assert torch.cuda.is_available()
+    binding.lib()
+
+
+def _adam_range(theta, m, v, g, e, lr, step, opt):
+    """Range of one oracle Adam step (AS.adam) over gradients in [g - e, g + e]."""
+    outs = []
+    for d in (-1.0, -0.5, 0.0, 0.5, 1.0):
+        th, mm, vv = theta.copy(), m.copy(), v.copy()
+        AS.adam(th, mm, vv, g + d * e, lr, step, opt)
+        outs.append(th)
+    return np.min(outs, 0), np.max(outs, 0)
+
+
+CASES = [
+    ("mlp_tiny", 1, dict(bigm_iters=5, as_iters=40, omega=3, max_cuts=5), 3, 0),     # Big-M
+    ("mlp_tiny", 1, dict(bigm_iters=5, as_iters=40, omega=3, max_cuts=5), 7, 2),     # AS, no addition
+    ("mlp_tiny", 1, dict(bigm_iters=5, as_iters=40, omega=3, max_cuts=5), 8, 2),     # AS, adds slot 2
+    ("small_conv", 3, dict(bigm_iters=5, as_iters=40, omega=3, max_cuts=5), 12, 4),  # stride 2 + 1, adds 4
+    ("small_conv", 3, dict(bigm_iters=5, as_iters=40, omega=3, max_cuts=7), 10, 3),
+    ("mlp_5_7_6_3", 4, dict(bigm_iters=2, as_iters=30, omega=4, max_cuts=8), 16, 6),  # adds slot 6
+    ("wide_conv", 9, dict(bigm_iters=5, as_iters=40, omega=3, max_cuts=5), 12, 4),   # 4x4 stride 2
+]
+
+
+@pytest.mark.parametrize("name,S,kw,it,nslots", CASES)
+def test_bf16_one_iteration_within_rounding_bound(name, S, kw, it, nslots):
+    prob = synth.problem(name, S=S, seed=0)
+    dense = nw.dense_layers(prob["net"])   # conv operators built once for all subproblems
+    Ps0 = nw.problems(prob, dense=dense)
+    lh, uh = oracle_bounds_f32(Ps0)
+    widths = Ps0[0].widths
+    Ps = nw.problems(prob, bounds=[(split_hidden(lh[s].astype(np.float64), widths)[1:],
+                                    split_hidden(uh[s].astype(np.float64), widths)[1:]) for s in range(S)],
+                     dense=dense)
+    ctx = binding.context_for(prob, binding.default_options(graph_chunk=0, precision=16, **kw), bounds=(lh, uh))
+    solvers = draw_state(Ps, ctx, kw, it, nslots, seed=100 + it)
+    opt = AS.Options(**{k: v for k, v in kw.items() if hasattr(AS.Options, k)})
+    # the oracle's pre-step values and the step's schedule
+    pre = [dict(alpha=[None if a is None else a.copy() for a in sv.st.alpha],
+                beta0=[None if a is None else a.copy() for a in sv.st.beta0],
+                beta1=[None if a is None else a.copy() for a in sv.st.beta1],
+                m={q: [None if a is None else a.copy() for a in sv.m[q]] for q in sv.m},
+                v={q: [None if a is None else a.copy() for a in sv.v[q]] for q in sv.v},
+                slots=[[(sl.beta.copy(), sl.m.copy(), sl.v.copy(), sl.added_at) for sl in sv.st.slots[k]]
+                       for k in range(sv.P.n)]) for sv in solvers]
+    if it < opt.bigm_iters:
+        lr, t = AS.linear_lr(opt.bigm_lr0, opt.bigm_lr1, it, opt.bigm_iters), -1
+    else:
+        t = it - opt.bigm_iters
+        lr = AS.linear_lr(opt.as_lr0, opt.as_lr1, t, opt.as_iters)
+    ctx.as_step(1)
+    xstar = ctx.get_state(binding.ST_XSTAR).reshape(S, -1)
+    zstar = ctx.get_state(binding.ST_ZSTAR, np.uint8).reshape(S, -1)
+    al = ctx.get_state(binding.ST_ALPHA).reshape(S, -1)
+    b0 = ctx.get_state(binding.ST_BETA0).reshape(S, -1)
+    b1 = ctx.get_state(binding.ST_BETA1).reshape(S, -1)
+    sb = ctx.get_state(binding.ST_SLOT_BETA).reshape(S, ctx.cap, -1)
+    checked = 0
+    for s, sv in enumerate(solvers):
+        P = sv.P
+        _, f, g, x, z = du.evaluate(P, sv.st)
+        grads = du.supergradient(P, sv.st, x, z)
+        # bf16 error bounds: col sums (f) over |W| |dual row sums|, row sums over |W| |x*|
+        ef, ex = [None] * P.n, [None] * P.n
+        for k in range(1, P.n):
+            rows = np.abs(sv.st.alpha[k]) + np.abs(sv.st.beta1[k]) + sum(np.abs(sl.beta) for sl in sv.st.slots[k])
+            ef[k - 1] = E_REL * (np.abs(P.W[k]).T @ rows) + 1e-6
+            ex[k] = E_REL * (np.abs(P.W[k]) @ np.abs(x[k - 1])) + 1e-6
+        ef[P.n - 1] = np.full(P.widths[P.n - 1], 1e-6)   # f of the last hidden layer: no product
+        np.testing.assert_array_equal(zstar[s], hidden_concat(z).astype(np.uint8))
+        xo = np.concatenate([x[k] for k in range(P.n)]).astype(np.float32)
+        decided = np.concatenate([np.abs(f[k]) > ef[k] for k in range(P.n)])
+        np.testing.assert_array_equal(xstar[s][decided], xo[decided])
+        if not (xstar[s] == xo).all():
+            continue   # a decision within the rounding bound differs: the duals follow other sums
+        checked += 1
+        slots_before = len(sv.st.slots[1])
+        sv.step(1)
+        pr = pre[s]
+
+        def in_range(gpu, theta, m, v, gr, e, step):
+            lo, hi = _adam_range(theta, m, v, gr, e, lr, step, opt)
+            slack = 1e-7 + 1e-6 * np.abs(hi)
+            assert ((gpu >= lo - slack) & (gpu <= hi + slack)).all(), \
+                (float(np.max(lo - gpu)), float(np.max(gpu - hi)))
+            assert (gpu >= 0).all()
+
+        offs = np.cumsum([0] + P.widths) - P.widths[0]
+        for k in range(1, P.n):
+            h = slice(offs[k], offs[k + 1])
+            in_range(al[s, h], pr["alpha"][k], pr["m"]["a"][k], pr["v"]["a"][k], grads["galpha"][k], ex[k], it + 1)
+            in_range(b0[s, h], pr["beta0"][k], pr["m"]["0"][k], pr["v"]["0"][k], grads["gbeta0"][k], 1e-6, it + 1)
+            in_range(b1[s, h], pr["beta1"][k], pr["m"]["1"][k], pr["v"]["1"][k], grads["gbeta1"][k], ex[k], it + 1)
+            for b, (beta, m, v, added) in enumerate(pr["slots"][k]):
+                in_range(sb[s, b, h], beta, m, v, grads["gslots"][k][b], 2 * ex[k], t - added + 1)
+            if len(sv.st.slots[k]) > slots_before:   # the slot this iteration added: zero start
+                I = rx.mask(P.W[k], P.lo[k - 1], P.hi[k - 1], x[k - 1], z[k])
+                lam_n, mu_n = rx.row_sums(P.W[k], P.lo[k - 1], P.hi[k - 1], I)
+                gnew = x[k] - (P.W[k] * I) @ x[k - 1] + lam_n * (1 - z[k]) - z[k] * (P.b[k] + mu_n)
+                zero = np.zeros_like(gnew)
+                in_range(sb[s, slots_before, h], zero, zero, zero, gnew, 2 * ex[k], 1)
+    assert checked >= 1
+
+
+FREE = [
+    ("mlp_tiny", 1, dict(bigm_iters=20, as_iters=80, omega=24, max_cuts=5)),
+    ("mlp_5_7_6_3", 4, dict(bigm_iters=30, as_iters=60, omega=20, max_cuts=4)),
+    ("small_conv", 3, dict(bigm_iters=20, as_iters=40, omega=12, max_cuts=5)),
+]
+
+
+@pytest.mark.parametrize("name,S,kw", FREE)
+def test_bf16_free_running_bound_is_valid_and_close_to_oracle(name, S, kw):
+    prob = synth.problem(name, S=S, seed=0)
+    Ps = nw.problems(prob)
+    iters = kw["bigm_iters"] + kw["as_iters"]
+    ctx = binding.context_for(prob, binding.default_options(graph_chunk=0, precision=16, **kw))
+    ctx.as_step(iters)
+    b = ctx.bound()
+    gaps = []
+    for s, P in enumerate(Ps):
+        ref = AS.ActiveSet(P, AS.Options(**kw)).step(iters).bound()
+        assert b[s] <= sample_min_output(P, 5000) + 1e-6
+        if name == "mlp_tiny":
+            assert b[s] <= float(netlp_for(P).solve("A", P.W[P.n][0], P.b[P.n][0])) + 1e-6
+        gaps.append(abs(b[s] - ref) / (1 + abs(ref)))
+    print(f"BF16 form vs oracle, {name}: max gap {max(gaps):.2e} (per unit of 1 + |bound|)")
+    assert max(gaps) <= GAP
+
+
+def test_bf16_graph_replay_equals_plain_launches():
+    """The captured graph (grouped GEMMs sizing their rows from the device counter) gives the
+    same iterates as plain launches."""
+    prob = synth.problem("small_conv", S=3, seed=1)
+    kw = dict(bigm_iters=10, as_iters=40, omega=8, max_cuts=5, precision=16)
+    a = binding.context_for(prob, binding.default_options(graph_chunk=0, **kw))
+    g = binding.context_for(prob, binding.default_options(graph_chunk=10, **kw))
+    a.as_step(50)
+    g.as_step(50)
+    np.testing.assert_array_equal(a.get_state(binding.ST_SLOT_BETA), g.get_state(binding.ST_SLOT_BETA))
+    np.testing.assert_array_equal(a.bound(), g.bound())
