@@ -11,10 +11,13 @@ the tensor cores, and check:
     exact (its coefficients need no products), x* equals the oracle's wherever the oracle's |f|
     clears e, and every dual lies in the range of the oracle's own Adam step over gradients
     within e of the oracle's (1e-7 + 1e-6 relative slack);
+    An input whose x* the GPU takes the other way (only possible within that bound) widens the
+    bound of the rows it feeds by |W| (|l| + |u|); a row whose own x* differs is checked for
+    validity only, and at least 90% of the rows must be checked in full;
   * free-running solves: every bound, which as_bound re-evaluates in float32 with float32 lambda,
-    kappa, is valid (below the network's minimum over sampled inputs and box vertices, and, on the
-    tiny net, below the exact LP over the tighter relaxation), and stays within the stated gap of
-    the oracle's own FP64 run with the same schedule.
+    kappa, is valid (below the network's minimum over sampled inputs and box vertices, and, on a
+    six-neuron net, below the exact LP over the tighter relaxation), and stays within the stated
+    gap of the oracle's own FP64 run with the same schedule.
 """
 import numpy as np
 import pytest
@@ -94,51 +97,62 @@ def test_bf16_one_iteration_within_rounding_bound(name, S, kw, it, nslots):
     b0 = ctx.get_state(binding.ST_BETA0).reshape(S, -1)
     b1 = ctx.get_state(binding.ST_BETA1).reshape(S, -1)
     sb = ctx.get_state(binding.ST_SLOT_BETA).reshape(S, ctx.cap, -1)
-    checked = 0
+    rows_checked = rows_total = 0
     for s, sv in enumerate(solvers):
         P = sv.P
         _, f, g, x, z = du.evaluate(P, sv.st)
         grads = du.supergradient(P, sv.st, x, z)
-        # bf16 error bounds: col sums (f) over |W| |dual row sums|, row sums over |W| |x*|
-        ef, ex = [None] * P.n, [None] * P.n
+        offs_t = np.cumsum([0] + P.widths)
+        np.testing.assert_array_equal(zstar[s], hidden_concat(z).astype(np.uint8))
+        xo = np.concatenate([x[k] for k in range(P.n)]).astype(np.float32)
+        # bf16 error bound of f: col sums over |W| |dual row sums|
+        ef = [None] * P.n
         for k in range(1, P.n):
             rows = np.abs(sv.st.alpha[k]) + np.abs(sv.st.beta1[k]) + sum(np.abs(sl.beta) for sl in sv.st.slots[k])
             ef[k - 1] = E_REL * (np.abs(P.W[k]).T @ rows) + 1e-6
-            ex[k] = E_REL * (np.abs(P.W[k]) @ np.abs(x[k - 1])) + 1e-6
         ef[P.n - 1] = np.full(P.widths[P.n - 1], 1e-6)   # f of the last hidden layer: no product
-        np.testing.assert_array_equal(zstar[s], hidden_concat(z).astype(np.uint8))
-        xo = np.concatenate([x[k] for k in range(P.n)]).astype(np.float32)
         decided = np.concatenate([np.abs(f[k]) > ef[k] for k in range(P.n)])
         np.testing.assert_array_equal(xstar[s][decided], xo[decided])
-        if not (xstar[s] == xo).all():
-            continue   # a decision within the rounding bound differs: the duals follow other sums
-        checked += 1
+        mism = [xstar[s][offs_t[k]:offs_t[k + 1]] != xo[offs_t[k]:offs_t[k + 1]] for k in range(P.n)]
+        # bf16 error bound of the row sums (W x*, masked products) over |W| |x*|, widened by every
+        # input whose x* the GPU took the other way (within the bound above): |W| (|l| + |u|)
+        ex = [None] * P.n
+        for k in range(1, P.n):
+            far = mism[k - 1] * (np.abs(P.lo[k - 1]) + np.abs(P.hi[k - 1]))
+            ex[k] = E_REL * (np.abs(P.W[k]) @ np.abs(x[k - 1])) + np.abs(P.W[k]) @ far + 1e-6
         slots_before = len(sv.st.slots[1])
         sv.step(1)
         pr = pre[s]
 
-        def in_range(gpu, theta, m, v, gr, e, step):
+        def in_range(gpu, theta, m, v, gr, e, step, own):
+            """gpu within the oracle's Adam step range; rows whose own x* differs: validity only."""
             lo, hi = _adam_range(theta, m, v, gr, e, lr, step, opt)
             slack = 1e-7 + 1e-6 * np.abs(hi)
-            assert ((gpu >= lo - slack) & (gpu <= hi + slack)).all(), \
-                (float(np.max(lo - gpu)), float(np.max(gpu - hi)))
+            ok = (gpu >= lo - slack) & (gpu <= hi + slack)
+            assert (ok | own).all(), (float(np.max((lo - gpu)[~own])), float(np.max((gpu - hi)[~own])))
             assert (gpu >= 0).all()
 
-        offs = np.cumsum([0] + P.widths) - P.widths[0]
+        offs = offs_t - P.widths[0]
         for k in range(1, P.n):
             h = slice(offs[k], offs[k + 1])
-            in_range(al[s, h], pr["alpha"][k], pr["m"]["a"][k], pr["v"]["a"][k], grads["galpha"][k], ex[k], it + 1)
-            in_range(b0[s, h], pr["beta0"][k], pr["m"]["0"][k], pr["v"]["0"][k], grads["gbeta0"][k], 1e-6, it + 1)
-            in_range(b1[s, h], pr["beta1"][k], pr["m"]["1"][k], pr["v"]["1"][k], grads["gbeta1"][k], ex[k], it + 1)
+            own = mism[k]
+            rows_checked += int((~own).sum())
+            rows_total += own.size
+            in_range(al[s, h], pr["alpha"][k], pr["m"]["a"][k], pr["v"]["a"][k], grads["galpha"][k], ex[k], it + 1,
+                     own)
+            in_range(b0[s, h], pr["beta0"][k], pr["m"]["0"][k], pr["v"]["0"][k], grads["gbeta0"][k], 1e-6, it + 1,
+                     own)
+            in_range(b1[s, h], pr["beta1"][k], pr["m"]["1"][k], pr["v"]["1"][k], grads["gbeta1"][k], ex[k], it + 1,
+                     own)
             for b, (beta, m, v, added) in enumerate(pr["slots"][k]):
-                in_range(sb[s, b, h], beta, m, v, grads["gslots"][k][b], 2 * ex[k], t - added + 1)
+                in_range(sb[s, b, h], beta, m, v, grads["gslots"][k][b], 2 * ex[k], t - added + 1, own)
             if len(sv.st.slots[k]) > slots_before:   # the slot this iteration added: zero start
                 I = rx.mask(P.W[k], P.lo[k - 1], P.hi[k - 1], x[k - 1], z[k])
                 lam_n, mu_n = rx.row_sums(P.W[k], P.lo[k - 1], P.hi[k - 1], I)
                 gnew = x[k] - (P.W[k] * I) @ x[k - 1] + lam_n * (1 - z[k]) - z[k] * (P.b[k] + mu_n)
                 zero = np.zeros_like(gnew)
-                in_range(sb[s, slots_before, h], zero, zero, zero, gnew, 2 * ex[k], 1)
-    assert checked >= 1
+                in_range(sb[s, slots_before, h], zero, zero, zero, gnew, 2 * ex[k], 1, own)
+    assert rows_checked >= 0.9 * rows_total, (rows_checked, rows_total)
 
 
 FREE = [
@@ -160,11 +174,21 @@ def test_bf16_free_running_bound_is_valid_and_close_to_oracle(name, S, kw):
     for s, P in enumerate(Ps):
         ref = AS.ActiveSet(P, AS.Options(**kw)).step(iters).bound()
         assert b[s] <= sample_min_output(P, 5000) + 1e-6
-        if name == "mlp_tiny":
-            assert b[s] <= float(netlp_for(P).solve("A", P.W[P.n][0], P.b[P.n][0])) + 1e-6
         gaps.append(abs(b[s] - ref) / (1 + abs(ref)))
     print(f"BF16 form vs oracle, {name}: max gap {max(gaps):.2e} (per unit of 1 + |bound|)")
     assert max(gaps) <= GAP
+
+
+def test_bf16_bound_below_the_exact_lp_of_the_tighter_relaxation():
+    """On a net small enough for the exact rational LP over every constraint of problem (4)
+    (4-3-3-1, six hidden neurons): the BF16 form's bound stays below the LP optimum."""
+    prob = synth.problem("mlp_4_3_3_1", seed=4)
+    P = nw.problems(prob)[0]
+    kw = dict(bigm_iters=20, as_iters=80, omega=24, max_cuts=5)
+    ctx = binding.context_for(prob, binding.default_options(graph_chunk=0, precision=16, **kw))
+    ctx.as_step(100)
+    lp_a = float(netlp_for(P).solve("A", P.W[P.n][0], P.b[P.n][0]))
+    assert ctx.bound()[0] <= lp_a + 1e-6
 
 
 def test_bf16_graph_replay_equals_plain_launches():
