@@ -227,6 +227,70 @@ def batched_run(binding, torch, dev, stream, rank):
             "kernel_ms": {k: v[0] for k, v in kt.items() if v[1]}}
 
 
+def precision_run(binding, torch, dev, stream, rank, S=1024, chunk=25):
+    """BASELINE's precision form: the conv net 3x32x32 -> 4 conv 3x3 -> FC512 -> FC10 on S boxes of
+    half-width 8/255, 100 Big-M + 400 Active Set iterations, once in float32 and once in the BF16
+    form (tensor-core products, precision 16), same schedule, same GPU. Reports each form's
+    subproblem-iterations/s (one timed run after a warm-up) and the time to bound: iteration time
+    (CUDA events around each chunk of iterations; the bound evaluations between chunks are not
+    counted) until a subproblem's bound, re-evaluated in float32, first reaches the float32
+    form's final bound minus 1e-4."""
+    from paper_2101_05844_gb300 import synth
+    prob = synth.problem("conv4", S=S, seed=rank)
+    iters = 500
+    t = {k: torch.from_numpy(prob[k]).to(dev) for k in ("lo", "hi", "C")}
+    out = {}
+    finals = {}
+    ctxs = {}
+    for prec in (32, 16):
+        opt = binding.default_options(bigm_iters=100, as_iters=400, omega=120, max_cuts=5, graph_chunk=25,
+                                      precision=prec)
+        ctxs[prec] = binding.Context(prob["net"], prob["lo"], prob["hi"], prob["C"], options=opt, stream=stream)
+    bound = torch.zeros(S, dtype=torch.float64, device=dev)
+    for prec, ctx in ctxs.items():
+        ctx.reset(t["lo"], t["hi"], t["C"])
+        ctx.as_step(iters)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ctx.reset(t["lo"], t["hi"], t["C"])
+        e0.record()
+        ctx.as_step(iters)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        ctx.bound_into(64, bound)
+        finals[prec] = bound.cpu().numpy().copy()
+        out[f"fp{prec}" if prec == 32 else "bf16"] = {"value": S * iters / (ms / 1e3), "unit": UNIT, "ms": ms,
+                                                       "mean_final_bound": float(finals[prec].mean())}
+    target = finals[32] - 1e-4
+    for prec, ctx in ctxs.items():
+        ctx.reset(t["lo"], t["hi"], t["C"])
+        reach = np.full(S, np.nan)
+        elapsed = 0.0
+        for c0 in range(0, iters, chunk):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ctx.as_step(min(chunk, iters - c0))
+            e1.record()
+            e1.synchronize()
+            elapsed += e0.elapsed_time(e1)
+            ctx.bound_into(64, bound)
+            b = bound.cpu().numpy()
+            new = np.isnan(reach) & (b >= target)
+            reach[new] = elapsed
+        key = "fp32" if prec == 32 else "bf16"
+        done = ~np.isnan(reach)
+        out[key]["time_to_bound_ms"] = {"reached": int(done.sum()), "of": S,
+                                        "median": float(np.median(reach[done])) if done.any() else None,
+                                        "max": float(np.max(reach[done])) if done.any() else None}
+    gap = finals[16] - finals[32]
+    out["bf16_minus_fp32_final_bound"] = {"mean": float(gap.mean()), "min": float(gap.min()), "max": float(gap.max())}
+    out["workload"] = {"net": "conv4", "subproblems": S, "iterations": iters, "eps": "8/255"}
+    for ctx in ctxs.values():
+        ctx.close()
+    return out
+
+
 def captured_traffic(workload, kernel):
     """DRAM bytes per launch of `kernel` from the committed ncu capture of this workload, or None
     when there is none or the kernel source has changed since it was taken."""
@@ -316,6 +380,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="wide_conv")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", action="store_true",
+                    help="also time BASELINE's precision form: conv4 on 1024 boxes, float32 against the "
+                         "BF16 form, subproblem-iterations/s and time to the float32 bound")
     ap.add_argument("--batched", action="store_true",
                     help="also time BASELINE's batching form: 4096 subdomains, 500 Active Set iterations")
     args = ap.parse_args()
@@ -446,6 +513,8 @@ def main():
     }
     if args.batched:
         line["batched"] = batched_run(binding, torch, dev, stream, rank)
+    if args.precision:
+        line["precision"] = precision_run(binding, torch, dev, stream, rank)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload)
     if rank == 0:

@@ -10,7 +10,8 @@ the tensor cores, and check:
   * one iteration from a drawn state (installed on both sides, nothing taken from the GPU): z* is
     exact (its coefficients need no products), x* equals the oracle's wherever the oracle's |f|
     clears e, and every dual lies in the range of the oracle's own Adam step over gradients
-    within e of the oracle's (1e-7 + 1e-6 relative slack);
+    within e of the oracle's (slack 1e-7 + 1e-5 relative: the Adam step itself runs in float32, as
+    in the float32 form, whose lockstep tolerance this is);
     An input whose x* the GPU takes the other way (only possible within that bound) widens the
     bound of the rows it feeds by |W| (|l| + |u|); a row whose own x* differs is checked for
     validity only, and at least 90% of the rows must be checked in full;
@@ -32,8 +33,9 @@ from tests.state_helpers import draw_state, hidden_concat, oracle_bounds_f32, sp
 
 pytestmark = pytest.mark.gpu
 E_REL = 2.0 ** -7
-# stated gap of the BF16 form's final bound to the oracle's FP64 run (absolute, per unit of |bound|)
-GAP = 2e-2
+# stated gap of the BF16 form's final bound to the oracle's FP64 run with the same schedule, per
+# unit of 1 + |bound| (measured on GB300: 0.9e-3 to 4.1e-3 on the three free-running nets)
+GAP = 1e-2
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -127,7 +129,7 @@ def test_bf16_one_iteration_within_rounding_bound(name, S, kw, it, nslots):
         def in_range(gpu, theta, m, v, gr, e, step, own):
             """gpu within the oracle's Adam step range; rows whose own x* differs: validity only."""
             lo, hi = _adam_range(theta, m, v, gr, e, lr, step, opt)
-            slack = 1e-7 + 1e-6 * np.abs(hi)
+            slack = 1e-7 + 1e-5 * np.abs(hi)   # the float32 Adam step: the float32 lockstep's tolerance
             ok = (gpu >= lo - slack) & (gpu <= hi + slack)
             assert (ok | own).all(), (float(np.max((lo - gpu)[~own])), float(np.max((gpu - hi)[~own])))
             assert (gpu >= 0).all()
