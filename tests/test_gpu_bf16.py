@@ -46,9 +46,11 @@ def _lib():
 
 
 def _adam_range(theta, m, v, g, e, lr, step, opt):
-    """Range of one oracle Adam step (AS.adam) over gradients in [g - e, g + e]."""
+    """Range of one oracle Adam step (AS.adam) over gradients in [g - e, g + e]. The step is not
+    monotone in g (the second moment grows with g^2, so m_hat / sqrt(v_hat) can peak inside the
+    interval when v is small): the interval is sampled densely."""
     outs = []
-    for d in (-1.0, -0.5, 0.0, 0.5, 1.0):
+    for d in np.linspace(-1.0, 1.0, 129):
         th, mm, vv = theta.copy(), m.copy(), v.copy()
         AS.adam(th, mm, vv, g + d * e, lr, step, opt)
         outs.append(th)
@@ -131,7 +133,17 @@ def test_bf16_one_iteration_within_rounding_bound(name, S, kw, it, nslots):
             lo, hi = _adam_range(theta, m, v, gr, e, lr, step, opt)
             slack = 1e-7 + 1e-5 * np.abs(hi)   # the float32 Adam step: the float32 lockstep's tolerance
             ok = (gpu >= lo - slack) & (gpu <= hi + slack)
-            assert (ok | own).all(), (float(np.max((lo - gpu)[~own])), float(np.max((gpu - hi)[~own])))
+            if not (ok | own).all():
+                q = int(np.argmax(np.where(own, -np.inf, np.maximum(lo - gpu, gpu - hi))))
+                # the gradient that gives the GPU's value, by a scan of the oracle's Adam step
+                gs = gr[q] + np.linspace(-20, 20, 4001) * e[q] if np.ndim(e) else gr[q] + np.linspace(-20, 20, 4001) * e
+                tq = np.full(gs.size, theta[q]); mq = np.full(gs.size, m[q]); vq = np.full(gs.size, v[q])
+                AS.adam(tq, mq, vq, gs, lr, step, opt)
+                gimp = float(gs[np.argmin(np.abs(tq - gpu[q]))])
+                eq = float(e[q]) if np.ndim(e) else float(e)
+                raise AssertionError(f"entry {q}: gpu {gpu[q]:.9g} not in [{lo[q]:.9g}, {hi[q]:.9g}]; theta {theta[q]:.6g}"
+                                     f" m {m[q]:.6g} v {v[q]:.6g}; oracle g {gr[q]:.6g} e {eq:.3g}; implied g {gimp:.6g};"
+                                     f" lr {lr:.6g} step {step}")
             assert (gpu >= 0).all()
 
         offs = offs_t - P.widths[0]
