@@ -181,23 +181,28 @@ __global__ void k_grad_box(DNet net, DState st, GradCtx gc, float* dlo, float* d
     if (dhi) dhi[u] += (float)(gc.gb[s] * (double)ah);
 }
 
-__device__ __forceinline__ void slot_sums_body(const DNet& net, const DState& st, const Segs& sg, int nadd, int bo);
+__device__ __forceinline__ void slot_sums_body(const DNet& net, const DState& st, const Segs& sg, int nadd, int bo,
+                                               int only);
 
 // lambda, kappa of every filled slot from the snapshot bits (after the caller replaced them).
 __global__ void __launch_bounds__(CB_THREADS) k_slot_sums(DNet net, DState st, Segs sg, int nadd, int bo) {
-    slot_sums_body(net, st, sg, nadd, bo);
+    slot_sums_body(net, st, sg, nadd, bo, -1);
 }
 
-// The same in float32 after an Active Set iteration that added a slot (BF16 form: the iteration
-// took the new slot's lambda from its bf16 products); returns at once after other iterations.
+// lambda, kappa in float32 of the slot an Active Set iteration just added (BF16 form: the
+// iteration took them from its bf16 products); returns at once after other iterations.
 __global__ void __launch_bounds__(CB_THREADS) k_slot_sums_after_add(DNet net, DState st, DSched sc, Segs sg) {
     const int it = st.ctr[0] - 1;   // the iteration that just ended
-    if (it < sc.TM || cb_slot_at(it - sc.TM, sc) < 0) return;
+    if (it < sc.TM) return;
+    const int b = cb_slot_at(it - sc.TM, sc);
+    if (b < 0) return;
     const int nadd = cb_additions_before(it - sc.TM + 1, sc);
-    slot_sums_body(net, st, sg, nadd, nadd & 1);
+    slot_sums_body(net, st, sg, nadd, nadd & 1, b);
 }
 
-__device__ __forceinline__ void slot_sums_body(const DNet& net, const DState& st, const Segs& sg, int nadd, int bo) {
+// only >= 0: that slot alone.
+__device__ __forceinline__ void slot_sums_body(const DNet& net, const DState& st, const Segs& sg, int nadd, int bo,
+                                               int only) {
     const int q = seg_of(sg, blockIdx.x);
     const DLayer& L = net.L[sg.layer[q]];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -218,18 +223,18 @@ __device__ __forceinline__ void slot_sums_body(const DNet& net, const DState& st
         const float Lc = w >= 0.f ? l : uu, Uc = w >= 0.f ? uu : l;
 #pragma unroll
         for (int b = 0; b < CB_MAXCUT; ++b)
-            if (b < nsl) {
+            if (b < nsl && (only < 0 || b == only)) {
                 if ((I >> b) & 1u) lam[b] += w * Lc;
                 else mu[b] += w * Uc;
             }
     });
 #pragma unroll
     for (int b = 0; b < CB_MAXCUT; ++b)
-        if (b < nsl) {
+        if (b < nsl && (only < 0 || b == only)) {
             lam[b] = warp_sum(lam[b]);
             mu[b] = warp_sum(mu[b]);
         }
-    if (lane < nsl) {
+    if (lane < nsl && (only < 0 || lane == only)) {
         float l = 0.f, m = 0.f;
 #pragma unroll
         for (int b = 0; b < CB_MAXCUT; ++b)

@@ -377,6 +377,24 @@ __device__ __forceinline__ void as_colA_body(const DNet& net, const DState& st, 
     }
 }
 
+// BF16 form, conv layers: a block of 256 threads takes 8 channels x 32 positions of one subproblem
+// (C channels of P positions), so that each warp reads the per-neuron vectors (channel-major)
+// contiguously while the block's 8 warps together cover whole 32-byte pieces of the channels-last
+// products and operand planes. Returns the neuron index c P + p, or -1 past the layer.
+__device__ __forceinline__ int tc_tile_unit(int t, int C, int P, int S, int& s) {
+    const int ncb = (C + 7) >> 3, npb = (P + 31) >> 5;
+    const int tile = t >> 8, lt = t & 255;
+    s = tile / (ncb * npb);
+    const int rem = tile - s * (ncb * npb);
+    const int cb = rem / npb, pb = rem - cb * npb;
+    const int c = cb * 8 + (lt >> 5), p = pb * 32 + (lt & 31);
+    if (s >= S || c >= C || p >= P) {
+        s = 0;
+        return -1;
+    }
+    return c * P + p;
+}
+
 __device__ __forceinline__ int tseg_of(const TSegs& sg, int blk) {
     int q = 0;
     while (q + 1 < sg.n && blk >= sg.start[q + 1]) ++q;
@@ -394,8 +412,13 @@ __global__ void __launch_bounds__(CB_THREADS, 4) k_as_colA_t(DNet net, DState st
     const int T = sg.T[q];
     const int t = (blockIdx.x - sg.start[q]) * CB_THREADS + threadIdx.x;
     const int unit = t / T, lane = t - unit * T;
-    const bool valid = unit < net.S * L.n_in;
-    const int s = valid ? unit / L.n_in : 0, o = valid ? unit - s * L.n_in : 0;
+    bool valid = unit < net.S * L.n_in;
+    int s = valid ? unit / L.n_in : 0, o = valid ? unit - s * L.n_in : 0;
+    if (tc && L.kind == 1) {   // one lane per unit, tiled
+        o = tc_tile_unit(t, L.ci, L.hi * L.wi, net.S, s);
+        valid = o >= 0;
+        o = valid ? o : 0;
+    }
     const int j = (valid && sg.perm[q]) ? sg.perm[q][o] : o;
     const Step sp = cb_step(st.ctr[0], sc, st.lr_tab);
     const int ns = min(sp.nadd_before, sc.maxcut);
@@ -573,8 +596,13 @@ __global__ void __launch_bounds__(CB_THREADS, 4) k_as_rowB_t(DNet net, DState st
     const int T = sg.T[q];
     const int t = (blockIdx.x - sg.start[q]) * CB_THREADS + threadIdx.x;
     const int unit = t / T, lane = t - unit * T;
-    const bool valid = unit < net.S * L.n_out;
-    const int s = valid ? unit / L.n_out : 0, i = valid ? unit - s * L.n_out : 0;
+    bool valid = unit < net.S * L.n_out;
+    int s = valid ? unit / L.n_out : 0, i = valid ? unit - s * L.n_out : 0;
+    if (tc && L.kind == 1) {   // one lane per unit, tiled
+        i = tc_tile_unit(t, L.co, L.ho * L.wo, net.S, s);
+        valid = i >= 0;
+        i = valid ? i : 0;
+    }
     const int it = st.ctr[0];
     const Step sp = cb_step(it, sc, st.lr_tab);
     const int ns = min(sp.nadd_before + (sp.b_new >= 0 ? 1 : 0), sc.maxcut);
