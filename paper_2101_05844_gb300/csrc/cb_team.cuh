@@ -318,12 +318,24 @@ __device__ __forceinline__ void as_colA_body(const DNet& net, const DState& st, 
         const size_t hs = (size_t)s * cap * NH + L.h_in + j;
         float sb = 0.f, gk = st.beta0[h] * st.uhat[h] + st.beta1[h] * st.lhat[h];
         double cterm = 0.0;
-        for (int b = 0; b < nsl; ++b) {
-            const float bb = st.bs[hs + (size_t)b * NH];
-            sb += bb;
-            gk += bb * st.kap[hs + (size_t)b * NH];
-            if (want_terms) cterm += (double)bb * st.lam[hs + (size_t)b * NH];
+        // all slot loads first (NS >= nsl), then the sums in slot order
+        float bbv[NS > 0 ? NS : 1], kpv[NS > 0 ? NS : 1], lmv[NS > 0 ? NS : 1];
+#pragma unroll
+        for (int b = 0; b < NS; ++b) {
+            bbv[b] = kpv[b] = lmv[b] = 0.f;
+            if (b < nsl) {
+                bbv[b] = st.bs[hs + (size_t)b * NH];
+                kpv[b] = st.kap[hs + (size_t)b * NH];
+                if (want_terms) lmv[b] = st.lam[hs + (size_t)b * NH];
+            }
         }
+#pragma unroll
+        for (int b = 0; b < NS; ++b)
+            if (b < nsl) {
+                sb += bbv[b];
+                gk += bbv[b] * kpv[b];
+                if (want_terms) cterm += (double)bbv[b] * lmv[b];
+            }
         f += st.alpha[h] - st.beta0[h] - st.beta1[h] - sb;
         const bool z = gk >= 0.f;
         st.zcur[h] = z;
@@ -532,6 +544,72 @@ __device__ __forceinline__ void as_rowB_body(const DNet& net, const DState& st, 
             else
                 *arec_entry(net, st, L, s, ap, e) = v;
         };
+        if (T == 1) {
+            // one lane per unit: every load first, so that they are in flight together (the state
+            // arrays may alias as far as the compiler knows, so it would not hoist them itself)
+            float th3[3] = {st.alpha[h], st.beta0[h], st.beta1[h]};
+            float m3[3] = {st.ma[h], st.m0[h], st.m1[h]};
+            float v3[3] = {st.va[h], st.v0[h], st.v1[h]};
+            const float uh = st.uhat[h], lh = st.lhat[h];
+            const int step = it + 1;
+            const float ib1 = inv_bias_corr(st.bc1_tab, sc.ntab, step, sc.b1);
+            const float ib2 = inv_bias_corr(st.bc2_tab, sc.ntab, step, sc.b2);
+            const float g3[3] = {xhat - x, x - z * uh, x - xhat + (1.f - z) * lh};
+#pragma unroll
+            for (int v = 0; v < 3; ++v) th3[v] = adam_step(th3[v], m3[v], v3[v], g3[v], sp.lr, ib1, ib2, sc);
+            st.alpha[h] = th3[0]; st.beta0[h] = th3[1]; st.beta1[h] = th3[2];
+            st.ma[h] = m3[0]; st.m0[h] = m3[1]; st.m1[h] = m3[2];
+            st.va[h] = v3[0]; st.v0[h] = v3[1]; st.v1[h] = v3[2];
+            contrib = th3[2] - th3[0];
+            // the slots in pairs: a pair's loads first, then its updates (larger groups spill)
+#pragma unroll
+            for (int b0 = 0; b0 < NS; b0 += 2) {
+                float bsv[2], msv[2], vsv[2], lamv[2], kapv[2];
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int b = b0 + q;
+                    bsv[q] = msv[q] = vsv[q] = lamv[q] = kapv[q] = 0.f;
+                    if (b < NS && b < nsl) {
+                        const size_t hs = hs0 + (size_t)b * NH;
+                        bsv[q] = st.bs[hs];
+                        msv[q] = st.ms[hs];
+                        vsv[q] = st.vs[hs];
+                        if (!(ADD && b == newb)) {
+                            lamv[q] = st.lam[hs];
+                            kapv[q] = st.kap[hs];
+                        }
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int b = b0 + q;
+                    if (b >= NS) continue;
+                    if (b >= nsl) {
+                        put(1 + b, 0.f);
+                        continue;
+                    }
+                    const size_t hs = hs0 + (size_t)b * NH;
+                    const bool zb = (zs >> b) & 1u;
+                    float lam = lamv[q], kap = kapv[q];
+                    if (ADD && b == newb) {
+                        const float lzh = st.lz[h];
+                        lam = zb ? lzh : acc[b];
+                        kap = zb ? lzh + bi : xhat;
+                        st.lam[hs] = lam;
+                        st.kap[hs] = kap;
+                    }
+                    const float prod = zb ? acc0 : acc[b];
+                    const float gb = x - prod + lam * (1.f - z) - z * (kap - lam);
+                    const int sstep = sp.t - cb_slot_added_at(b, sc) + 1;
+                    const float nv = adam_step(bsv[q], msv[q], vsv[q], gb, sp.lr,
+                                               inv_bias_corr(st.bc1_tab, sc.ntab, sstep, sc.b1),
+                                               inv_bias_corr(st.bc2_tab, sc.ntab, sstep, sc.b2), sc);
+                    st.bs[hs] = nv; st.ms[hs] = msv[q]; st.vs[hs] = vsv[q];
+                    if (zb) contrib += nv;
+                    put(1 + b, zb ? 0.f : nv);
+                }
+            }
+        } else
         for (int v = lane; v < 3 + NS; v += T) {
             if (v < 3) {
                 float* th = v == 0 ? st.alpha : (v == 1 ? st.beta0 : st.beta1);
