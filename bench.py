@@ -320,6 +320,16 @@ def precision_run(binding, torch, dev, stream, rank, S=1024, chunk=25):
                                                   "median": float(np.median(r[done])) if done.any() else None,
                                                   "max": float(np.max(r[done])) if done.any() else None}
     lc.close()
+    # per-kernel device time of 60 iterations (20 Big-M + 40 Active Set, 5 slots), each form
+    out["kernel_ms_60_iterations"] = {}
+    for prec in (32, 16):
+        popt = binding.default_options(bigm_iters=20, as_iters=40, omega=12, max_cuts=5, graph_chunk=0, profile=1,
+                                       precision=prec)
+        pc = binding.Context(prob["net"], prob["lo"], prob["hi"], prob["C"], options=popt, stream=stream)
+        pc.as_step(60)
+        out["kernel_ms_60_iterations"]["fp32" if prec == 32 else "bf16"] = {
+            k: v[0] for k, v in pc.kernel_times().items() if v[1]}
+        pc.close()
     out["workload"] = {"net": "conv4", "subproblems": S, "iterations": iters, "eps": "8/255"}
     for ctx in ctxs.values():
         ctx.close()
