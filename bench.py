@@ -336,6 +336,44 @@ def precision_run(binding, torch, dev, stream, rank, S=1024, chunk=25):
     return out
 
 
+def differentiation_run(binding, torch, dev, stream, rank):
+    """BASELINE's differentiation form: MLP 784-1024-1024-1024-10 on 256 boxes of half-width 0.1,
+    60 Big-M + 240 Active Set iterations in float32 (timed after a warm-up), then the bound and its
+    envelope gradient with respect to W, b and the box endpoints (as_bound_backward, timed)."""
+    from paper_2101_05844_gb300 import synth
+    prob = synth.problem("mlp_wide", S=256, seed=rank)
+    S, iters = 256, 300
+    opt = binding.default_options(bigm_iters=60, as_iters=240, omega=72, max_cuts=5, graph_chunk=25)
+    t = {k: torch.from_numpy(prob[k]).to(dev) for k in ("lo", "hi", "C")}
+    ctx = binding.Context(prob["net"], prob["lo"], prob["hi"], prob["C"], options=opt, stream=stream)
+    dW = [torch.zeros(L["W"].shape, device=dev) for L in prob["net"]]
+    db = [torch.zeros(L["b"].shape, device=dev) for L in prob["net"]]
+    dlo, dhi = torch.zeros(t["lo"].shape, device=dev), torch.zeros(t["hi"].shape, device=dev)
+    g = torch.ones(S, dtype=torch.float64, device=dev)
+    bound = torch.zeros(S, dtype=torch.float64, device=dev)
+
+    def run():
+        ctx.reset(t["lo"], t["hi"], t["C"])
+        ctx.as_step(iters)
+
+    run()
+    ctx.backward(g, dW, db, dlo, dhi)
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    e[0].record()
+    run()
+    e[1].record()
+    ctx.bound_into(64, bound)
+    ctx.backward(g, dW, db, dlo, dhi)
+    e[2].record()
+    e[2].synchronize()
+    ms_it, ms_bw = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+    ctx.close()
+    return {"workload": {"net": "mlp_784_1024x3_10", "subproblems": S, "iterations": iters, "eps": 0.1},
+            "value": S * iters / (ms_it / 1e3), "unit": UNIT, "ms_iterations": ms_it,
+            "ms_bound_and_backward": ms_bw, "mean_final_bound": float(bound.mean())}
+
+
 def captured_traffic(workload, kernel):
     """DRAM bytes per launch of `kernel` from the committed ncu capture of this workload, or None
     when there is none or the kernel source has changed since it was taken."""
@@ -430,6 +468,9 @@ def main():
                          "BF16 form, subproblem-iterations/s and time to the float32 bound")
     ap.add_argument("--precision-subproblems", type=int, default=1024,
                     help="boxes of the precision form (1024 as BASELINE's; fewer for a profiler capture)")
+    ap.add_argument("--differentiation", action="store_true",
+                    help="also time BASELINE's differentiation form: MLP 784-1024x3-10, 256 boxes, 300 "
+                         "Active Set iterations, then the bound and its envelope gradient")
     ap.add_argument("--batched", action="store_true",
                     help="also time BASELINE's batching form: 4096 subdomains, 500 Active Set iterations")
     args = ap.parse_args()
@@ -560,6 +601,8 @@ def main():
     }
     if args.batched:
         line["batched"] = batched_run(binding, torch, dev, stream, rank)
+    if args.differentiation:
+        line["differentiation"] = differentiation_run(binding, torch, dev, stream, rank)
     if args.precision:
         line["precision"] = precision_run(binding, torch, dev, stream, rank, S=args.precision_subproblems)
     if rank == 0 and not args.no_cpu_baseline:
