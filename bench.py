@@ -368,10 +368,28 @@ def differentiation_run(binding, torch, dev, stream, rank):
     e[2].record()
     e[2].synchronize()
     ms_it, ms_bw = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+    b32 = bound.cpu().numpy().copy()
     ctx.close()
+    # the same iterations in the BF16 form (the gradient is taken in float32 either way)
+    opt16 = binding.default_options(bigm_iters=60, as_iters=240, omega=72, max_cuts=5, graph_chunk=25, precision=16)
+    c16 = binding.Context(prob["net"], prob["lo"], prob["hi"], prob["C"], options=opt16, stream=stream)
+    c16.reset(t["lo"], t["hi"], t["C"])
+    c16.as_step(iters)
+    torch.cuda.synchronize()
+    c16.reset(t["lo"], t["hi"], t["C"])
+    e[0].record()
+    c16.as_step(iters)
+    e[1].record()
+    e[1].synchronize()
+    ms16 = e[0].elapsed_time(e[1])
+    c16.bound_into(64, bound)
+    b16 = bound.cpu().numpy()
+    c16.close()
     return {"workload": {"net": "mlp_784_1024x3_10", "subproblems": S, "iterations": iters, "eps": 0.1},
             "value": S * iters / (ms_it / 1e3), "unit": UNIT, "ms_iterations": ms_it,
-            "ms_bound_and_backward": ms_bw, "mean_final_bound": float(bound.mean())}
+            "ms_bound_and_backward": ms_bw, "mean_final_bound": float(b32.mean()),
+            "bf16": {"value": S * iters / (ms16 / 1e3), "ms_iterations": ms16, "mean_final_bound": float(b16.mean()),
+                     "minus_fp32_final_bound_mean": float((b16 - b32).mean())}}
 
 
 def captured_traffic(workload, kernel):
