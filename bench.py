@@ -40,10 +40,11 @@ AS_BIGM, AS_ITERS, SP_BIGM, SP_ITERS = 200, 800, 200, 1000
 
 
 def workload_options(binding, profile=0):
+    # autotune: each context times its passes' team sizes on its own net and batch at creation
     as_opt = binding.default_options(bigm_iters=AS_BIGM, as_iters=AS_ITERS, omega=round(0.3 * AS_ITERS),
-                                     max_cuts=5, graph_chunk=25, profile=profile)
+                                     max_cuts=5, graph_chunk=25, profile=profile, autotune=1)
     sp_opt = binding.default_options(bigm_iters=SP_BIGM, as_iters=0, max_cuts=5, graph_chunk=25,
-                                     profile=profile)
+                                     profile=profile, autotune=1)
     return as_opt, sp_opt
 
 
@@ -187,7 +188,7 @@ def batched_run(binding, torch, dev, stream, rank):
     from paper_2101_05844_gb300 import synth
     prob = synth.problem("wide_conv_bab", S=4096, seed=rank)
     S = 4096
-    opt = binding.default_options(bigm_iters=100, as_iters=400, omega=120, max_cuts=5, graph_chunk=25)
+    opt = binding.default_options(bigm_iters=100, as_iters=400, omega=120, max_cuts=5, graph_chunk=25, autotune=1)
     t = {k: torch.from_numpy(prob[k]).to(dev) for k in ("lo", "hi", "C", "splits", "caps")}
     ctx = binding.Context(prob["net"], prob["lo"], prob["hi"], prob["C"], splits=prob["splits"],
                           caps=prob["caps"], options=opt, stream=stream)
@@ -206,7 +207,7 @@ def batched_run(binding, torch, dev, stream, rank):
     e1.record()
     e1.synchronize()
     ms = e0.elapsed_time(e1)
-    prof = binding.default_options(bigm_iters=100, as_iters=400, omega=120, max_cuts=5, profile=1)
+    prof = binding.default_options(bigm_iters=100, as_iters=400, omega=120, max_cuts=5, profile=1, autotune=1)
     pc = binding.Context(prob["net"], prob["lo"], prob["hi"], prob["C"], splits=prob["splits"],
                          caps=prob["caps"], options=prof, stream=stream)
     run(pc)
@@ -219,9 +220,11 @@ def batched_run(binding, torch, dev, stream, rank):
     flops = algorithmic_flops(prob["net"], S, top, mean_slots, kt[top][1])
     peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2.07e9 / 1e12
     achieved = flops / (kt[top][0] / 1e3) / 1e12
+    teams = ctx.team_targets()
     ctx.close()
     pc.close()
     return {"workload": "wide_conv_bab", "subproblems": S, "iterations": 500, "value": S * 500 / (ms / 1e3),
+            "team_targets": {"row": teams[0], "col": teams[1]},
             "unit": UNIT, "ms": ms, "roofline": {"bound": "alu", "kernel": top, "achieved": achieved, "peak": peak,
                                                  "unit": "TFLOP/s", "frac": achieved / peak},
             "kernel_ms": {k: v[0] for k, v in kt.items() if v[1]}}
@@ -603,7 +606,9 @@ def main():
         "config": {"workload": args.workload, "subproblems_per_gpu": S,
                    "iterations_per_step": {"active_set": AS_BIGM + AS_ITERS, "big_m_before_sp": SP_BIGM,
                                            "saddle_point": SP_ITERS},
-                   "l2": "flushed between timed steps (write of 2x L2)", "parallelism": f"replicas x{world}"},
+                   "l2": "flushed between timed steps (write of 2x L2)", "parallelism": f"replicas x{world}",
+                   "team_targets": {"active_set": list(ctx_as.team_targets()),
+                                    "saddle_point": list(ctx_sp.team_targets())}},
         "e2e": {"value": e2e_value, "unit": UNIT, "ms_per_step": ms_e2e,
                 "h2d_bytes_per_step": 2 * (lo_h.numel() * 4 + hi_h.numel() * 4 + C_h.numel() * 4),
                 "d2h_bytes_per_step": 2 * S * 8},

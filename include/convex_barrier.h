@@ -80,6 +80,9 @@ typedef struct as_options {
     int track_best;      /* 1: evaluate the bound at every iteration and keep the best        */
     int graph_chunk;     /* iterations per captured CUDA graph (0: plain launches)           */
     int profile;         /* 1: time every kernel with CUDA events (disables graphs)           */
+    int autotune;        /* 1: as_init times the float32 passes' team-size targets (threads per
+                          * layer segment) on this context's net and batch, a few iterations
+                          * each, and keeps the fastest (see as_team_targets); 0: defaults  */
     int precision;       /* products of the Big-M / Active Set passes: 32 (float32, default) or
                           * 16 (the BF16 form: W x* and every masked product (W o I_b) x*, W^T and
                           * every masked W^T product run on the tensor cores with bf16 operands
@@ -236,6 +239,12 @@ const char* as_last_error(as_ctx* ctx);
 #define AS_NOALLOC_SCRATCH_FLOATS (1u << 22)
 int as_ibp_noalloc(const as_net* net, int S, const float* x_lo, const float* x_hi,
                    const signed char* splits, float* lhat, float* uhat, void* stream);
+
+/* The team-size targets of the float32 Active Set passes (threads a layer segment of the row
+ * and of the col pass aims for; the lanes per neuron follow from them): the defaults, or what
+ * as_options.autotune chose. Host pointers; AS_ERR_ARG if any is null. No counterpart in the
+ * paper: launch geometry of this implementation. */
+int as_team_targets(as_ctx* ctx, long long* row, long long* col);
 
 /* BF16 tensor-core GEMM, D = A . B^T (the building block of the BF16 form of the masked
  * products of Sec. 4.1 / eq. 6 and eq. 9: at Active Set iterates every masked product is a dense

@@ -26,7 +26,8 @@ MAX_LAYERS, MAX_CUTS = 10, 8
 
 EXPORTS = ["as_default_options", "as_init", "as_reset", "as_step", "sp_step", "as_bound",
            "as_bound_backward", "as_state_size", "as_get_state", "as_set_state", "as_launch_count",
-           "as_kernel_times", "as_destroy", "as_last_error", "as_ibp_noalloc", "as_gemm_bf16"]
+           "as_kernel_times", "as_destroy", "as_last_error", "as_ibp_noalloc", "as_gemm_bf16",
+           "as_team_targets"]
 KERNELS = ["as_colA", "as_rowB", "reduce", "sp_colA", "sp_rowB", "sp_colC", "spi_row", "spi_col", "tc_col",
            "tc_row", "slot_sums"]
 
@@ -51,7 +52,7 @@ class Options(ct.Structure):
                 ("sp_gamma0", ct.c_double), ("sp_c_alpha", ct.c_double), ("sp_c_beta", ct.c_double),
                 ("sp_init_steps", ct.c_int), ("sp_init_lr0", ct.c_double), ("sp_init_lr1", ct.c_double),
                 ("track_best", ct.c_int), ("graph_chunk", ct.c_int), ("profile", ct.c_int),
-                ("precision", ct.c_int)]
+                ("autotune", ct.c_int), ("precision", ct.c_int)]
 
 
 _lib = None
@@ -90,6 +91,8 @@ def lib() -> ct.CDLL:
         L.as_gemm_bf16.argtypes = [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_int, ct.c_int,
                                    ct.c_int, ct.c_int, ct.c_int, ct.c_void_p]
         L.as_gemm_bf16.restype = ct.c_int
+        L.as_team_targets.argtypes = [ct.c_void_p, ct.POINTER(ct.c_longlong), ct.POINTER(ct.c_longlong)]
+        L.as_team_targets.restype = ct.c_int
         _lib = L
     return _lib
 
@@ -189,6 +192,12 @@ class Context:
                 conv(uhat, np.float32), conv(splits, np.int8), conv(caps, np.int32)]
         self._reset_keep = args
         self._check(lib().as_reset(self.h, *[_ptr(a) for a in args]))
+
+    def team_targets(self) -> tuple:
+        """(row, col) team-size targets of the float32 passes: defaults or as_options.autotune's."""
+        r, c = ct.c_longlong(), ct.c_longlong()
+        self._check(lib().as_team_targets(self.h, ct.byref(r), ct.byref(c)))
+        return r.value, c.value
 
     def kernel_times(self) -> dict:
         """{kernel name: (total ms, launches)} with options.profile = 1."""

@@ -63,6 +63,7 @@ struct as_ctx {
     int* tc_status = nullptr;                     // set by a tensor-core kernel whose wait ran out
     TSegs tA1{}, tB1{};                           // one lane per unit
     int blocksTA1 = 0, blocksTB1 = 0;
+    long long team_row = 40000, team_col = 40000; // team-size targets of the float32 passes
 };
 
 static int fail(as_ctx* c, int code, const char* fmt, ...) {
@@ -137,6 +138,13 @@ extern "C" void as_default_options(as_options* o) {
 }
 
 extern "C" const char* as_last_error(as_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+extern "C" int as_team_targets(as_ctx* c, long long* row, long long* col) {
+    if (!c || !row || !col) return AS_ERR_ARG;
+    *row = c->team_row;
+    *col = c->team_col;
+    return AS_OK;
+}
 extern "C" long long as_launch_count(as_ctx* c) { return c ? c->launches : -1; }
 
 static int check_launch(as_ctx* c, const char* what) {
@@ -390,14 +398,14 @@ static int team_size(long long units, long long fan, long long target) {
     return T;
 }
 
+// Threads a layer's segment aims for, row and col passes (as_options.autotune picks them per
+// context; the default was measured on the Wide conv net with 9 subproblems: about a quarter of
+// the threads the GPU holds at once, teams long enough to keep loads in flight, short enough not
+// to replicate per-unit work). CB_TEAM_TARGET_ROW / CB_TEAM_TARGET_COL override them.
 static int make_team_segs(as_ctx* c) {
     DNet& D = c->net;
     const int n = D.n, S = D.S;
-    // threads a layer's segment aims for, row and col passes; measured on the Wide conv net with
-    // 9 subproblems (about a quarter of the threads the GPU holds at once does best: teams long
-    // enough to keep loads in flight, short enough not to replicate per-unit work);
-    // CB_TEAM_TARGET_ROW / CB_TEAM_TARGET_COL override them
-    long long target_row = 40000, target_col = 40000;
+    long long target_row = c->team_row, target_col = c->team_col;
     if (const char* e = getenv("CB_TEAM_TARGET_ROW")) target_row = atoll(e) > 0 ? atoll(e) : target_row;
     if (const char* e = getenv("CB_TEAM_TARGET_COL")) target_col = atoll(e) > 0 ? atoll(e) : target_col;
     auto build = [&](TSegs& sg, int& blocks, bool col) -> int {
@@ -604,6 +612,58 @@ extern "C" int as_reset(as_ctx* c, const float* x_lo, const float* x_hi, const f
     return load_batch(c, x_lo, x_hi, C, lhat, uhat, splits, caps, false);
 }
 
+static int launch_as_iter(as_ctx* c, cudaStream_t s);
+
+// Device time of `reps` float32 Active Set iterations at the last planned iteration (every slot in
+// use: the walks' cost does not depend on the dual values), after one untimed iteration.
+static int time_iters(as_ctx* c, int reps, float* ms) {
+    const int it = c->sc.ntab - 2 > 0 ? c->sc.ntab - 2 : 0;
+    int w[3] = {it, 0, 0};
+    CUDA_TRY(c, cudaMemcpyAsync(c->st.ctr, w, sizeof w, cudaMemcpyHostToDevice, c->stream));
+    TRY(launch_as_iter(c, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->st.ctr, w, sizeof w, cudaMemcpyHostToDevice, c->stream));
+    cudaEvent_t a, b;
+    CUDA_TRY(c, cudaEventCreate(&a));
+    CUDA_TRY(c, cudaEventCreate(&b));
+    CUDA_TRY(c, cudaEventRecord(a, c->stream));
+    int r = AS_OK;
+    for (int q = 0; q < reps && r == AS_OK; ++q) r = launch_as_iter(c, c->stream);
+    cudaEventRecord(b, c->stream);
+    cudaError_t e = cudaEventSynchronize(b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (r != AS_OK) return r;
+    if (e != cudaSuccess) return fail(c, AS_ERR_CUDA, "autotune timing failed: %s", cudaGetErrorString(e));
+    return AS_OK;
+}
+
+// as_options.autotune: the team-size targets of the col pass, then of the row pass, each the
+// fastest of a doubling sequence on this context's own net and batch. The caller reloads the
+// batch afterwards (the timing iterations move the duals).
+static int autotune_teams(as_ctx* c) {
+    static const long long cand[] = {5000, 10000, 20000, 40000, 80000, 160000, 320000};
+    const bool prof = c->opt.profile != 0;
+    c->opt.profile = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        long long best = pass ? c->team_row : c->team_col;
+        float best_ms = 0.f;
+        for (long long t : cand) {
+            (pass ? c->team_row : c->team_col) = t;
+            TRY(make_team_segs(c));
+            float ms = 0.f;
+            TRY(time_iters(c, 4, &ms));
+            if (best_ms == 0.f || ms < best_ms) {
+                best_ms = ms;
+                best = t;
+            }
+        }
+        (pass ? c->team_row : c->team_col) = best;
+    }
+    c->opt.profile = prof ? 1 : 0;
+    return make_team_segs(c);
+}
+
 static int init_impl(as_ctx* c, const as_net* net, int S, const float* x_lo, const float* x_hi, const float* C,
                      const float* lhat, const float* uhat, const signed char* splits, const int* caps,
                      const as_options* opt) {
@@ -703,6 +763,10 @@ static int init_impl(as_ctx* c, const as_net* net, int S, const float* x_lo, con
     TRY(build_tables(c));
     if (c->opt.precision == 16) TRY(build_bf16(c, Wh));
     TRY(load_batch(c, x_lo, x_hi, C, lhat, uhat, splits, caps, true));
+    if (c->opt.autotune && c->opt.precision == 32) {
+        TRY(autotune_teams(c));
+        TRY(load_batch(c, x_lo, x_hi, C, lhat, uhat, splits, caps, false));   // back to zero duals
+    }
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     return AS_OK;
 }

@@ -531,3 +531,23 @@ def test_batched_subdomains_lockstep_with_splits_and_caps():
             np.testing.assert_allclose(sb[s, b][ok], ref[ok], rtol=1e-5, atol=1e-7)
         for b in range(nslots, ctx.cap):
             assert (sb[s, b] == 0).all()      # capped: the slot stays empty
+
+
+def test_autotune_picks_a_candidate_and_starts_from_zero_duals():
+    """as_options.autotune times team-size targets with real iterations at init, then reloads the
+    batch: the context starts at zero duals (the interval bound) and iterates to valid bounds."""
+    prob, Ps = _problems("small_conv", 3)
+    kw = dict(bigm_iters=10, as_iters=30, omega=8, max_cuts=5)
+    ctx = binding.context_for(prob, binding.default_options(graph_chunk=0, autotune=1, **kw))
+    cands = {5000, 10000, 20000, 40000, 80000, 160000, 320000}
+    row, col = ctx.team_targets()
+    assert row in cands and col in cands
+    b0 = ctx.bound()
+    for s, P in enumerate(Ps):
+        assert b0[s] == pytest.approx(P.ibp_output_bound(), abs=1e-4, rel=1e-5)
+    ctx.as_step(40)
+    b = ctx.bound()
+    for s, P in enumerate(Ps):
+        assert b0[s] - 1e-6 <= b[s] <= sample_min_output(P, 5000) + 1e-6
+    plain = binding.context_for(prob, binding.default_options(graph_chunk=0, **kw))
+    assert plain.team_targets() == (40000, 40000)
