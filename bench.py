@@ -223,8 +223,21 @@ def batched_run(binding, torch, dev, stream, rank):
     teams = ctx.team_targets()
     ctx.close()
     pc.close()
+    # the same run in the BF16 form (tensor-core products), for comparison
+    o16 = binding.default_options(bigm_iters=100, as_iters=400, omega=120, max_cuts=5, graph_chunk=25, precision=16)
+    c16 = binding.Context(prob["net"], prob["lo"], prob["hi"], prob["C"], splits=prob["splits"],
+                          caps=prob["caps"], options=o16, stream=stream)
+    run(c16)
+    torch.cuda.synchronize()
+    e0.record()
+    run(c16)
+    e1.record()
+    e1.synchronize()
+    ms16 = e0.elapsed_time(e1)
+    c16.close()
     return {"workload": "wide_conv_bab", "subproblems": S, "iterations": 500, "value": S * 500 / (ms / 1e3),
             "team_targets": {"row": teams[0], "col": teams[1]},
+            "bf16": {"value": S * 500 / (ms16 / 1e3), "ms": ms16},
             "unit": UNIT, "ms": ms, "roofline": {"bound": "alu", "kernel": top, "achieved": achieved, "peak": peak,
                                                  "unit": "TFLOP/s", "frac": achieved / peak},
             "kernel_ms": {k: v[0] for k, v in kt.items() if v[1]}}
