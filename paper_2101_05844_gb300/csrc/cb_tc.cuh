@@ -9,9 +9,9 @@
 // column = output column, float32). K advances in tiles of 64: every thread stages 16-byte pieces
 // of the A and B tiles into shared memory with cp.async, in the canonical no-swizzle K-major layout
 // (8-row x 16-byte core matrices; core (r8, k8) at byte ((r8 * 8) + k8) * 128 of the tile, so that
-// core matrices adjacent in K are 128 bytes apart and those adjacent in M/N 1024 bytes apart), two
-// stages deep. One thread issues four tcgen05.mma (K = 16 each) per tile and commits them to the
-// stage's mbarrier; the stage is refilled once that barrier completes. The epilogue reads the
+// core matrices adjacent in K are 128 bytes apart and those adjacent in M/N 1024 bytes apart), four
+// stages deep (three tiles' loads in flight). One thread issues four tcgen05.mma (K = 16 each) per
+// tile and commits them to the stage's mbarrier; the stage is refilled once that barrier completes. The epilogue reads the
 // accumulator back with tcgen05.ld (each warp its 32 TMEM lanes) and stores it to global memory.
 //
 // Every wait is bounded: a barrier that does not complete within the limit sets *status and the
@@ -25,7 +25,7 @@
 namespace cb {
 namespace tc {
 
-constexpr int TC_BM = 128, TC_BK = 64, TC_THREADS = 128, TC_STAGES = 2;
+constexpr int TC_BM = 128, TC_BK = 64, TC_THREADS = 128, TC_STAGES = 4;
 constexpr uint32_t TC_WAIT_LIMIT = 1u << 24;   // try_wait rounds before a barrier counts as lost
 constexpr int TC_ERR_TIMEOUT = 6;             // value written to *status (AS_ERR_TIMEOUT)
 constexpr int TC_ZERO_CHUNK = -2147483647 - 1; // K-offset marking a chunk of zeros
@@ -208,29 +208,34 @@ __device__ __forceinline__ void gemm_tile(const Gather& ga, const uint16_t* __re
     const int KT = (K + TC_BK - 1) / TC_BK;
     bool ok = true;
 
-    stage_gather(sbase, ga, rb, m0, M, 0, K);
-    stage_tile(sbase + A_BYTES, B, ldb, n0, N, 0, K, BN);
-    cp_async_commit();
+    // prologue: tiles 0 .. TC_STAGES - 2 in flight (one cp.async group per tile, empty past KT)
+#pragma unroll
+    for (int p = 0; p < TC_STAGES - 1; ++p) {
+        if (p < KT) {
+            const uint32_t st = sbase + p * STAGE;
+            stage_gather(st, ga, rb, m0, M, p * TC_BK, K);
+            stage_tile(st + A_BYTES, B, ldb, n0, N, p * TC_BK, K, BN);
+        }
+        cp_async_commit();
+    }
     int issued = 0;   // commits issued by thread 0 (stage of commit c: c % TC_STAGES)
     for (int kt = 0; kt < KT; ++kt) {
         const int s = kt % TC_STAGES;
+        const int kn = kt + TC_STAGES - 1;   // the tile loaded this iteration
         bool w_ok = true;
-        // stage (kt + 1) % TC_STAGES was last read by the MMAs of tile kt + 1 - TC_STAGES
-        if (kt + 1 < KT && kt + 1 >= TC_STAGES)
-            w_ok = mbar_wait(&bars[(kt + 1) % TC_STAGES], ((kt + 1 - TC_STAGES) / TC_STAGES) & 1u);
+        // its stage was last read by the MMAs of tile kt - 1
+        if (kn < KT && kt >= 1) w_ok = mbar_wait(&bars[(kt - 1) % TC_STAGES], ((kt - 1) / TC_STAGES) & 1u);
         if (!__syncthreads_and(w_ok)) {   // the decision is the CTA's, so every thread leaves together
             ok = false;
             break;
         }
-        if (kt + 1 < KT) {
-            const uint32_t st = sbase + ((kt + 1) % TC_STAGES) * STAGE;
-            stage_gather(st, ga, rb, m0, M, (kt + 1) * TC_BK, K);
-            stage_tile(st + A_BYTES, B, ldb, n0, N, (kt + 1) * TC_BK, K, BN);
-            cp_async_commit();
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
+        if (kn < KT) {
+            const uint32_t st = sbase + (kn % TC_STAGES) * STAGE;
+            stage_gather(st, ga, rb, m0, M, kn * TC_BK, K);
+            stage_tile(st + A_BYTES, B, ldb, n0, N, kn * TC_BK, K, BN);
         }
+        cp_async_commit();
+        cp_async_wait<TC_STAGES - 1>();   // tile kt has landed
         fence_proxy_async();
         __syncthreads();
         if (tid == 0) {
