@@ -9,9 +9,10 @@
 // column = output column, float32). K advances in tiles of 64: every thread stages 16-byte pieces
 // of the A and B tiles into shared memory with cp.async, in the canonical no-swizzle K-major layout
 // (8-row x 16-byte core matrices; core (r8, k8) at byte ((r8 * 8) + k8) * 128 of the tile, so that
-// core matrices adjacent in K are 128 bytes apart and those adjacent in M/N 1024 bytes apart), four
-// stages deep (three tiles' loads in flight). One thread issues four tcgen05.mma (K = 16 each) per
-// tile and commits them to the stage's mbarrier; the stage is refilled once that barrier completes. The epilogue reads the
+// core matrices adjacent in K are 128 bytes apart and those adjacent in M/N 1024 bytes apart),
+// TC_STAGES deep (two: on GB300 more CTAs per SM hid the load latency better than deeper stages,
+// measured with four). One thread issues four tcgen05.mma (K = 16 each) per tile and commits them
+// to the stage's mbarrier; the stage is refilled once that barrier completes. The epilogue reads the
 // accumulator back with tcgen05.ld (each warp its 32 TMEM lanes) and stores it to global memory.
 //
 // Every wait is bounded: a barrier that does not complete within the limit sets *status and the
@@ -25,7 +26,7 @@
 namespace cb {
 namespace tc {
 
-constexpr int TC_BM = 128, TC_BK = 64, TC_THREADS = 128, TC_STAGES = 4;
+constexpr int TC_BM = 128, TC_BK = 64, TC_THREADS = 128, TC_STAGES = 2;
 constexpr uint32_t TC_WAIT_LIMIT = 1u << 24;   // try_wait rounds before a barrier counts as lost
 constexpr int TC_ERR_TIMEOUT = 6;             // value written to *status (AS_ERR_TIMEOUT)
 constexpr int TC_ZERO_CHUNK = -2147483647 - 1; // K-offset marking a chunk of zeros
