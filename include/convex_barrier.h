@@ -240,10 +240,12 @@ const char* as_last_error(as_ctx* ctx);
 int as_ibp_noalloc(const as_net* net, int S, const float* x_lo, const float* x_hi,
                    const signed char* splits, float* lhat, float* uhat, void* stream);
 
-/* The team-size targets of the float32 Active Set passes (threads a layer segment of the row
- * and of the col pass aims for; the lanes per neuron follow from them): the defaults, or what
- * as_options.autotune chose. Host pointers; AS_ERR_ARG if any is null. No counterpart in the
- * paper: launch geometry of this implementation. */
+/* The team-size targets of the float32 Active Set passes in effect (threads a layer segment of
+ * the row and of the col pass aims for; the lanes per neuron follow from them): the defaults,
+ * what as_options.autotune chose, or the values of the environment variables
+ * CB_TEAM_TARGET_ROW / CB_TEAM_TARGET_COL, which take precedence and are not tuned. Host
+ * pointers; AS_ERR_ARG if any is null. No counterpart in the paper: launch geometry of this
+ * implementation. */
 int as_team_targets(as_ctx* ctx, long long* row, long long* col);
 
 /* BF16 tensor-core GEMM, D = A . B^T (the building block of the BF16 form of the masked

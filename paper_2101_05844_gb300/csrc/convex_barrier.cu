@@ -408,6 +408,8 @@ static int make_team_segs(as_ctx* c) {
     long long target_row = c->team_row, target_col = c->team_col;
     if (const char* e = getenv("CB_TEAM_TARGET_ROW")) target_row = atoll(e) > 0 ? atoll(e) : target_row;
     if (const char* e = getenv("CB_TEAM_TARGET_COL")) target_col = atoll(e) > 0 ? atoll(e) : target_col;
+    c->team_row = target_row;   // the targets in effect (as_team_targets)
+    c->team_col = target_col;
     auto build = [&](TSegs& sg, int& blocks, bool col) -> int {
         const int nseg = col ? n : n - 1;
         sg.n = nseg;
@@ -616,6 +618,22 @@ static int launch_as_iter(as_ctx* c, cudaStream_t s);
 
 // Device time of `reps` float32 Active Set iterations at the last planned iteration (every slot in
 // use: the walks' cost does not depend on the dual values), after one untimed iteration.
+static int time_iters(as_ctx* c, int reps, float* ms);
+
+// Device time per iteration, over at least `reps` iterations and about 2 ms (small workloads
+// iterate in tens of microseconds: a few iterations alone would measure noise).
+static int time_per_iter(as_ctx* c, float* ms_per) {
+    float ms = 0.f;
+    TRY(time_iters(c, 4, &ms));
+    int reps = 4;
+    if (ms < 2.f) {
+        reps = (int)std::min(256.f, std::ceil(4.f * 2.f / std::max(ms, 1e-3f)));
+        TRY(time_iters(c, reps, &ms));
+    }
+    *ms_per = ms / reps;
+    return AS_OK;
+}
+
 static int time_iters(as_ctx* c, int reps, float* ms) {
     const int it = c->sc.ntab - 2 > 0 ? c->sc.ntab - 2 : 0;
     int w[3] = {it, 0, 0};
@@ -646,13 +664,15 @@ static int autotune_teams(as_ctx* c) {
     const bool prof = c->opt.profile != 0;
     c->opt.profile = 0;
     for (int pass = 0; pass < 2; ++pass) {
+        // a target pinned by CB_TEAM_TARGET_COL / CB_TEAM_TARGET_ROW is not tuned
+        if (getenv(pass ? "CB_TEAM_TARGET_ROW" : "CB_TEAM_TARGET_COL")) continue;
         long long best = pass ? c->team_row : c->team_col;
         float best_ms = 0.f;
         for (long long t : cand) {
             (pass ? c->team_row : c->team_col) = t;
             TRY(make_team_segs(c));
             float ms = 0.f;
-            TRY(time_iters(c, 4, &ms));
+            TRY(time_per_iter(c, &ms));
             if (best_ms == 0.f || ms < best_ms) {
                 best_ms = ms;
                 best = t;
