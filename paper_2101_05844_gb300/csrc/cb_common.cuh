@@ -49,9 +49,9 @@ struct BfLayer {
     long long PX, PR;         // elements of an input plane [Hp][Wp][Cip], of an output plane [Hpo][Wpo][Cop]
     uint16_t* X;              // [1 + cap][S][2][Hp][Wp][Cip] bf16: x* (slot 0), x* p_b (sign 0) and x* q_b (sign 1)
     uint16_t* R;              // [1 + cap][S][Hpo][Wpo][Cop] bf16: rp (slot 0), bz_b
-    float* Drow;              // [(1 + cap) S Ho Wo][co]: W x* (slot 0) and (W o I_b) x* per output neuron
+    float* Drow;              // [(1 + cap) S][co][Ho Wo]: W x* (slot 0) and (W o I_b) x* per output neuron
     int nph;                  // stride phases (stride^2); input j = (c, y, x) is in phase (y + pad) % st, (x + pad) % st
-    float* Dcol[CB_MAXPH];    // per phase [(1 + cap) S nY nX][2 ci]: W+^T and W-^T products per input
+    float* Dcol[CB_MAXPH];    // per phase [(1 + cap) S][2 ci][nY nX]: W+^T and W-^T products per input
     int Y0a[CB_MAXPH], X0a[CB_MAXPH], nY[CB_MAXPH], nX[CB_MAXPH];   // (y + pad) / st spans nY values from Y0a
 };
 

@@ -183,9 +183,13 @@ constexpr int tc_smem_bytes() {
 // One CTA's 128 x BN tile (blockIdx.x, blockIdx.y) of D = A . B^T with A [M][K] gathered as
 // described by ga, B [N][K] (row stride ldb), D [M][N] (row stride ldd); K and ldb multiples of 8
 // (16-byte row pieces).
+// D layout: row-major [M][N] (row stride ldd), or with dt_P > 0 plane-transposed: row m = q dt_P + p
+// of column n at D[(q N + n) dt_P + p] (for rows (plane, position): the positions of one column
+// contiguous, so that lanes holding consecutive rows store consecutive addresses).
 template <int BN>
 __device__ __forceinline__ void gemm_tile(const Gather& ga, const uint16_t* __restrict__ B, int ldb,
-                                          float* __restrict__ D, int ldd, int M, int N, int K, int* status) {
+                                          float* __restrict__ D, int ldd, int M, int N, int K, int* status,
+                                          int dt_P = 0) {
     static_assert(BN == 32 || BN == 64 || BN == 128 || BN == 256, "BN");
     extern __shared__ __align__(128) uint8_t smem[];
     constexpr int A_BYTES = TC_BM * TC_BK * 2, B_BYTES = BN * TC_BK * 2, STAGE = A_BYTES + B_BYTES;
@@ -266,7 +270,13 @@ __device__ __forceinline__ void gemm_tile(const Gather& ga, const uint16_t* __re
         for (int c0 = 0; c0 < BN; c0 += 16) {
             float v[16];
             tmem_ld16(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0, v);
-            if (row < M) {
+            if (row < M && dt_P > 0) {
+                const int q = row / dt_P, p = row - q * dt_P;
+                float* dr = D + ((size_t)q * N + n0 + c0) * dt_P + p;
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    if (n0 + c0 + j < N) dr[(size_t)j * dt_P] = v[j];
+            } else if (row < M) {
                 float* dr = D + (size_t)row * ldd + n0 + c0;
                 if (n0 + c0 + 16 <= N && (ldd & 3) == 0) {
 #pragma unroll
@@ -306,6 +316,7 @@ struct GemmGroup {
     int rows_per_slot[CB_MAXPH];
     int ldb[CB_MAXPH];
     int N, ldd;
+    int transposed;               // store D plane-transposed with the gather's P (gemm_tile)
     const int* ctr;               // device iteration counter
     DSched sc;
     int row_pass;
@@ -325,7 +336,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_group_bf16(GemmGroup gg, in
     const long long want = (long long)(1 + ns) * gg.rows_per_slot[g];
     const int M = want < gg.M[g] ? (int)want : gg.M[g];
     if ((int)blockIdx.x * TC_BM >= M) return;   // the whole CTA leaves together, before any barrier
-    gemm_tile<BN>(gg.ga[g], gg.B[g], gg.ldb[g], gg.D[g], gg.ldd, M, gg.N, gg.K[g], status);
+    gemm_tile<BN>(gg.ga[g], gg.B[g], gg.ldb[g], gg.D[g], gg.ldd, M, gg.N, gg.K[g], status,
+                  gg.transposed ? gg.ga[g].P : 0);
 }
 
 }  // namespace tc

@@ -243,14 +243,14 @@ __device__ __forceinline__ void as_colA_body(const DNet& net, const DState& st, 
             ph = (ty - Y0 * L.st) * L.st + (tx - X0 * L.st);
             q = (Y0 - B.Y0a[ph]) * B.nX[ph] + (X0 - B.X0a[ph]);
         }
-        const int P = B.nY[ph] * B.nX[ph], ld = 2 * L.ci;
-        const size_t slot = (size_t)net.S * P * ld;
-        const float* d = B.Dcol[ph] + ((size_t)s * P + q) * ld + c;
-        acc = d[0] + d[L.ci];
+        const int P = B.nY[ph] * B.nX[ph];
+        const size_t slot = (size_t)net.S * 2 * L.ci * P, neg = (size_t)L.ci * P;
+        const float* d = B.Dcol[ph] + ((size_t)s * 2 * L.ci + c) * P + q;
+        acc = d[0] + d[neg];
 #pragma unroll
         for (int b = 0; b < NS; ++b) {
             Pp[b] = d[(b + 1) * slot];
-            Pn[b] = d[(b + 1) * slot + L.ci];
+            Pn[b] = d[(b + 1) * slot + neg];
         }
     } else if (valid && k <= net.n - 1) {
         int g, base;
@@ -483,7 +483,7 @@ __device__ __forceinline__ void as_rowB_body(const DNet& net, const DState& st, 
     if (valid && tc) {
         const int P = L.ho * L.wo;
         const size_t slot = (size_t)net.S * P * L.co;
-        const float* d = net.bf[li].Drow + ((size_t)s * P + p) * L.co + co;
+        const float* d = net.bf[li].Drow + ((size_t)s * L.co + co) * P + p;
         acc0 = d[0];
 #pragma unroll
         for (int b = 0; b < NS; ++b) acc[b] = d[(b + 1) * slot];
