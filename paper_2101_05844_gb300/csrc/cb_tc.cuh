@@ -270,7 +270,7 @@ __device__ __forceinline__ void gemm_tile(const Gather& ga, const uint16_t* __re
         for (int c0 = 0; c0 < BN; c0 += 16) {
             float v[16];
             tmem_ld16(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0, v);
-            if (row < M && dt_P > 0) {
+            if (row < M && dt_P > 1) {   // (one position per plane is the row-major layout)
                 const int q = row / dt_P, p = row - q * dt_P;
                 float* dr = D + ((size_t)q * N + n0 + c0) * dt_P + p;
 #pragma unroll
@@ -337,7 +337,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_group_bf16(GemmGroup gg, in
     const int M = want < gg.M[g] ? (int)want : gg.M[g];
     if ((int)blockIdx.x * TC_BM >= M) return;   // the whole CTA leaves together, before any barrier
     gemm_tile<BN>(gg.ga[g], gg.B[g], gg.ldb[g], gg.D[g], gg.ldd, M, gg.N, gg.K[g], status,
-                  gg.transposed ? gg.ga[g].P : 0);
+                  gg.transposed && gg.ga[g].P > 1 ? gg.ga[g].P : 0);
 }
 
 }  // namespace tc
