@@ -143,16 +143,45 @@ __global__ void k_post_from_pre(DNet net, DState st) {
 }
 
 // Property-folded output row: Wout[s] = C[s]^T W_n, bout[s] = C[s] . b_n (FP64 accumulation).
+// Property rows folded into the last layer: Wout[s] = C_s^T W_n, bout[s] = C_s^T b_n (FP64 sums
+// rounded to float32). One block per subproblem: warp 0 first lists the row's nonzero entries in
+// order (ballots over chunks of 32), so that rows like +-e_i cost one term per input; a row with
+// more than CB_FOLD_NZ nonzeros takes the dense sum.
+#define CB_FOLD_NZ 256
 __global__ void k_fold(DNet net, const float* Wlast, const float* blast, const float* C, int n_out,
                        float* Wout, float* bout) {
+    __shared__ int nz_o[CB_FOLD_NZ];
+    __shared__ double nz_c[CB_FOLD_NZ];
+    __shared__ int nnz;
     const int nin = net.L[net.n - 1].n_in;
-    const size_t n = (size_t)net.S * (nin + 1);
-    for (size_t u = blockIdx.x * (size_t)blockDim.x + threadIdx.x; u < n; u += (size_t)gridDim.x * blockDim.x) {
-        const int s = (int)(u / (nin + 1)), j = (int)(u - (size_t)s * (nin + 1));
+    const int s = blockIdx.x;
+    if (threadIdx.x < 32) {
+        int cnt = 0;
+        for (int o0 = 0; o0 < n_out; o0 += 32) {
+            const int o = o0 + (int)threadIdx.x;
+            const double c = o < n_out ? (C ? (double)C[(size_t)s * n_out + o] : 1.0) : 0.0;
+            const unsigned m = __ballot_sync(0xffffffffu, c != 0.0);
+            const int pos = cnt + __popc(m & ((1u << threadIdx.x) - 1u));
+            if (c != 0.0 && pos < CB_FOLD_NZ) {
+                nz_o[pos] = o;
+                nz_c[pos] = c;
+            }
+            cnt += __popc(m);
+        }
+        if (threadIdx.x == 0) nnz = cnt;
+    }
+    __syncthreads();
+    const int k = nnz;
+    for (int j = threadIdx.x; j <= nin; j += blockDim.x) {
         double a = 0.0;
-        for (int o = 0; o < n_out; ++o) {
-            const double c = C ? (double)C[(size_t)s * n_out + o] : 1.0;
-            a += c * (j < nin ? (double)Wlast[(size_t)o * nin + j] : (double)blast[o]);
+        if (k <= CB_FOLD_NZ) {
+            for (int q = 0; q < k; ++q)
+                a += nz_c[q] * (j < nin ? (double)Wlast[(size_t)nz_o[q] * nin + j] : (double)blast[nz_o[q]]);
+        } else {
+            for (int o = 0; o < n_out; ++o) {
+                const double c = C ? (double)C[(size_t)s * n_out + o] : 1.0;
+                a += c * (j < nin ? (double)Wlast[(size_t)o * nin + j] : (double)blast[o]);
+            }
         }
         if (j < nin) Wout[(size_t)s * nin + j] = (float)a;
         else bout[s] = (float)a;

@@ -563,9 +563,8 @@ static int load_batch(as_ctx* c, const float* x_lo, const float* x_hi, const flo
         c->launches++;
     }
     if (C) CUDA_TRY(c, cudaMemcpyAsync(c->C, C, (size_t)S * c->n_out * sizeof(float), cudaMemcpyDefault, s));
-    k_fold<<<grid_for((size_t)S * (c->widths[n - 1] + 1)), CB_THREADS, 0, s>>>(D, c->Wlast, c->blast,
-                                                                             C ? c->C : nullptr, c->n_out,
-                                                                             (float*)D.Wout, (float*)D.bout);
+    k_fold<<<S, CB_THREADS, 0, s>>>(D, c->Wlast, c->blast, C ? c->C : nullptr, c->n_out, (float*)D.Wout,
+                                    (float*)D.bout);
     c->launches++;
     TRY(check_launch(c, "k_fold"));
     if (lhat) {
