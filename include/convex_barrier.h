@@ -240,6 +240,26 @@ const char* as_last_error(as_ctx* ctx);
 int as_ibp_noalloc(const as_net* net, int S, const float* x_lo, const float* x_hi,
                    const signed char* splits, float* lhat, float* uhat, void* stream);
 
+/* Intermediate bounds by batched dual solves (App. E): the pre-activation bounds of hidden layer
+ * k >= 2 are tightened, layer by layer in order, by the Big-M / Active Set bounds (Alg. 1) of
+ * min x_hat_k[i] and of min -x_hat_k[i] over the relaxation of layers 1 .. k-1, with the bounds
+ * already tightened for those layers. Each layer's 2 n_k subproblems per box form batches of
+ * contexts over the sub-network of layers 1 .. k (a conv layer k enters as its dense operator);
+ * the solves run bigm_iters + as_iters iterations of opt (NULL: defaults) and the final iterate's
+ * bound is taken. Layer 1 keeps its interval bounds (exact for an affine map of the box); every
+ * layer's result is intersected with interval propagation and rounded outward to float32. Splits
+ * act through interval propagation (as in as_init), whose clamped intervals contain the tightened
+ * ones; every sub-network solve takes the clamped bounds of the layers before it.
+ *  net, S, x_lo, x_hi, splits: as for as_init (host or device).
+ *  max_batch:  subproblems per context (rounded down to even; 0: 16384), bounding device memory.
+ *  lhat, uhat: outputs, hidden vectors [S][n_1 + ... + n_{n-1}] of float, host or device.
+ *  stream:     cudaStream_t the work is enqueued on; the call synchronises it.
+ * The results feed as_init / as_reset as caller bounds. Returns the first error of the contexts
+ * it creates (AS_ERR_ARG, AS_ERR_SHAPE, AS_ERR_OOM, AS_ERR_CUDA, AS_ERR_NUMERIC). */
+int as_intermediate_bounds(const as_net* net, int S, const float* x_lo, const float* x_hi,
+                           const signed char* splits, const as_options* opt, long long max_batch,
+                           float* lhat, float* uhat, void* stream);
+
 /* The team-size targets of the float32 Active Set passes in effect (threads a layer segment of
  * the row and of the col pass aims for; the lanes per neuron follow from them): the defaults,
  * what as_options.autotune chose, or the values of the environment variables

@@ -27,7 +27,7 @@ MAX_LAYERS, MAX_CUTS = 10, 8
 EXPORTS = ["as_default_options", "as_init", "as_reset", "as_step", "sp_step", "as_bound",
            "as_bound_backward", "as_state_size", "as_get_state", "as_set_state", "as_launch_count",
            "as_kernel_times", "as_destroy", "as_last_error", "as_ibp_noalloc", "as_gemm_bf16",
-           "as_team_targets"]
+           "as_team_targets", "as_intermediate_bounds"]
 KERNELS = ["as_colA", "as_rowB", "reduce", "sp_colA", "sp_rowB", "sp_colC", "spi_row", "spi_col", "tc_col",
            "tc_row", "slot_sums"]
 
@@ -93,6 +93,10 @@ def lib() -> ct.CDLL:
         L.as_gemm_bf16.restype = ct.c_int
         L.as_team_targets.argtypes = [ct.c_void_p, ct.POINTER(ct.c_longlong), ct.POINTER(ct.c_longlong)]
         L.as_team_targets.restype = ct.c_int
+        L.as_intermediate_bounds.argtypes = [ct.POINTER(Net), ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_void_p,
+                                             ct.POINTER(Options), ct.c_longlong, ct.c_void_p, ct.c_void_p,
+                                             ct.c_void_p]
+        L.as_intermediate_bounds.restype = ct.c_int
         _lib = L
     return _lib
 
@@ -271,6 +275,28 @@ def ibp_noalloc(net: list, lo, hi, lhat_out, uhat_out, splits=None, stream: int 
     n = Net(len(net), layers)
     return lib().as_ibp_noalloc(ct.byref(n), int(lo.shape[0]), _ptr(lo), _ptr(hi), _ptr(splits),
                                 _ptr(lhat_out), _ptr(uhat_out), ct.c_void_p(stream))
+
+
+def intermediate_bounds(net: list, lo, hi, splits=None, options: Options | None = None, max_batch: int = 0,
+                        stream: int = 0):
+    """as_intermediate_bounds: pre-activation bounds [S][NH] (lhat, uhat) of every hidden layer,
+    layers 2 .. n-1 tightened by batched Big-M / Active Set solves over sub-networks. Arrays are
+    numpy (host) or torch tensors; numpy outputs are returned."""
+    keep = []
+    layers = (Layer * len(net))(*[_layer_struct(x, keep) for x in net])
+    n = Net(len(net), layers)
+    conv = lambda a, dt: (np.ascontiguousarray(a, dt) if isinstance(a, np.ndarray) else a)
+    lo, hi, splits = conv(lo, np.float32), conv(hi, np.float32), conv(splits, np.int8)
+    S = int(lo.shape[0])
+    NH = sum(x["n_out"] for x in net[:-1])
+    lhat = np.empty((S, NH), np.float32)
+    uhat = np.empty((S, NH), np.float32)
+    opt = options if options is not None else default_options()
+    r = lib().as_intermediate_bounds(ct.byref(n), S, _ptr(lo), _ptr(hi), _ptr(splits), ct.byref(opt),
+                                     int(max_batch), _ptr(lhat), _ptr(uhat), ct.c_void_p(stream))
+    if r != AS_OK:
+        raise CBError(r, "as_intermediate_bounds")
+    return lhat, uhat
 
 
 def gemm_bf16(A, B, D, bn: int = 128, stream: int = 0) -> int:
