@@ -260,6 +260,71 @@ int as_intermediate_bounds(const as_net* net, int S, const float* x_lo, const fl
                            const signed char* splits, const as_options* opt, long long max_batch,
                            float* lhat, float* uhat, void* stream);
 
+/* Branch and bound with stratified bounding (Sec. 6.2) for one property c . f(x) > 0 over one
+ * input box (the canonical form: the property holds when the minimum is positive).
+ * Domains are (box, ReLU splits); each batch takes the batch / 2 domains with the lowest lower
+ * bounds (creation order on ties) and bounds their children together: the split of the ambiguous
+ * unsplit neuron with the largest -lhat uhat / (uhat - lhat) into +1 (passing, first) and -1
+ * (blocking). A child's lower bound is the larger of its own solve's and its parent's; it is
+ * pruned when positive. The network at the input point x_0* of each solve's final iterate gives
+ * the upper bound (Sec. 6.2, footnote); the search stops "falsified" at a negative value
+ * (confirmed by a float64 forward pass on the host), "verified" when no domain is left, and
+ * "unknown" at a limit. Stratification: at the root l_{a_t-a_l} = l_{a_t}(r) - l_{a_l}(r); an
+ * exponential moving average i of the parent-to-child increase (children solved by their parent's
+ * algorithm; re-solves excluded) gives |s|_l = 2^(-l_{a_l}(p)/i + 1) - 1 and
+ * |s|_t = 2^(-(l_{a_l}(p) + l_{a_t-a_l})/i + 1) - 1, and s with its whole subtree moves to a_t when
+ * |s|_l / |s|_t > c_{a_t/a_l} (before the first sample: a_l; i <= 0: a_t when l_{a_t-a_l} > 0; a
+ * non-positive |s|_t: a_t). Warm start (Sec. 8.2): a child's solve starts from its parent's final
+ * alpha, beta_0, beta_1, with zero Adam moments, an empty active set and its algorithm's full
+ * schedule. A domain with no ambiguous unsplit neuron left and a non-positive bound (an exact
+ * relaxation whose solve has not converged) is solved again from its own duals up to
+ * leaf_rebounds times, then set aside (the result is then "unknown" unless falsified).
+ * Intermediate bounds of a domain: interval propagation with its split clamps, intersected with
+ * the root's as_intermediate_bounds when root_intermediate is set. */
+#define AS_BAB_UNKNOWN 0
+#define AS_BAB_VERIFIED 1
+#define AS_BAB_FALSIFIED 2
+typedef struct as_bab_options {
+    as_options loose;        /* a_l: the inexpensive algorithm (default Big-M, 180 iterations: Sec. 8.2) */
+    as_options tight;        /* a_t: the tighter one (default 100 Active Set iterations, after 20 of Big-M) */
+    int stratify;            /* 1: switch from a_l to a_t as above; 0: a_t everywhere                */
+    double cost_ratio;       /* c_{a_t/a_l}; <= 0: the ratio of the two root solves' measured times   */
+    double ema_weight;       /* weight of the newest increase in the moving average (0.3)           */
+    int batch;               /* children bounded together, even, >= 2 (Sec. 8.2: 200-300)           */
+    long long max_domains;   /* solves after which the search stops "unknown"                       */
+    double time_limit;       /* seconds after which it stops "unknown" (<= 0: none)                 */
+    int warm_start;          /* 1: children start from their parent's duals                         */
+    int leaf_rebounds;       /* re-solves of a domain that cannot be split (8)                      */
+    int root_intermediate;   /* 1: tighten the root's intermediate bounds (as_intermediate_bounds)  */
+    as_options intermediate; /* the schedule of those solves                                        */
+} as_bab_options;
+
+typedef struct as_bab_result {
+    int status;              /* AS_BAB_VERIFIED, AS_BAB_FALSIFIED or AS_BAB_UNKNOWN                  */
+    double lower;            /* min lower bound over the final frontier (pruned domains when empty)   */
+    double upper;            /* least property value found (float64 forward at a solve's x_0*)       */
+    long long bounded;       /* solves done (the root counts twice when stratified)                   */
+    long long hard_bounded;  /* of which by a_t                                                       */
+    long long batches, max_depth, frontier;
+    double seconds;          /* wall time of the call                                                 */
+    double cost_ratio;       /* the c_{a_t/a_l} in effect                                             */
+} as_bab_result;
+
+/* Fills *opt with the defaults above. */
+void as_bab_default_options(as_bab_options* opt);
+
+/* Runs the search.
+ *  net:        as for as_init (host or device W, b).
+ *  x_lo, x_hi: [n_0] the input box, host.
+ *  c:          [n_out] the property row, host; NULL when n_out == 1 (c = 1).
+ *  res:        host result; x_best: host [n_0] receiving the point of res->upper, or NULL.
+ *  stream:     cudaStream_t every solve is enqueued on.
+ * Device memory: three contexts of `batch` subproblems (a_l, a_t and a point evaluator) and the
+ * alpha, beta_0, beta_1 of every open domain (12 bytes per hidden neuron per domain). Returns
+ * AS_OK (the verdict is in res->status) or the first error of a context call. */
+int as_bab(const as_net* net, const float* x_lo, const float* x_hi, const float* c, const as_bab_options* opt,
+           as_bab_result* res, float* x_best, void* stream);
+
 /* The team-size targets of the float32 Active Set passes in effect (threads a layer segment of
  * the row and of the col pass aims for; the lanes per neuron follow from them): the defaults,
  * what as_options.autotune chose, or the values of the environment variables

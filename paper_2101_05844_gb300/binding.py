@@ -27,7 +27,7 @@ MAX_LAYERS, MAX_CUTS = 10, 8
 EXPORTS = ["as_default_options", "as_init", "as_reset", "as_step", "sp_step", "as_bound",
            "as_bound_backward", "as_state_size", "as_get_state", "as_set_state", "as_launch_count",
            "as_kernel_times", "as_destroy", "as_last_error", "as_ibp_noalloc", "as_gemm_bf16",
-           "as_team_targets", "as_intermediate_bounds"]
+           "as_team_targets", "as_intermediate_bounds", "as_bab", "as_bab_default_options"]
 KERNELS = ["as_colA", "as_rowB", "reduce", "sp_colA", "sp_rowB", "sp_colC", "spi_row", "spi_col", "tc_col",
            "tc_row", "slot_sums"]
 
@@ -54,6 +54,21 @@ class Options(ct.Structure):
                 ("track_best", ct.c_int), ("graph_chunk", ct.c_int), ("profile", ct.c_int),
                 ("autotune", ct.c_int), ("precision", ct.c_int)]
 
+
+class BabOptions(ct.Structure):
+    _fields_ = [("loose", Options), ("tight", Options), ("stratify", ct.c_int), ("cost_ratio", ct.c_double),
+                ("ema_weight", ct.c_double), ("batch", ct.c_int), ("max_domains", ct.c_longlong),
+                ("time_limit", ct.c_double), ("warm_start", ct.c_int), ("leaf_rebounds", ct.c_int),
+                ("root_intermediate", ct.c_int), ("intermediate", Options)]
+
+
+class BabResult(ct.Structure):
+    _fields_ = [("status", ct.c_int), ("lower", ct.c_double), ("upper", ct.c_double), ("bounded", ct.c_longlong),
+                ("hard_bounded", ct.c_longlong), ("batches", ct.c_longlong), ("max_depth", ct.c_longlong),
+                ("frontier", ct.c_longlong), ("seconds", ct.c_double), ("cost_ratio", ct.c_double)]
+
+
+BAB_STATUS = {0: "unknown", 1: "verified", 2: "falsified"}
 
 _lib = None
 
@@ -97,6 +112,11 @@ def lib() -> ct.CDLL:
                                              ct.POINTER(Options), ct.c_longlong, ct.c_void_p, ct.c_void_p,
                                              ct.c_void_p]
         L.as_intermediate_bounds.restype = ct.c_int
+        L.as_bab_default_options.argtypes = [ct.POINTER(BabOptions)]
+        L.as_bab_default_options.restype = None
+        L.as_bab.argtypes = [ct.POINTER(Net), ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.POINTER(BabOptions),
+                             ct.POINTER(BabResult), ct.c_void_p, ct.c_void_p]
+        L.as_bab.restype = ct.c_int
         _lib = L
     return _lib
 
@@ -297,6 +317,43 @@ def intermediate_bounds(net: list, lo, hi, splits=None, options: Options | None 
     if r != AS_OK:
         raise CBError(r, "as_intermediate_bounds")
     return lhat, uhat
+
+
+def bab_default_options(loose=None, tight=None, intermediate=None, **kw) -> BabOptions:
+    """as_bab_default_options, then the given fields (loose / tight / intermediate: dicts of
+    as_options fields applied on top of their defaults)."""
+    o = BabOptions()
+    lib().as_bab_default_options(ct.byref(o))
+    for name, d in (("loose", loose), ("tight", tight), ("intermediate", intermediate)):
+        for k, v in (d or {}).items():
+            setattr(getattr(o, name), k, v)
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise AttributeError(k)
+        setattr(o, k, v)
+    return o
+
+
+def bab(net: list, lo, hi, crow=None, options: BabOptions | None = None, stream: int = 0) -> dict:
+    """as_bab: branch and bound with stratified bounding for crow . f(x) > 0 over the box [lo, hi]
+    (host arrays); returns the result fields, the status as a word and the point of `upper`."""
+    keep = []
+    layers = (Layer * len(net))(*[_layer_struct(x, keep) for x in net])
+    n = Net(len(net), layers)
+    lo = np.ascontiguousarray(lo, np.float32)
+    hi = np.ascontiguousarray(hi, np.float32)
+    c = None if crow is None else np.ascontiguousarray(crow, np.float32)
+    opt = options if options is not None else bab_default_options()
+    res = BabResult()
+    x = np.full(lo.shape, np.nan, np.float32)
+    r = lib().as_bab(ct.byref(n), _ptr(lo), _ptr(hi), _ptr(c), ct.byref(opt), ct.byref(res), _ptr(x),
+                     ct.c_void_p(stream))
+    if r != AS_OK:
+        raise CBError(r, "as_bab")
+    out = {f: getattr(res, f) for f, _ in BabResult._fields_}
+    out["status"] = BAB_STATUS[res.status]
+    out["x"] = None if np.isnan(x).any() else x
+    return out
 
 
 def gemm_bf16(A, B, D, bn: int = 128, stream: int = 0) -> int:

@@ -2,7 +2,6 @@
 points, and verdicts against the exact minimum of small networks, found by enumerating every
 ReLU activation pattern and solving each linear region's LP exactly."""
 import math
-from itertools import product
 
 import numpy as np
 import pytest
@@ -10,47 +9,9 @@ import pytest
 from oracle import active_set as AS
 from oracle import bab
 from oracle import intermediate as IM
-from oracle import lp
 from oracle import network as nw
 from paper_2101_05844_gb300 import synth
-
-
-def exact_min(net, lo, hi, crow):
-    """min over the box of crow . f(x): every activation pattern's region is a polytope on which
-    f is affine; the minimum is the least of the regions' LP minima."""
-    dense = nw.dense_layers(net)
-    hidden = dense[:-1]
-    Wn, bn, _ = dense[-1]
-    NH = sum(W.shape[0] for W, _, _ in hidden)
-    n0 = len(lo)
-    best = math.inf
-    for pat in product((0, 1), repeat=NH):
-        A, a = np.eye(n0), np.zeros(n0)
-        rows, rhs, off = [], [], 0
-        for W, b, _ in hidden:
-            Ah, ah = W @ A, W @ a + b
-            D = np.array(pat[off:off + W.shape[0]], np.float64)
-            for i in range(W.shape[0]):
-                if D[i]:   # xhat >= 0
-                    rows.append(-Ah[i])
-                    rhs.append(ah[i])
-                else:      # xhat <= 0
-                    rows.append(Ah[i])
-                    rhs.append(-ah[i])
-            A, a = D[:, None] * Ah, D * ah
-            off += W.shape[0]
-        obj = crow @ Wn @ A
-        val, _ = lp.simplex_min(list(obj), [list(r) for r in rows], rhs, list(lo), list(hi))
-        if val is not None:
-            best = min(best, float(val) + float(crow @ (Wn @ a + bn)))
-    return best
-
-
-def shifted(net, t):
-    """The same network with t subtracted from its (single) output."""
-    net = [dict(L) for L in net]
-    net[-1]["b"] = (net[-1]["b"].astype(np.float64) - t).astype(np.float32)
-    return net
+from tests.helpers import exact_min, net_with_shifted_output as _case
 
 
 def _opts(**kw):
@@ -58,18 +19,6 @@ def _opts(**kw):
              batch=8, max_domains=600)
     o.update(kw)
     return bab.BabOptions(**o)
-
-
-def _case(name, seed, margin):
-    """(net shifted so that the property is f(x) - t > 0, box, exact minimum of the shifted net);
-    t = m + margin (M - m) with m, M the exact minimum and maximum of f over the box."""
-    prob = synth.problem(name, S=1, seed=seed)
-    lo, hi = prob["lo"][0], prob["hi"][0]
-    ones = np.ones(1)
-    m = exact_min(prob["net"], lo, hi, ones)
-    M = -exact_min(prob["net"], lo, hi, -ones)
-    net = shifted(prob["net"], m + margin * (M - m))
-    return net, lo, hi, exact_min(net, lo, hi, ones)
 
 
 def test_subtree_ratio_at_hand_evaluated_points():
