@@ -408,6 +408,87 @@ def differentiation_run(binding, torch, dev, stream, rank):
                      "minus_fp32_final_bound_mean": float((b16 - b32).mean())}}
 
 
+def intermediate_run(binding, torch, dev, stream, rank):
+    """Intermediate bounds by batched sub-network solves (App. E) on the wide conv net, one box:
+    layer 2 (2048 conv neurons: 4096 subproblems of conv16 -> conv32 as a dense map) and layer 3
+    (100 neurons: 200 subproblems of conv16 -> conv32 -> FC100), 100 Big-M + 100 Active Set
+    iterations each (timed after a warm-up call); then the headline Active Set schedule on the 9
+    properties of the box, once over interval bounds and once over the tightened bounds."""
+    import numpy as np
+    from paper_2101_05844_gb300 import synth
+    prob = synth.problem("wide_conv", seed=rank)
+    net, S9 = prob["net"], prob["lo"].shape[0]
+    lo1, hi1 = prob["lo"][:1], prob["hi"][:1]
+    ib_bigm, ib_as = 100, 100
+    opt = binding.default_options(bigm_iters=ib_bigm, as_iters=ib_as, omega=40, max_cuts=3, graph_chunk=25,
+                                  autotune=1)
+    binding.intermediate_bounds(net, lo1, hi1, None, opt, stream=stream)
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    e[0].record()
+    lh, uh = binding.intermediate_bounds(net, lo1, hi1, None, opt, stream=stream)
+    e[1].record()
+    e[1].synchronize()
+    ms = e[0].elapsed_time(e[1])
+    widths = [L["n_out"] for L in net[:-1]]
+    units = sum(2 * w for w in widths[1:]) * (ib_bigm + ib_as)
+    # interval bounds for comparison: a context over the whole net computes them at creation
+    ci = binding.Context(net, lo1, hi1, prob["C"][:1], options=binding.default_options(graph_chunk=0))
+    il, iu = ci.get_state(binding.ST_LHAT).reshape(1, -1), ci.get_state(binding.ST_UHAT).reshape(1, -1)
+    ci.close()
+    offs = np.cumsum([0] + widths)
+    width_ratio = {f"layer{k}": float(np.sum(uh[0, offs[k - 1]:offs[k]] - lh[0, offs[k - 1]:offs[k]]) /
+                                      np.sum(iu[0, offs[k - 1]:offs[k]] - il[0, offs[k - 1]:offs[k]]))
+                   for k in range(1, len(widths) + 1)}
+    final = {}
+    aopt, _ = workload_options(binding)
+    for tag, (L, U) in (("interval", (il, iu)), ("tightened", (lh, uh))):
+        c = binding.Context(net, prob["lo"], prob["hi"], prob["C"], np.repeat(L, S9, 0), np.repeat(U, S9, 0),
+                            options=aopt, stream=stream)
+        c.as_step(AS_BIGM + AS_ITERS)
+        final[tag] = [float(v) for v in c.bound()]
+        c.close()
+    gain = np.array(final["tightened"]) - np.array(final["interval"])
+    return {"workload": {"net": "wide_conv 3x32x32 conv16-conv32-FC100-FC10", "boxes": 1, "eps": 2.0 / 255.0,
+                         "subproblems": {"layer2": 2 * widths[1], "layer3": 2 * widths[2]},
+                         "iterations": {"bigm": ib_bigm, "active_set": ib_as, "max_cuts": 3}},
+            "value": units / (ms / 1e3), "unit": UNIT, "ms": ms,
+            "width_over_interval_width": width_ratio,
+            "final_bound_9_properties": {"schedule": f"{AS_BIGM} Big-M + {AS_ITERS} Active Set",
+                                         "interval_bounds_mean": float(np.mean(final["interval"])),
+                                         "tightened_bounds_mean": float(np.mean(final["tightened"])),
+                                         "gain_min": float(gain.min()), "gain_mean": float(gain.mean())}}
+
+
+def bab_run(binding, torch, dev, stream, rank, time_limit):
+    """Branch and bound with stratified bounding (Sec. 6.2) on the wide conv net's box and each of
+    its 9 properties in turn: a_l = 180 Big-M iterations, a_t = the same followed by 100 Active Set
+    iterations (Sec. 8.2), 256 children per batch, warm starts from the parent, root intermediate
+    bounds by 100 Big-M + 100 Active Set iterations; time_limit seconds per property."""
+    from paper_2101_05844_gb300 import synth
+    prob = synth.problem("wide_conv", seed=rank)
+    net, lo, hi = prob["net"], prob["lo"][0], prob["hi"][0]
+    opt = binding.bab_default_options(batch=256, time_limit=time_limit, root_intermediate=1,
+                                      intermediate=dict(bigm_iters=100, as_iters=100, omega=40, max_cuts=3))
+    keys = ("status", "lower", "upper", "bounded", "hard_bounded", "batches", "max_depth", "frontier", "seconds",
+            "cost_ratio")
+    rows, units, secs = [], 0, 0.0
+    it_l = opt.loose.bigm_iters + opt.loose.as_iters
+    it_t = opt.tight.bigm_iters + opt.tight.as_iters
+    for s in range(prob["C"].shape[0]):
+        r = binding.bab(net, lo, hi, prob["C"][s], opt, stream=stream)
+        rows.append({k: r[k] for k in keys})
+        units += (r["bounded"] - r["hard_bounded"]) * it_l + r["hard_bounded"] * it_t
+        secs += r["seconds"]
+    verdicts = {v: sum(1 for x in rows if x["status"] == v) for v in ("verified", "falsified", "unknown")}
+    return {"workload": {"net": "wide_conv 3x32x32 conv16-conv32-FC100-FC10", "boxes": 1, "eps": 2.0 / 255.0,
+                         "properties": len(rows), "batch": 256, "time_limit_s": time_limit,
+                         "a_l": f"Big-M {it_l}", "a_t": f"Big-M {opt.tight.bigm_iters} + Active Set {opt.tight.as_iters}"},
+            "verdicts": verdicts, "domains_per_s": sum(x["bounded"] for x in rows) / secs,
+            "value": units / secs, "unit": UNIT + " (solved domains only, root intermediate bounds included in time)",
+            "seconds": secs, "properties": rows}
+
+
 def captured_traffic(workload, kernel):
     """DRAM bytes per launch of `kernel` from the committed ncu capture of this workload, or None
     when there is none or the kernel source has changed since it was taken."""
@@ -507,6 +588,12 @@ def main():
                          "Active Set iterations, then the bound and its envelope gradient")
     ap.add_argument("--batched", action="store_true",
                     help="also time BASELINE's batching form: 4096 subdomains, 500 Active Set iterations")
+    ap.add_argument("--intermediate", action="store_true",
+                    help="also time intermediate bounds by batched sub-network solves on the wide conv "
+                         "net (one box, layers 2 and 3) and the final bounds they give")
+    ap.add_argument("--bab", action="store_true",
+                    help="also run branch and bound with stratified bounding on the wide conv net's 9 properties")
+    ap.add_argument("--bab-time", type=float, default=10.0, help="time limit per property of --bab (seconds)")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)
@@ -639,6 +726,10 @@ def main():
         line["batched"] = batched_run(binding, torch, dev, stream, rank)
     if args.differentiation:
         line["differentiation"] = differentiation_run(binding, torch, dev, stream, rank)
+    if args.bab:
+        line["bab"] = bab_run(binding, torch, dev, stream, rank, args.bab_time)
+    if args.intermediate:
+        line["intermediate"] = intermediate_run(binding, torch, dev, stream, rank)
     if args.precision:
         line["precision"] = precision_run(binding, torch, dev, stream, rank, S=args.precision_subproblems)
     if rank == 0 and not args.no_cpu_baseline:

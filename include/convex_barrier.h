@@ -286,7 +286,8 @@ int as_intermediate_bounds(const as_net* net, int S, const float* x_lo, const fl
 #define AS_BAB_FALSIFIED 2
 typedef struct as_bab_options {
     as_options loose;        /* a_l: the inexpensive algorithm (default Big-M, 180 iterations: Sec. 8.2) */
-    as_options tight;        /* a_t: the tighter one (default 100 Active Set iterations, after 20 of Big-M) */
+    as_options tight;        /* a_t: the tighter one (default: a_l's 180 Big-M iterations, which
+                              * initialise Active Set (App. B), then 100 Active Set iterations)     */
     int stratify;            /* 1: switch from a_l to a_t as above; 0: a_t everywhere                */
     double cost_ratio;       /* c_{a_t/a_l}; <= 0: the ratio of the two root solves' measured times   */
     double ema_weight;       /* weight of the newest increase in the moving average (0.3)           */

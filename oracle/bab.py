@@ -34,7 +34,7 @@ Readings where Sec. 6.2 and Sec. 8.2 leave the procedure open:
     do not enter the moving average (they tighten by iterations, not by splitting);
   * the search stops with "falsified" as soon as an evaluated point has a negative property value,
     with "verified" when no domain is left, and with "unknown" when max_domains bounds are done;
-  * warm start (Sec. 8.2: dual variables start from the parent's bounding computation): a child's
+  * warm start (Sec. 8.2 starts each child's duals from its parent's solve): a child's
     solve starts from its parent's final alpha, beta_0, beta_1, with zero Adam moments, an empty
     active set and its algorithm's full schedule (its Big-M phase, then Active Set); the root
     starts from zero duals.

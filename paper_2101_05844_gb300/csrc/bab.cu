@@ -328,7 +328,7 @@ extern "C" void as_bab_default_options(as_bab_options* p) {
     p->loose.as_iters = 0;
     p->loose.graph_chunk = 0;
     as_default_options(&p->tight);
-    p->tight.bigm_iters = 20;
+    p->tight.bigm_iters = 180;   // a_t = a_l followed by Active Set: Big-M initialises it (App. B)
     p->tight.as_iters = 100;
     p->tight.omega = 40;
     p->tight.max_cuts = 3;
