@@ -15,6 +15,7 @@ minimiser is unique, dd/dtheta = dL/dtheta at (x*, z*), using the constraint for
   du_0[j]    = -f_0[j] [x_0*[j] = u_0[j]] + sum_i sum_I beta_I[i] ( (1 - z[i]) W I [W < 0]
                                                                   - z[i] W (1 - I) [W >= 0] )[i, j]
 (the last terms come from Lcheck and Ucheck of layer 1, which are built from l_0 and u_0).
+chain_gradient below also lets the intermediate bounds follow theta through interval propagation.
 Parity unpinned against the paper (it has no such gradient); pinned by finite differences.
 """
 from __future__ import annotations
@@ -76,3 +77,58 @@ def bias_gradient(db_dense: np.ndarray, L: dict) -> np.ndarray:
         return db_dense
     oc, oh, ow = L["out_shape"]
     return db_dense.reshape(oc, oh * ow).sum(axis=1)
+
+
+def chain_gradient(P, st: du.DualState, splits=None):
+    """The envelope gradient through the interval propagation that produced the bounds.
+
+    Here lhat_k, uhat_k (k >= 1) are not held fixed but follow theta through interval propagation
+    (App. E, last paragraph), l_k = max(lhat_k, 0), u_k = max(uhat_k, 0), with a split clamping a
+    straddling neuron to a constant. At fixed duals and masks the bound depends on them through
+      * x_k* at an end of its box: dd/dl_k = -f_k [x_k* = l_k], dd/du_k = -f_k [x_k* = u_k];
+      * Lcheck, Ucheck of layer k+1 (the l_0, u_0 terms above, for every k);
+      * the Big-M rows: dd/dlhat_k = beta_{k,1} (1 - z_k), dd/duhat_k = -beta_{k,0} z_k;
+    and interval propagation, lhat_k = W+ l_{k-1} + W- u_{k-1} + b, uhat_k = W+ u_{k-1} + W- l_{k-1}
+    + b, carries these back, layer by layer, to W, b and the box. The kink of max(., 0) at 0 takes
+    the zero derivative; a clamped entry (split +1 with lhat = 0, split -1 with uhat = 0) is a
+    constant. P must hold the interval bounds of its box (Problem built without `bounds`).
+    """
+    val, f, g, x, z = du.evaluate(P, st)
+    base = envelope_gradient(P, st)
+    n = P.n
+    Lb, Ub = [None] * n, [None] * n
+    for k in range(n):
+        lo, hi = P.lo[k], P.hi[k]
+        same = lo == hi
+        a = np.where(same, -0.5 * f[k], np.where(x[k] == lo, -f[k], 0.0))
+        c = np.where(same, -0.5 * f[k], np.where(x[k] == hi, -f[k], 0.0))
+        if k + 1 <= n - 1:
+            W = P.W[k + 1]
+            pos = W >= 0
+            for sl in st.slots[k + 1]:
+                If = sl.I.astype(np.float64)
+                A = (1 - z[k + 1])[:, None] * W * If
+                Cm = z[k + 1][:, None] * W * (1 - If)
+                a = a + sl.beta @ (A * pos - Cm * ~pos)
+                c = c + sl.beta @ (A * ~pos - Cm * pos)
+        Lb[k], Ub[k] = a, c
+    offs = np.cumsum([0] + [P.widths[k] for k in range(1, n)])
+    dW = [None if w is None else w.copy() for w in base["dW"]]
+    db = [None if v is None else v.copy() for v in base["db"]]
+    for k in range(n - 1, 0, -1):
+        lh, uh = P.lhat[k], P.uhat[k]
+        Ah = st.beta1[k] * (1 - z[k]) + np.where(lh > 0, Lb[k], 0.0)
+        Uh = -st.beta0[k] * z[k] + np.where(uh > 0, Ub[k], 0.0)
+        if splits is not None:
+            sp = np.asarray(splits)[offs[k - 1]:offs[k]]
+            Ah = np.where((sp > 0) & (lh == 0), 0.0, Ah)
+            Uh = np.where((sp < 0) & (uh == 0), 0.0, Uh)
+        W = P.W[k]
+        Wp, Wn = np.maximum(W, 0.0), np.minimum(W, 0.0)
+        Lb[k - 1] = Lb[k - 1] + Wp.T @ Ah + Wn.T @ Uh
+        Ub[k - 1] = Ub[k - 1] + Wn.T @ Ah + Wp.T @ Uh
+        pos = W >= 0
+        lo, hi = P.lo[k - 1][None, :], P.hi[k - 1][None, :]
+        dW[k] = dW[k] + Ah[:, None] * np.where(pos, lo, hi) + Uh[:, None] * np.where(pos, hi, lo)
+        db[k] = db[k] + Ah + Uh
+    return dict(value=val, dW=dW, db=db, dlo0=Lb[0], dhi0=Ub[0], x=x, z=z)

@@ -159,3 +159,80 @@ def test_interval_bounds_contain_sampled_preactivations_and_respect_splits():
             assert (P.lhat[k] <= P.uhat[k]).all()
             h = np.maximum(pre, 0)
             off += P.widths[k]
+
+
+def _chain_bound(P, st, splits, mod):
+    """The bound at fixed duals and masks, with interval propagation redone after mod(Q)."""
+    Q = nw.Problem.__new__(nw.Problem)
+    Q.__dict__.update(P.__dict__)
+    Q.W = [None if w is None else w.copy() for w in P.W]
+    Q.b = [None if w is None else w.copy() for w in P.b]
+    lo0, hi0 = P.lo[0].copy(), P.hi[0].copy()
+    Q.lo, Q.hi = [lo0], [hi0]
+    mod(Q)
+    lh, uh, lo, hi = nw.ibp(Q.W[1:Q.n], Q.b[1:Q.n], Q.lo[0], Q.hi[0], splits)
+    Q.lhat, Q.uhat, Q.lo, Q.hi = lh, uh, lo, hi
+    st2 = du.DualState(st.alpha, st.beta0, st.beta1, [[] for _ in range(P.n)])
+    for k in range(1, P.n):
+        for sl in st.slots[k]:
+            du.add_slot(Q, st2, k, sl.I, beta=sl.beta)
+    return du.evaluate(Q, st2)[0]
+
+
+@pytest.mark.parametrize("name,with_splits", [("mlp_4_5_5_1", False), ("small_conv", False),
+                                              ("mlp_3_4_4_4_1", True)])
+def test_chain_gradient_matches_finite_differences(name, with_splits):
+    """Central differences of the bound with the intermediate bounds recomputed by interval
+    propagation at every perturbed point; the chain gradient differs from the fixed-bound one."""
+    prob = synth.problem(name, seed=4)
+    splits = None
+    if with_splits:
+        NH = sum(L["n_out"] for L in prob["net"][:-1])
+        P0 = nw.problems(prob)[0]
+        lh = np.concatenate(P0.lhat[1:])
+        uh = np.concatenate(P0.uhat[1:])
+        amb = np.flatnonzero((lh < 0) & (uh > 0))
+        splits = np.zeros(NH, np.int8)
+        splits[amb[0]] = 1
+        splits[amb[-1]] = -1
+        prob = dict(prob, splits=splits[None, :].repeat(prob["lo"].shape[0], 0))
+    P = nw.problems(prob)[0]
+    s = AS.ActiveSet(P, AS.Options(bigm_iters=30, as_iters=30, omega=10, max_cuts=3)).step(60)
+    st = s.st
+    grad = ev.chain_gradient(P, st, splits)
+    base = ev.envelope_gradient(P, st)
+    rng = synth.SplitMix64(11)
+    h = 1e-6
+
+    def fd(mod):
+        return (_chain_bound(P, st, splits, lambda Q: mod(Q, h)) -
+                _chain_bound(P, st, splits, lambda Q: mod(Q, -h))) / (2 * h)
+
+    checks, differs = 0, 0
+    for k in range(1, P.n + 1):
+        for _ in range(5):
+            i = int(rng.integers(1, 0, P.W[k].shape[0] - 1)[0])
+            j = int(rng.integers(1, 0, P.W[k].shape[1] - 1)[0])
+            if abs(P.W[k][i, j]) < 10 * h:
+                continue
+
+            def m(Q, d):
+                Q.W[k][i, j] += d
+            assert fd(m) == pytest.approx(grad["dW"][k][i, j], rel=1e-5, abs=1e-7)
+            differs += abs(grad["dW"][k][i, j] - base["dW"][k][i, j]) > 1e-4
+            checks += 1
+        i = int(rng.integers(1, 0, P.W[k].shape[0] - 1)[0])
+
+        def mb(Q, d):
+            Q.b[k][i] += d
+        assert fd(mb) == pytest.approx(grad["db"][k][i], rel=1e-5, abs=1e-7)
+    for j in range(min(6, P.widths[0])):
+        def ml(Q, d):
+            Q.lo[0][j] += d
+
+        def mh(Q, d):
+            Q.hi[0][j] += d
+        assert fd(ml) == pytest.approx(grad["dlo0"][j], rel=1e-5, abs=1e-7)
+        assert fd(mh) == pytest.approx(grad["dhi0"][j], rel=1e-5, abs=1e-7)
+        differs += abs(grad["dlo0"][j] - base["dlo0"][j]) > 1e-4
+    assert checks >= 8 and differs >= 2
