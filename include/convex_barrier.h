@@ -151,6 +151,17 @@ int as_bound(as_ctx* ctx, int precision, double* out, double* best);
 int as_bound_backward(as_ctx* ctx, const double* grad_bound, float* const* dW, float* const* db,
                       float* dlo, float* dhi);
 
+/* As as_bound_backward, with the intermediate bounds differentiated too: lhat_k, uhat_k follow W,
+ * b and the box through the interval propagation that as_init / as_reset computed them by
+ * (App. E), post-activation bounds l_k = max(lhat_k, 0), u_k = max(uhat_k, 0), split clamps held
+ * as constants. At fixed duals and masks the bound depends on them through the ends of x_k*'s box,
+ * Lcheck / Ucheck of the next layer's masks, and the Big-M rows (d/dlhat = beta_1 (1 - z),
+ * d/duhat = -beta_0 z); these adjoints run back through W+ and W- layer by layer (the kink of
+ * max(., 0) at 0 takes the zero derivative). Not in the paper. AS_ERR_STATE when the batch's
+ * bounds were given by the caller. Allocates 8 bytes per neuron per subproblem for the call. */
+int as_bound_backward_ibp(as_ctx* ctx, const double* grad_bound, float* const* dW, float* const* db,
+                          float* dlo, float* dhi);
+
 /* Named state buffers, for warm starts and inspection. Sizes in bytes via as_state_size. */
 #define AS_ST_ALPHA 0     /* float [S][NH]                                                    */
 #define AS_ST_BETA0 1     /* float [S][NH]                                                    */

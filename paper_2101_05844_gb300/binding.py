@@ -27,7 +27,7 @@ MAX_LAYERS, MAX_CUTS = 10, 8
 EXPORTS = ["as_default_options", "as_init", "as_reset", "as_step", "sp_step", "as_bound",
            "as_bound_backward", "as_state_size", "as_get_state", "as_set_state", "as_launch_count",
            "as_kernel_times", "as_destroy", "as_last_error", "as_ibp_noalloc", "as_gemm_bf16",
-           "as_team_targets", "as_intermediate_bounds", "as_bab", "as_bab_default_options"]
+           "as_team_targets", "as_intermediate_bounds", "as_bab", "as_bab_default_options", "as_bound_backward_ibp"]
 KERNELS = ["as_colA", "as_rowB", "reduce", "sp_colA", "sp_rowB", "sp_colC", "spi_row", "spi_col", "tc_col",
            "tc_row", "slot_sums"]
 
@@ -90,6 +90,9 @@ def lib() -> ct.CDLL:
         L.as_step.argtypes = [ct.c_void_p, ct.c_int]
         L.sp_step.argtypes = [ct.c_void_p, ct.c_int]
         L.as_bound.argtypes = [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p]
+        L.as_bound_backward_ibp.argtypes = [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p,
+                                            ct.c_void_p]
+        L.as_bound_backward_ibp.restype = ct.c_int
         L.as_bound_backward.argtypes = [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p,
                                         ct.c_void_p]
         L.as_state_size.argtypes = [ct.c_void_p, ct.c_int, ct.POINTER(ct.c_longlong)]
@@ -247,13 +250,16 @@ class Context:
     def bound_into(self, precision: int, out, best=None):
         self._check(lib().as_bound(self.h, precision, _ptr(out), _ptr(best)))
 
-    def backward(self, grad_bound, dW: list, db: list, dlo=None, dhi=None):
+    def backward(self, grad_bound, dW: list, db: list, dlo=None, dhi=None, through_bounds: bool = False):
+        """as_bound_backward (intermediate bounds held fixed), or as_bound_backward_ibp with
+        through_bounds (differentiated through the interval propagation that produced them)."""
         g = np.ascontiguousarray(grad_bound, np.float64) if isinstance(grad_bound, np.ndarray) else grad_bound
         n = self.n_layers
         pw = (ct.c_void_p * n)(*[_ptr(x) for x in dW]) if dW is not None else None
         pb = (ct.c_void_p * n)(*[_ptr(x) for x in db]) if db is not None else None
-        self._check(lib().as_bound_backward(self.h, _ptr(g), ct.cast(pw, ct.c_void_p) if pw else None,
-                                            ct.cast(pb, ct.c_void_p) if pb else None, _ptr(dlo), _ptr(dhi)))
+        fn = lib().as_bound_backward_ibp if through_bounds else lib().as_bound_backward
+        self._check(fn(self.h, _ptr(g), ct.cast(pw, ct.c_void_p) if pw else None,
+                       ct.cast(pb, ct.c_void_p) if pb else None, _ptr(dlo), _ptr(dhi)))
 
     def state_size(self, which: int) -> int:
         n = ct.c_longlong()

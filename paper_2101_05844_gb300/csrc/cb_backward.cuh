@@ -20,11 +20,13 @@ struct GradCtx {
     const double* gb;      // [S] upstream gradient of each subproblem's bound
     int nsl_before;        // slots before the current iteration (global)
     int bo;                // snapshot buffer parity
+    const float* Ah = nullptr;   // [S][NH] adjoints of lhat, uhat (through interval propagation), or null
+    const float* Uh = nullptr;
 };
 
 // Term of dL/dW for subproblem s and pair (i, j) of hidden layer L.
 __device__ __forceinline__ float wgrad_term(const DNet& net, const DState& st, const DLayer& L, int s, int i,
-                                            int j, float w, int nsl, int bo) {
+                                            int j, float w, int nsl, int bo, const float* Ah, const float* Uh) {
     const size_t NT = net.NT, NH = net.NH;
     const size_t xo = (size_t)s * NT + L.in_off + j;
     const size_t h = (size_t)s * NH + L.h_out + i;
@@ -41,6 +43,10 @@ __device__ __forceinline__ float wgrad_term(const DNet& net, const DState& st, c
             g += bb * (((I >> b) & 1u) ? (1.f - z) * Lc - x : -z * Uc);
         }
     }
+    if (Ah) {   // interval propagation: lhat = W+ l + W- u + b, uhat = W+ u + W- l + b
+        const float lo = st.lo[xo], hi = st.hi[xo];
+        g += Ah[h] * (w >= 0.f ? lo : hi) + Uh[h] * (w >= 0.f ? hi : lo);
+    }
     return g;
 }
 
@@ -54,7 +60,7 @@ __global__ void k_grad_W_linear(DNet net, DState st, int li, GradCtx gc, float* 
         double acc = 0.0;
         for (int s = 0; s < net.S; ++s) {
             const int nsl = min(gc.nsl_before, st.caps[s]);
-            acc += gc.gb[s] * (double)wgrad_term(net, st, L, s, i, j, w, nsl, gc.bo);
+            acc += gc.gb[s] * (double)wgrad_term(net, st, L, s, i, j, w, nsl, gc.bo, gc.Ah, gc.Uh);
         }
         dW[u] += (float)acc;
     }
@@ -78,7 +84,7 @@ __global__ void k_grad_W_conv(DNet net, DState st, int li, GradCtx gc, float* dW
         if (y < 0 || y >= L.hi || x < 0 || x >= L.wi) continue;
         const int i = co * P + p, j = (c * L.hi + y) * L.wi + x;
         const int nsl = min(gc.nsl_before, st.caps[s]);
-        acc += gc.gb[s] * (double)wgrad_term(net, st, L, s, i, j, w, nsl, gc.bo);
+        acc += gc.gb[s] * (double)wgrad_term(net, st, L, s, i, j, w, nsl, gc.bo, gc.Ah, gc.Uh);
     }
     __shared__ double red[CB_THREADS];
     red[threadIdx.x] = acc;
@@ -106,6 +112,7 @@ __global__ void k_grad_b(DNet net, DState st, int li, GradCtx gc, float* db) {
             const size_t hs = (size_t)s * net.cap * net.NH + L.h_out + i;
             for (int b = 0; b < nsl; ++b) g -= st.bs[hs + (size_t)b * net.NH];
         }
+        if (gc.Ah) g += gc.Ah[h] + gc.Uh[h];
         acc += gc.gb[s] * (double)g;
     }
     __shared__ double red[CB_THREADS];
@@ -179,6 +186,105 @@ __global__ void k_grad_box(DNet net, DState st, GradCtx gc, float* dlo, float* d
     }
     if (dlo) dlo[u] += (float)(gc.gb[s] * (double)al);
     if (dhi) dhi[u] += (float)(gc.gb[s] * (double)ah);
+}
+
+// Through interval propagation (the chain form of the gradient). Per subproblem and unscaled:
+// Lb, Ub [S][NT] are dd/dl_k, dd/du_k of the post-activation bounds, Ah, Uh [S][NH] dd/dlhat_k,
+// dd/duhat_k of the pre-activation ones.
+//
+// Direct part for the inputs of layer li (post-activation layer li): x* at an end of its box, and
+// Lcheck, Ucheck of layer li's masks (as k_grad_box, for any layer).
+__global__ void k_post_adj(DNet net, DState st, int li, GradCtx gc, float* Lb, float* Ub) {
+    const DLayer& L = net.L[li];
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= net.S * L.n_in) return;
+    const int s = u / L.n_in, j = u - s * L.n_in;
+    const int nsl = min(gc.nsl_before, st.caps[s]);
+    const size_t xo = (size_t)s * net.NT + L.in_off + j;
+    const float lo = st.lo[xo], hi = st.hi[xo];
+    const unsigned xs = st.xsnap[gc.bo][xo];
+    float al = 0.f, ah = 0.f;
+    if (nsl && li <= net.n - 2) {
+        const size_t rb = (size_t)s * net.NH + L.h_out;
+        const size_t sb = (size_t)s * net.cap * net.NH + L.h_out;
+        col_walk(L, j, [&](int i, float w) {
+            const unsigned I = cb_slot_mask(st.zsnap[gc.bo][rb + i], xs, lo == hi, w);
+            const float z = st.zcur[rb + i] ? 1.f : 0.f;
+            float bsum_in = 0.f, bsum_out = 0.f;
+            for (int b = 0; b < nsl; ++b) {
+                const float bb = st.bs[sb + (size_t)b * net.NH + i];
+                if ((I >> b) & 1u) bsum_in += bb;
+                else bsum_out += bb;
+            }
+            const float ti = (1.f - z) * w * bsum_in, to = -z * w * bsum_out;
+            if (w >= 0.f) { al += ti; ah += to; }
+            else { ah += ti; al += to; }
+        });
+    }
+    const float f = st.fval[xo], x = st.xval[xo];
+    if (lo == hi) {
+        al += -0.5f * f;
+        ah += -0.5f * f;
+    } else if (x == hi) {
+        ah += -f;
+    } else {
+        al += -f;
+    }
+    Lb[xo] = al;
+    Ub[xo] = ah;
+}
+
+// Hidden layer li + 1 (outputs of layer li): the Big-M rows give dd/dlhat = beta_1 (1 - z) and
+// dd/duhat = -beta_0 z; l = max(lhat, 0), u = max(uhat, 0) pass Lb, Ub where positive; a split
+// clamp (+1 with lhat = 0, -1 with uhat = 0) makes the bound a constant.
+__global__ void k_hat_adj(DNet net, DState st, int li, const signed char* splits, const float* Lb, const float* Ub,
+                          float* Ah, float* Uh) {
+    const DLayer& L = net.L[li];
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= net.S * L.n_out) return;
+    const int s = u / L.n_out, i = u - s * L.n_out;
+    const size_t h = (size_t)s * net.NH + L.h_out + i;
+    const size_t xo = (size_t)s * net.NT + net.L[li + 1].in_off + i;
+    const float z = st.zcur[h] ? 1.f : 0.f;
+    const float lh = st.lhat[h], uh = st.uhat[h];
+    float a = st.beta1[h] * (1.f - z) + (lh > 0.f ? Lb[xo] : 0.f);
+    float b = -st.beta0[h] * z + (uh > 0.f ? Ub[xo] : 0.f);
+    if (splits) {
+        if (splits[h] > 0 && lh == 0.f) a = 0.f;
+        if (splits[h] < 0 && uh == 0.f) b = 0.f;
+    }
+    Ah[h] = a;
+    Uh[h] = b;
+}
+
+// Back through lhat = W+ l + W- u + b, uhat = W+ u + W- l + b of layer li: adds W+^T Ah + W-^T Uh
+// to Lb and W-^T Ah + W+^T Uh to Ub of its inputs (one thread per input, no atomics).
+__global__ void k_prop_adj(DNet net, int li, const float* Ah, const float* Uh, float* Lb, float* Ub) {
+    const DLayer& L = net.L[li];
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= net.S * L.n_in) return;
+    const int s = u / L.n_in, j = u - s * L.n_in;
+    const size_t rb = (size_t)s * net.NH + L.h_out;
+    float al = 0.f, au = 0.f;
+    col_walk(L, j, [&](int i, float w) {
+        const float a = Ah[rb + i], b = Uh[rb + i];
+        if (w >= 0.f) { al += w * a; au += w * b; }
+        else { al += w * b; au += w * a; }
+    });
+    const size_t xo = (size_t)s * net.NT + L.in_off + j;
+    Lb[xo] += al;
+    Ub[xo] += au;
+}
+
+// dlo, dhi += gb[s] Lb, Ub of the input layer
+__global__ void k_box_out(DNet net, GradCtx gc, const float* Lb, const float* Ub, float* dlo, float* dhi) {
+    const DLayer& L = net.L[0];
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= net.S * L.n_in) return;
+    const int s = u / L.n_in, j = u - s * L.n_in;
+    const size_t xo = (size_t)s * net.NT + L.in_off + j;
+    if (dlo) dlo[u] += (float)(gc.gb[s] * (double)Lb[xo]);
+    if (dhi) dhi[u] += (float)(gc.gb[s] * (double)Ub[xo]);
 }
 
 __device__ __forceinline__ void slot_sums_body(const DNet& net, const DState& st, const Segs& sg, int nadd, int bo,

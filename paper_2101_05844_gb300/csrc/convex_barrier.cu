@@ -30,6 +30,8 @@ struct as_ctx {
     std::vector<as_layer> layers;  // shapes (pointers not kept)
     std::vector<int> widths;       // neuron layers 0..n-1
     bool sp_started = false;
+    bool bounds_ibp = true;        // lhat, uhat of the batch came from interval propagation
+    bool have_splits = false;      // ... with the split clamps of splits_dev
     bool sp_need_phaseA = true;    // the next Saddle Point iteration starts with a separate phase A
     long long launches = 0;
     Segs segA{}, segB{}, segP{};
@@ -528,6 +530,8 @@ static int load_batch(as_ctx* c, const float* x_lo, const float* x_hi, const flo
     cudaStream_t s = c->stream;
     CUDA_TRY(c, cudaMemsetAsync(c->zero_arena, 0, c->zero_bytes, s));
     TRY(clear_planes(c));
+    c->bounds_ibp = lhat == nullptr;
+    c->have_splits = splits != nullptr && lhat == nullptr;
     k_fill<<<grid_for(S), CB_THREADS, 0, s>>>(st.best, (size_t)S, -INFINITY);
     c->launches++;
     c->sp_started = false;

@@ -384,6 +384,60 @@ def test_bound_backward_matches_envelope_gradient(name, S):
         np.testing.assert_allclose(db[k], refb[k], rtol=1e-4, atol=1e-5)
 
 
+@pytest.mark.parametrize("name,S,with_splits", [("mlp_5_7_6_3", 3, False), ("small_conv", 2, False),
+                                                ("mlp_5_7_6_3", 3, True)])
+def test_bound_backward_through_interval_propagation_matches_chain_gradient(name, S, with_splits):
+    """as_bound_backward_ibp against the oracle's chain gradient: the context computes its own
+    interval bounds (with split clamps); the oracle's Problems hold its float64 interval bounds
+    rounded outward to float32 per layer. Tolerance as the fixed-bound backward: 1e-4 relative."""
+    prob = synth.problem(name, S=S, seed=0)
+    if with_splits:
+        P0 = nw.problems(prob)
+        NH = sum(L["n_out"] for L in prob["net"][:-1])
+        sp = np.zeros((S, NH), np.int8)
+        for s, P in enumerate(P0):
+            l, u = np.concatenate(P.lhat[1:]), np.concatenate(P.uhat[1:])
+            amb = np.flatnonzero((l < 0) & (u > 0))
+            sp[s, amb[::3]] = 1
+            sp[s, amb[1::3]] = -1
+        prob = dict(prob, splits=sp)
+    Ps0 = nw.problems(prob)
+    lh, uh = oracle_bounds_f32(Ps0)
+    Ps = nw.problems(prob, bounds=[(split_hidden(lh[s].astype(np.float64), Ps0[0].widths)[1:],
+                                    split_hidden(uh[s].astype(np.float64), Ps0[0].widths)[1:])
+                                   for s in range(S)])
+    kw = dict(bigm_iters=2, as_iters=30, omega=3, max_cuts=4)
+    ctx = binding.context_for(prob, binding.default_options(graph_chunk=0, **kw))
+    solvers = draw_state(Ps, ctx, kw, it=9, nslots=4, seed=7)
+    gb = synth.SplitMix64(3).uniform(S) + 0.5
+    net = prob["net"]
+    dW = [np.zeros_like(L["W"]) for L in net]
+    db = [np.zeros_like(L["b"]) for L in net]
+    dlo, dhi = np.zeros_like(prob["lo"]), np.zeros_like(prob["hi"])
+    ctx.backward(gb, dW, db, dlo, dhi, through_bounds=True)
+    refW = [np.zeros(L["W"].shape) for L in net]
+    refb = [np.zeros(L["b"].shape) for L in net]
+    for s, sv in enumerate(solvers):
+        g = ev.chain_gradient(sv.P, sv.st, None if not with_splits else prob["splits"][s])
+        for k, L in enumerate(net[:-1], start=1):
+            if L["kind"] == "linear":
+                refW[k - 1] += gb[s] * g["dW"][k]
+            else:
+                refW[k - 1] += gb[s] * ev.filter_gradient(g["dW"][k], sv.P.taps[k], L["W"].shape)
+            refb[k - 1] += gb[s] * ev.bias_gradient(g["db"][k], L)
+        refW[-1] += gb[s] * np.outer(prob["C"][s], g["dW"][sv.P.n][0])
+        refb[-1] += gb[s] * prob["C"][s]
+        np.testing.assert_allclose(dlo[s], gb[s] * g["dlo0"], rtol=1e-4, atol=1e-5)
+        np.testing.assert_allclose(dhi[s], gb[s] * g["dhi0"], rtol=1e-4, atol=1e-5)
+    for k in range(len(net)):
+        np.testing.assert_allclose(dW[k], refW[k], rtol=1e-4, atol=1e-5)
+        np.testing.assert_allclose(db[k], refb[k], rtol=1e-4, atol=1e-5)
+    # caller-given bounds have no interval propagation to differentiate
+    ctx2 = binding.context_for(prob, binding.default_options(graph_chunk=0, **kw), bounds=(lh, uh))
+    with pytest.raises(binding.CBError):
+        ctx2.backward(gb, dW, db, dlo, dhi, through_bounds=True)
+
+
 def test_invalid_arguments_are_rejected_before_any_kernel():
     prob = synth.problem("mlp_tiny", seed=0)
     bad = dict(prob)
