@@ -86,8 +86,17 @@ def coefficients(P, st: DualState):
 
 
 def closed_form(P, f, g):
-    """Inner minimisation, eqs. (7)-(8): x_k* at the upper end of its box where f_k >= 0."""
+    """Inner minimisation, eqs. (7)-(8): x_k* at the upper end of its box where f_k >= 0.
+
+    Over an ellipsoid input set (P.ball; centre c, half-widths e of the box) the x_0 part,
+    min -f_0^T x_0, is attained at x_0* = c + e^2 f_0 / |e f_0|_2 (c where f_0 = 0), value
+    -f_0^T c - |e f_0|_2 (Sec. 2: the input set needs only a closed-form linear minimisation)."""
     x = [np.where(f[k] >= 0, P.hi[k], P.lo[k]) for k in range(P.n)]
+    if getattr(P, "ball", False):
+        c = 0.5 * (P.lo[0] + P.hi[0])
+        e = 0.5 * (P.hi[0] - P.lo[0])
+        nrm = float(np.sqrt(((e * f[0]) ** 2).sum()))
+        x[0] = c + (e * e * f[0] / nrm if nrm > 0 else 0.0)
     z = [None] + [np.where(g[k] >= 0, 1.0, 0.0) for k in range(1, P.n)]
     return x, z
 

@@ -53,7 +53,7 @@ def dense_layers(net: list[dict]):
     return out
 
 
-def ibp(Ws: list, bs: list, lo0: np.ndarray, hi0: np.ndarray, splits=None):
+def ibp(Ws: list, bs: list, lo0: np.ndarray, hi0: np.ndarray, splits=None, ball=False):
     """Interval bound propagation (Gowal et al.; App. E of the paper, last paragraph).
 
     Ws, bs are the hidden layers' dense operators (k = 1..n-1). Returns (lhat, uhat, lo, hi) as
@@ -63,16 +63,27 @@ def ibp(Ws: list, bs: list, lo0: np.ndarray, hi0: np.ndarray, splits=None):
     splits (int8 over all hidden neurons, layer-major) clamps a neuron whose interval straddles
     zero: +1 (active) sets lhat = 0, -1 (inactive) sets uhat = 0, before the next layer is
     propagated. A split on a neuron that does not straddle zero changes nothing.
+
+    ball: the input set is the ellipsoid inscribed in the box, {x : sum_j ((x_j - c_j) / e_j)^2 <= 1}
+    with c = (lo0 + hi0) / 2 and e = (hi0 - lo0) / 2 (an l2 ball of radius e when the half-widths
+    are equal; Sec. 2 allows any input set with a closed-form linear minimisation). Layer 1's bounds
+    are then the exact range of W_1 x + b_1 over it: W_1 c + b_1 -+ |W_1 D|_2 row by row, D = diag(e).
     """
     lo = [np.asarray(lo0, np.float64)]
     hi = [np.asarray(hi0, np.float64)]
     lhat, uhat = [None], [None]
     off = 0
-    for W, b in zip(Ws, bs):
-        Wp = np.maximum(W, 0.0)
-        Wn = np.minimum(W, 0.0)
-        lh = Wp @ lo[-1] + Wn @ hi[-1] + b
-        uh = Wp @ hi[-1] + Wn @ lo[-1] + b
+    for k, (W, b) in enumerate(zip(Ws, bs)):
+        if ball and k == 0:
+            c = 0.5 * (lo[0] + hi[0])
+            r = np.sqrt(((W * (0.5 * (hi[0] - lo[0]))[None, :]) ** 2).sum(axis=1))
+            lh = W @ c + b - r
+            uh = W @ c + b + r
+        else:
+            Wp = np.maximum(W, 0.0)
+            Wn = np.minimum(W, 0.0)
+            lh = Wp @ lo[-1] + Wn @ hi[-1] + b
+            uh = Wp @ hi[-1] + Wn @ lo[-1] + b
         if splits is not None:
             sp = splits[off:off + W.shape[0]]
             amb = (lh < 0) & (uh > 0)
@@ -93,9 +104,10 @@ class Problem:
     scalar array of shape [1]); lhat/uhat[k] for k = 1..n-1; lo/hi[k] for k = 0..n-1.
     """
 
-    def __init__(self, net, lo0, hi0, crow, splits=None, bounds=None, dense=None):
+    def __init__(self, net, lo0, hi0, crow, splits=None, bounds=None, dense=None, ball=False):
         dense = dense if dense is not None else dense_layers(net)
         self.net = net
+        self.ball = ball   # x_0 in the ellipsoid inscribed in [lo0, hi0] (see ibp)
         self.taps = [None] + [d[2] for d in dense]
         self.W = [None] + [d[0] for d in dense[:-1]]
         self.b = [None] + [d[1] for d in dense[:-1]]
@@ -108,7 +120,7 @@ class Problem:
         self.widths = [len(lo0)] + [self.W[k].shape[0] for k in range(1, self.n)]
         if bounds is None:
             self.lhat, self.uhat, self.lo, self.hi = ibp(self.W[1:self.n], self.b[1:self.n],
-                                                         lo0, hi0, splits)
+                                                         lo0, hi0, splits, ball)
         else:
             lh, uh = bounds
             self.lhat = [None] + [np.asarray(v, np.float64) for v in lh]
@@ -124,12 +136,13 @@ class Problem:
 
 
 def problems(prob: dict, bounds=None, dense=None) -> list[Problem]:
-    """One Problem per subproblem of a synthetic problem dict."""
+    """One Problem per subproblem of a synthetic problem dict (prob["ball"]: ellipsoid inputs)."""
     dense = dense if dense is not None else dense_layers(prob["net"])
     out = []
     S = prob["lo"].shape[0]
     for s in range(S):
         sp = None if prob.get("splits") is None else prob["splits"][s]
         bd = None if bounds is None else bounds[s]
-        out.append(Problem(prob["net"], prob["lo"][s], prob["hi"][s], prob["C"][s], sp, bd, dense))
+        out.append(Problem(prob["net"], prob["lo"][s], prob["hi"][s], prob["C"][s], sp, bd, dense,
+                           bool(prob.get("ball", False))))
     return out

@@ -1,0 +1,125 @@
+"""Pins of the ellipsoid (l2-ball) input set in the oracle (Sec. 2: any input set with a closed-form
+linear minimisation): the exact range of layer 1, a closed-form minimum on an affine region,
+weak duality against sampled inputs, and the box LP below the ball's bound."""
+import numpy as np
+import pytest
+
+from oracle import active_set as AS
+from oracle import bab
+from oracle import dual as du
+from oracle import lp
+from oracle import network as nw
+from oracle import relaxation as rx
+from paper_2101_05844_gb300 import synth
+
+
+def _ellipsoid_points(lo, hi, n, seed):
+    """n points uniform in the ellipsoid inscribed in [lo, hi]."""
+    rng = synth.SplitMix64(seed)
+    d = lo.size
+    g = rng.normal(n * d).reshape(n, d)
+    g /= np.linalg.norm(g, axis=1, keepdims=True)
+    r = rng.uniform(n) ** (1.0 / d)
+    c, e = 0.5 * (lo + hi), 0.5 * (hi - lo)
+    return c[None, :] + e[None, :] * g * r[:, None]
+
+
+def _ball_prob(name, seed, S=1, scale=1.0, equal=False):
+    prob = synth.problem(name, S=S, seed=seed)
+    lo, hi = prob["lo"].astype(np.float64), prob["hi"].astype(np.float64)
+    c = 0.5 * (lo + hi)
+    e = 0.5 * (hi - lo) * scale
+    if not equal:   # unequal half-widths: an ellipsoid
+        e = e * (0.5 + synth.SplitMix64(seed + 7).uniform(e.size).reshape(e.shape))
+    return dict(prob, lo=(c - e).astype(np.float32), hi=(c + e).astype(np.float32), ball=True)
+
+
+def test_layer1_interval_is_the_exact_range_over_the_ellipsoid():
+    prob = _ball_prob("mlp_5_7_6_3", 1)
+    lo, hi = prob["lo"][0].astype(np.float64), prob["hi"][0].astype(np.float64)
+    W, b, _ = nw.dense_layers(prob["net"])[0]
+    lh, uh, _, _ = nw.ibp([W], [b], lo, hi, ball=True)
+    c, e = 0.5 * (lo + hi), 0.5 * (hi - lo)
+    for i in range(W.shape[0]):
+        d = e * e * W[i] / np.linalg.norm(e * W[i])
+        for x, v in ((c + d, uh[1][i]), (c - d, lh[1][i])):
+            assert np.sum(((x - c) / e) ** 2) == pytest.approx(1.0, abs=1e-12)   # on the surface
+            assert W[i] @ x + b[i] == pytest.approx(v, abs=1e-12)                  # attains the bound
+    X = _ellipsoid_points(lo, hi, 4000, 3)
+    A = X @ W.T + b[None, :]
+    assert np.all(A >= lh[1][None, :] - 1e-12) and np.all(A <= uh[1][None, :] + 1e-12)
+    box_l, box_u, _, _ = nw.ibp([W], [b], lo, hi)
+    assert np.all(lh[1] >= box_l[1] - 1e-12) and np.all(uh[1] <= box_u[1] + 1e-12)
+
+
+def test_interior_inputs_give_masks_equal_to_z():
+    """Eq. (3) at a binary z and inputs strictly inside their box: the bit is z (1 where W = 0)."""
+    rng = synth.SplitMix64(5)
+    W = rng.normal(6 * 5).reshape(6, 5)
+    W[0, 0] = 0.0
+    lo, hi = -np.ones(5), np.ones(5)
+    x = 0.9 * (rng.uniform(5) * 2 - 1)
+    z = (rng.uniform(6) < 0.5).astype(np.float64)
+    I = rx.mask(W, lo, hi, x, z)
+    np.testing.assert_array_equal(I, rx.mask_exact(W, lo, hi, x, z))
+    expect = np.repeat(z[:, None] > 0, 5, axis=1) | (W == 0)
+    np.testing.assert_array_equal(I, expect)
+
+
+def test_affine_region_reaches_the_closed_form_minimum():
+    """A small ellipsoid on which no neuron is ambiguous: f is affine there, f(x) = a . x + f0, and
+    its minimum is f(c) - |D a|_2. Converged Big-M duals reach it from below."""
+    prob = _ball_prob("mlp_4_3_3_1", 2, scale=0.05)
+    P = nw.problems(prob)[0]
+    for k in range(1, P.n):
+        assert not np.any((P.lhat[k] < 0) & (P.uhat[k] > 0))
+    dense = nw.dense_layers(prob["net"])
+    lo, hi = P.lo[0], P.hi[0]
+    c, e = 0.5 * (lo + hi), 0.5 * (hi - lo)
+    A = np.eye(lo.size)
+    a0 = np.zeros(lo.size)
+    h0 = c.copy()
+    for W, b, _ in dense[:-1]:   # the active pattern at the centre holds on the whole ellipsoid
+        act = (W @ h0 + b) > 0
+        A, a0, h0 = act[:, None] * (W @ A), act * (W @ a0 + b), np.maximum(W @ h0 + b, 0.0)
+    Wn, bn, _ = dense[-1]
+    a = prob["C"][0] @ Wn @ A
+    f_c = float(prob["C"][0] @ (Wn @ h0 + bn))
+    exact = f_c - float(np.linalg.norm(e * a))
+    X = _ellipsoid_points(lo, hi, 3000, 9)
+    vals = [float(prob["C"][0] @ bab.forward(dense, x)) for x in X]
+    assert min(vals) >= exact - 1e-12 and min(vals) <= exact + 0.05 * (max(vals) - min(vals))
+    _, best, _ = AS.solve(P, AS.Options(bigm_iters=3000))
+    assert exact - 1e-4 <= best <= exact + 1e-9
+
+
+@pytest.mark.parametrize("name,seed", [("mlp_5_7_6_3", 1), ("small_conv", 2)])
+def test_bounds_are_below_every_sampled_input(name, seed):
+    prob = _ball_prob(name, seed)
+    P = nw.problems(prob)[0]
+    s = AS.ActiveSet(P, AS.Options(bigm_iters=60, as_iters=60, omega=15, max_cuts=3)).step(120)
+    x0 = du.evaluate(P, s.st)[3][0]
+    c, e = 0.5 * (P.lo[0] + P.hi[0]), 0.5 * (P.hi[0] - P.lo[0])
+    assert np.sum(((x0 - c) / e) ** 2) == pytest.approx(1.0, abs=1e-9)   # x_0* on the surface
+    dense = nw.dense_layers(prob["net"])
+    X = _ellipsoid_points(P.lo[0], P.hi[0], 3000, seed)
+
+    m = min(float(prob["C"][0] @ bab.forward(dense, x)) for x in X)
+    assert s.best <= m + 1e-9
+    assert s.best >= P.ibp_output_bound() - 1e-9
+
+
+def test_ball_bound_is_above_the_box_lp():
+    """With equal half-widths the ball lies inside the box, so its relaxation lies inside the box's:
+    converged Big-M over the ball ends above the exact LP(M) over the box, and below the sampled
+    minimum over the ball."""
+    prob = _ball_prob("mlp_4_3_3_1", 3, equal=True)
+    P = nw.problems(prob)[0]
+    box = nw.problems(dict(prob, ball=False))[0]
+    v_box = float(lp.NetLP(box.W[1:box.n], box.b[1:box.n], box.lhat, box.uhat, box.lo, box.hi)
+                  .solve("M", box.W[box.n][0], box.b[box.n][0]))
+    _, best, _ = AS.solve(P, AS.Options(bigm_iters=2000))
+    assert best >= v_box - 1e-4
+    dense = nw.dense_layers(prob["net"])
+    X = _ellipsoid_points(P.lo[0], P.hi[0], 4000, 4)
+    assert best <= min(float(bab.forward(dense, x)[0]) for x in X) + 1e-9
