@@ -91,6 +91,14 @@ typedef struct as_options {
                           * recomputed in float32 after each addition; as_bound re-evaluates the
                           * bound in float32 with float64 summation). Saddle Point runs in
                           * float32 on any context.                                        */
+    int input_l2;        /* 1: the input set of each subproblem is the ellipsoid inscribed in its box,
+                          * {sum_j ((x_j - c_j) / e_j)^2 <= 1} with c, e the box's centre and half-widths
+                          * (an l2 ball of radius e for equal half-widths; Sec. 2 needs only a closed-form
+                          * linear minimisation over the input set): layer 1's interval bounds are its exact
+                          * range W c + b -+ |W D|_2 and x_0* = c + e^2 f_0 / |e f_0|_2. Big-M / Active Set in
+                          * float32 only (precision 16: AS_ERR_ARG; sp_step: AS_ERR_STATE), and
+                          * as_bound_backward gives dW, db only (dlo, dhi or the chain form: AS_ERR_STATE).
+                          * 0 (default): the box itself.                                        */
 } as_options;
 
 typedef struct as_ctx as_ctx;
@@ -291,7 +299,8 @@ int as_intermediate_bounds(const as_net* net, int S, const float* x_lo, const fl
  * relaxation whose solve has not converged) is solved again from its own duals up to
  * leaf_rebounds times, then set aside (the result is then "unknown" unless falsified).
  * Intermediate bounds of a domain: interval propagation with its split clamps, intersected with
- * the root's as_intermediate_bounds when root_intermediate is set. */
+ * the root's as_intermediate_bounds when root_intermediate is set. The input set is the box or,
+ * with input_l2 in loose and tight (which must agree: AS_ERR_ARG), its inscribed ellipsoid. */
 #define AS_BAB_UNKNOWN 0
 #define AS_BAB_VERIFIED 1
 #define AS_BAB_FALSIFIED 2

@@ -52,7 +52,7 @@ class Options(ct.Structure):
                 ("sp_gamma0", ct.c_double), ("sp_c_alpha", ct.c_double), ("sp_c_beta", ct.c_double),
                 ("sp_init_steps", ct.c_int), ("sp_init_lr0", ct.c_double), ("sp_init_lr1", ct.c_double),
                 ("track_best", ct.c_int), ("graph_chunk", ct.c_int), ("profile", ct.c_int),
-                ("autotune", ct.c_int), ("precision", ct.c_int)]
+                ("autotune", ct.c_int), ("precision", ct.c_int), ("input_l2", ct.c_int)]
 
 
 class BabOptions(ct.Structure):

@@ -358,6 +358,8 @@ extern "C" int as_bab(const as_net* net, const float* x_lo, const float* x_hi, c
     else as_bab_default_options(&b.o);
     if (b.o.batch < 2 || (b.o.batch & 1) || b.o.ema_weight < 0 || b.o.ema_weight > 1 || b.o.leaf_rebounds < 0)
         return AS_ERR_ARG;
+    if (b.o.loose.input_l2 != b.o.tight.input_l2) return AS_ERR_ARG;   // one input set for the search
+    b.o.intermediate.input_l2 = b.o.tight.input_l2;
     b.st = static_cast<cudaStream_t>(stream);
     const int n = net->n_layers;
     const as_layer& L0 = net->layers[0];

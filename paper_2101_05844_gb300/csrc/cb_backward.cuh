@@ -34,7 +34,7 @@ __device__ __forceinline__ float wgrad_term(const DNet& net, const DState& st, c
     float g = (st.alpha[h] - st.beta1[h]) * x;
     if (nsl) {
         const float lo = st.lo[xo], hi = st.hi[xo];
-        const unsigned I = cb_slot_mask(st.zsnap[bo][h], st.xsnap[bo][xo], lo == hi, w);
+        const unsigned I = cb_slot_mask(st.zsnap[bo][h], st.xsnap[bo][xo], lo == hi, w, net.ball && L.in_off == 0);
         const float z = st.zcur[h] ? 1.f : 0.f;
         const float Lc = w >= 0.f ? lo : hi, Uc = w >= 0.f ? hi : lo;
         const size_t hs = (size_t)s * net.cap * NH + L.h_out + i;
@@ -160,7 +160,7 @@ __global__ void k_grad_box(DNet net, DState st, GradCtx gc, float* dlo, float* d
         const size_t rb = (size_t)s * net.NH + L.h_out;
         const size_t sb = (size_t)s * net.cap * net.NH + L.h_out;
         col_walk(L, j, [&](int i, float w) {
-            const unsigned I = cb_slot_mask(st.zsnap[gc.bo][rb + i], xs, lo == hi, w);
+            const unsigned I = cb_slot_mask(st.zsnap[gc.bo][rb + i], xs, lo == hi, w, net.ball != 0);
             const float z = st.zcur[rb + i] ? 1.f : 0.f;
             float bsum_in = 0.f, bsum_out = 0.f;
             for (int b = 0; b < nsl; ++b) {
@@ -208,7 +208,7 @@ __global__ void k_post_adj(DNet net, DState st, int li, GradCtx gc, float* Lb, f
         const size_t rb = (size_t)s * net.NH + L.h_out;
         const size_t sb = (size_t)s * net.cap * net.NH + L.h_out;
         col_walk(L, j, [&](int i, float w) {
-            const unsigned I = cb_slot_mask(st.zsnap[gc.bo][rb + i], xs, lo == hi, w);
+            const unsigned I = cb_slot_mask(st.zsnap[gc.bo][rb + i], xs, lo == hi, w, net.ball && li == 0);
             const float z = st.zcur[rb + i] ? 1.f : 0.f;
             float bsum_in = 0.f, bsum_out = 0.f;
             for (int b = 0; b < nsl; ++b) {
@@ -325,7 +325,7 @@ __device__ __forceinline__ void slot_sums_body(const DNet& net, const DState& st
     for (int b = 0; b < CB_MAXCUT; ++b) lam[b] = mu[b] = 0.f;
     row_walk(L, i, lane, [&](int j, float w) {
         const float l = st.lo[ib + j], uu = st.hi[ib + j];
-        const unsigned I = cb_slot_mask(zs, st.xsnap[bo][ib + j], l == uu, w);
+        const unsigned I = cb_slot_mask(zs, st.xsnap[bo][ib + j], l == uu, w, net.ball && L.in_off == 0);
         const float Lc = w >= 0.f ? l : uu, Uc = w >= 0.f ? uu : l;
 #pragma unroll
         for (int b = 0; b < CB_MAXCUT; ++b)

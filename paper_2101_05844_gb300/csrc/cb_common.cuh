@@ -64,6 +64,8 @@ struct DNet {
     const float* Wout;     // [S][n_{n-1}] property-folded output row
     const float* bout;     // [S]
     const BfLayer* bf;     // [n - 1] device array, BF16 form only (else null)
+    int ball;              // 1: the input set is the ellipsoid inscribed in the box (l2 ball for equal
+                           // half-widths); 0: the box
 };
 
 // Solver schedule constants (float32 copies prepared on the host from the double options).

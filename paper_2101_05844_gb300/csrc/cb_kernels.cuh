@@ -19,9 +19,12 @@ namespace cb {
 // zs: bit b = z*_k[i] when slot b was added; xs: bit b = (x*_{k-1}[j] was at its upper bound).
 // With z = 1 the row is all ones; with z = 0 the bit is 1 where the coefficient
 // ((1-z) Lcheck + z Ucheck - x) W is >= 0: W > 0 and x at its lower bound, W < 0 and x at its
-// upper bound, W = 0, or l = u (fixed input, coefficient exactly 0).
-__device__ __forceinline__ unsigned cb_slot_mask(unsigned zs, unsigned xs, bool fixed, float w) {
-    unsigned xm = fixed ? 0xFFu : (w > 0.f ? (~xs & 0xFFu) : (w < 0.f ? xs : 0xFFu));
+// upper bound, W = 0, or l = u (fixed input, coefficient exactly 0). An input strictly inside its
+// box (interior: layer 0 over an ellipsoid) is at neither end: the bit is z, or 1 where W = 0 or l = u.
+__device__ __forceinline__ unsigned cb_slot_mask(unsigned zs, unsigned xs, bool fixed, float w,
+                                                 bool interior = false) {
+    unsigned xm = fixed ? 0xFFu
+                        : (w > 0.f ? (interior ? 0u : (~xs & 0xFFu)) : (w < 0.f ? (interior ? 0u : xs) : 0xFFu));
     return zs | xm;
 }
 
@@ -86,14 +89,24 @@ __global__ void k_ibp(DNet net, DState st, int li, const signed char* splits) {
     const float* lo = st.lo + (size_t)s * net.NT + L.in_off;
     const float* hi = st.hi + (size_t)s * net.NT + L.in_off;
     double a = 0.0, c = 0.0;
+    const bool ell = net.ball && li == 0;
     row_walk(L, i, lane, [&](int j, float w) {
         const double wd = w;
-        if (w >= 0.f) { a += wd * lo[j]; c += wd * hi[j]; }
+        if (ell) {   // centre product and the squared radius of W_i over the ellipsoid
+            const double e = 0.5 * ((double)hi[j] - (double)lo[j]);
+            a += wd * 0.5 * ((double)lo[j] + (double)hi[j]);
+            c += wd * wd * e * e;
+        } else if (w >= 0.f) { a += wd * lo[j]; c += wd * hi[j]; }
         else { a += wd * hi[j]; c += wd * lo[j]; }
     });
     a = warp_sum(a);
     c = warp_sum(c);
     if (lane == 0) {
+        if (ell) {   // the exact range of W_i x + b over {sum ((x - c) / e)^2 <= 1}: W_i c + b -+ |W_i D|
+            const double r = sqrt(c);
+            c = a + r;
+            a = a - r;
+        }
         a += (double)L.b[i];
         c += (double)L.b[i];
         const size_t h = (size_t)s * net.NH + L.h_out + i;
@@ -273,7 +286,7 @@ __global__ void __launch_bounds__(CB_THREADS) k_sp_convert_P(DNet net, DState st
     col_walk(L, j, [&](int i, float w) {
         float sb = b1[i];
         if (nsl) {
-            const unsigned I = cb_slot_mask(zs[i], xs, fixed, w);
+            const unsigned I = cb_slot_mask(zs[i], xs, fixed, w, net.ball && L.in_off == 0);
             for (int b = 0; b < nsl; ++b)
                 if ((I >> b) & 1u) sb += bsl[(size_t)b * NH + i];
         }

@@ -302,7 +302,9 @@ __device__ __forceinline__ void as_colA_body(const DNet& net, const DState& st, 
     const unsigned fxm = fixed ? 0xFFu : 0u;
     float f;
     if (k <= net.n - 1) {
-        const unsigned pm = ((~xs) & 0xFFu) | fxm, qm = xs | fxm;
+        // an interior input (layer 0 over an ellipsoid) is at neither end of its box: eq. (3) gives z
+        const bool interior = net.ball && L.in_off == 0;
+        const unsigned pm = (interior ? 0u : ((~xs) & 0xFFu)) | fxm, qm = (interior ? 0u : xs) | fxm;
         f = acc;
 #pragma unroll
         for (int b = 0; b < NS; ++b) {
@@ -386,6 +388,47 @@ __device__ __forceinline__ void as_colA_body(const DNet& net, const DState& st, 
             reinterpret_cast<float2*>(st.xin + (size_t)s * net.XT + L.xo)[xin_pos(L, j)] =
                 make_float2(xv, __uint_as_float(mpos | (mneg << 8)));
         }
+    }
+}
+
+// Ellipsoid input set {sum_j ((x_j - c_j) / e_j)^2 <= 1} inscribed in the box (c, e its centre and
+// half-widths; an l2 ball for equal half-widths), one block per subproblem, after the col pass has
+// written f_0: the x_0 part of the inner minimisation, min -f_0^T x_0, is attained at
+// x_0* = c + e^2 f_0 / |e f_0|_2 (c where f_0 = 0) with value -f_0^T c - |e f_0|_2 (Sec. 2 needs only
+// this closed form of the input set). Writes x_0*, the per-input bound terms of that value (-f c -
+// e^2 f^2 / |e f|, summing to it exactly whatever the rounding of x_0*), and the row-pass records:
+// x_0* lies strictly inside the box, so the mask bits of eq. (3) are z alone (cb_slot_mask,
+// interior) and the producer bits p_b, q_b are set only for fixed inputs.
+__global__ void __launch_bounds__(CB_THREADS) k_ball_x0(DNet net, DState st) {
+    const int s = blockIdx.x;
+    const DLayer& L = net.L[0];
+    const size_t base = (size_t)s * net.NT + L.in_off;
+    double acc = 0.0;
+    for (int j = threadIdx.x; j < L.n_in; j += blockDim.x) {
+        const double e = 0.5 * ((double)st.hi[base + j] - (double)st.lo[base + j]);
+        const double f = st.fval[base + j];
+        acc += e * e * f * f;
+    }
+    __shared__ double red[CB_THREADS];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int h = CB_THREADS / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    const double nrm = sqrt(red[0]);
+    float2* rec = reinterpret_cast<float2*>(st.xin + (size_t)s * net.XT + L.xo);
+    for (int j = threadIdx.x; j < L.n_in; j += blockDim.x) {
+        const size_t xo = base + j;
+        const float lo = st.lo[xo], hi = st.hi[xo];
+        const double c = 0.5 * ((double)lo + (double)hi), e = 0.5 * ((double)hi - (double)lo);
+        const double f = st.fval[xo];
+        const double d = nrm > 0.0 ? e * e * f / nrm : 0.0;
+        const float xv = fminf(fmaxf((float)(c + d), lo), hi);
+        st.xval[xo] = xv;
+        st.terms[xo] = -f * c - f * d;
+        const unsigned fxm = st.efix[xo] ? 0xFFu : 0u;
+        rec[xin_pos(L, j)] = make_float2(xv, __uint_as_float(fxm | (fxm << 8)));
     }
 }
 

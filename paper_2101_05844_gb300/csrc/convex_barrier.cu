@@ -137,6 +137,7 @@ extern "C" void as_default_options(as_options* o) {
     o->track_best = 0;
     o->graph_chunk = 16;
     o->precision = 32;
+    o->input_l2 = 0;
 }
 
 extern "C" const char* as_last_error(as_ctx* c) { return c ? c->err.c_str() : "null context"; }
@@ -219,6 +220,8 @@ static int validate_opt(as_ctx* c, const as_options& o) {
     if (!(o.sp_c_alpha > 0 && o.sp_c_beta > 0)) return fail(c, AS_ERR_ARG, "price-cap constants must be > 0");
     if (o.sp_init_steps < 0 || o.graph_chunk < 0) return fail(c, AS_ERR_ARG, "negative step counts");
     if (o.precision != 32 && o.precision != 16) return fail(c, AS_ERR_ARG, "precision must be 32 or 16");
+    if (o.input_l2 != 0 && o.input_l2 != 1) return fail(c, AS_ERR_ARG, "input_l2 must be 0 or 1");
+    if (o.input_l2 && o.precision == 16) return fail(c, AS_ERR_ARG, "the ellipsoid input set runs in float32 only");
     return AS_OK;
 }
 
@@ -702,6 +705,7 @@ static int init_impl(as_ctx* c, const as_net* net, int S, const float* x_lo, con
     DNet& D = c->net;
     D.n = n;
     D.S = S;
+    D.ball = c->opt.input_l2;
     D.cap = std::max(1, c->opt.max_cuts);
     D.RS = ((1 + D.cap) + 3) / 4 * 4;
     int NT = 0;
@@ -860,9 +864,15 @@ static int launch_as_iter(as_ctx* c, cudaStream_t s) {
     // the per-neuron bound terms are only summed when the best bound is tracked
     const int mode = c->opt.track_best ? 0 : 2;
     LAUNCH(c, s, CB_K_AS_COLA, (k_as_colA_t<<<c->blocksTA, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->tA, mode, 0)));
+    if (c->net.ball) LAUNCH(c, s, CB_K_AS_COLA, (k_ball_x0<<<c->net.S, CB_THREADS, 0, s>>>(c->net, c->st)));
     if (c->opt.track_best)
         LAUNCH(c, s, CB_K_REDUCE, (k_reduce<<<c->net.S, CB_THREADS, 0, s>>>(c->net, c->st, 64, nullptr, 1)));
     LAUNCH(c, s, CB_K_AS_ROWB, (k_as_rowB_t<<<c->blocksTB, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->tB, 0)));
+    // an interior x_0* breaks the row pass's kappa = W x* + b of a new slot's z = 0 rows (it holds at
+    // box vertices only; kappa is multiplied by z = 0 in that iteration): recompute it in float32
+    if (c->net.ball)
+        LAUNCH(c, s, CB_K_SLOT_SUMS,
+               (k_slot_sums_after_add<<<c->blocksB, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->segB)));
     return check_launch(c, "Active Set iteration");
 }
 
@@ -958,6 +968,7 @@ static int sp_start(as_ctx* c) {
 
 extern "C" int sp_step(as_ctx* c, int n_iters) {
     if (!c) return AS_ERR_ARG;
+    if (c->net.ball) return fail(c, AS_ERR_STATE, "Saddle Point runs over box inputs only");
     if (n_iters < 0) return fail(c, AS_ERR_ARG, "n_iters < 0");
     if (!c->sp_started) TRY(sp_start(c));
     if (n_iters == 0) return AS_OK;
@@ -980,6 +991,7 @@ extern "C" int as_bound(as_ctx* c, int precision, double* out, double* best) {
         // the BF16 form's iterates give a bound through float32 lambda, kappa and records
         if (c->opt.precision == 16) TRY(recompute_slot_sums(c));
         LAUNCH(c, s, CB_K_AS_COLA, (k_as_colA_t<<<c->blocksTA, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->tA, 1, 0)));
+        if (c->net.ball) LAUNCH(c, s, CB_K_AS_COLA, (k_ball_x0<<<S, CB_THREADS, 0, s>>>(c->net, c->st)));
     }
     double* dout = c->bound_out;
     LAUNCH(c, s, CB_K_REDUCE, (k_reduce<<<S, CB_THREADS, 0, s>>>(c->net, c->st, precision, dout, 1)));

@@ -130,6 +130,7 @@ extern "C" int as_intermediate_bounds(const as_net* net, int S, const float* x_l
         as_ctx* c = nullptr;
         as_options oi;
         as_default_options(&oi);
+        oi.input_l2 = o.input_l2;   // the same input set as the solves
         const int nout = net->layers[n - 1].out_c;
         std::vector<float> C1;
         if (nout != 1) {   // any property row serves: only the interval bounds are read

@@ -33,11 +33,13 @@ def split_hidden(vec, widths):
     return out
 
 
-def draw_state(Ps, ctx, opt_kw, it, nslots, seed, scale=0.3, adam=True, subset=None):
+def draw_state(Ps, ctx, opt_kw, it, nslots, seed, scale=0.3, adam=True, subset=None, interior0=False):
     """Draw a state at global iteration `it` with `nslots` filled slots; install it on both sides.
 
     Returns the oracle ActiveSet solvers: a list over all subproblems, or a dict over `subset`
-    (the oracle side is then built for those subproblems only)."""
+    (the oracle side is then built for those subproblems only). interior0: the inputs (layer 0)
+    were strictly inside their box when each slot was added (an ellipsoid input set), so layer 1's
+    masks are the oracle's eq. (3) at an interior point, whatever the drawn snapshot bits."""
     rng = SplitMix64(seed)
     S, NH, NT, cap = ctx.S, ctx.NH, ctx.NT, ctx.cap
     widths = ctx.widths
@@ -88,6 +90,8 @@ def draw_state(Ps, ctx, opt_kw, it, nslots, seed, scale=0.3, adam=True, subset=N
             for k in range(1, P.n):
                 xprev_bits = xs_bits[s, offs[k - 1]:offs[k], b]
                 xprev = np.where(xprev_bits, P.hi[k - 1], P.lo[k - 1])
+                if interior0 and k == 1:
+                    xprev = 0.5 * (P.lo[0] + P.hi[0])
                 zk = zs_bits[s, offs[k] - widths[0]:offs[k + 1] - widths[0], b].astype(np.float64)
                 I = rx.mask(P.W[k], P.lo[k - 1], P.hi[k - 1], xprev, zk)
                 hk = slice(offs[k] - widths[0], offs[k + 1] - widths[0])

@@ -1,0 +1,212 @@
+"""Parity of the ellipsoid (l2-ball) input set, as_options.input_l2, with the oracle.
+
+Tolerances as for the box (tests/test_gpu_parity.py): interval bounds contain the FP64 ones and are
+within 4e-6 (1 + |v|); one-iteration lockstep of the duals 1e-5 relative where the update direction
+is decided; bounds 1e-4 absolute / 1e-5 relative. x_0* is no longer a box vertex: it is compared
+to 1e-5 relative (float32 f_0 against FP64), the hidden layers' x*, z* exactly.
+"""
+import numpy as np
+import pytest
+
+from oracle import active_set as AS
+from oracle import bab
+from oracle import dual as du
+from oracle import envelope as ev
+from oracle import network as nw
+from oracle import relaxation as rx
+from paper_2101_05844_gb300 import binding, synth
+from tests.state_helpers import draw_state, hidden_concat, oracle_bounds_f32, split_hidden
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    assert torch.cuda.is_available()
+    binding.lib()
+
+
+def _ball(name, S, seed=0, equal=False):
+    prob = synth.problem(name, S=S, seed=seed)
+    lo, hi = prob["lo"].astype(np.float64), prob["hi"].astype(np.float64)
+    c, e = 0.5 * (lo + hi), 0.5 * (hi - lo)
+    if not equal:
+        e = e * (0.5 + synth.SplitMix64(seed + 7).uniform(e.size).reshape(e.shape))
+    return dict(prob, lo=(c - e).astype(np.float32), hi=(c + e).astype(np.float32), ball=True)
+
+
+def _opts(**kw):
+    return binding.default_options(graph_chunk=0, input_l2=1, **kw)
+
+
+@pytest.mark.parametrize("name,S", [("mlp_5_7_6_3", 3), ("small_conv", 2)])
+def test_interval_bounds_over_the_ellipsoid(name, S):
+    prob = _ball(name, S)
+    ctx = binding.context_for(prob, _opts())
+    lh = ctx.get_state(binding.ST_LHAT).reshape(S, -1)
+    uh = ctx.get_state(binding.ST_UHAT).reshape(S, -1)
+    for s, P in enumerate(nw.problems(prob)):
+        rl, ru = hidden_concat(P.lhat), hidden_concat(P.uhat)
+        assert np.all(lh[s] <= rl) and np.all(uh[s] >= ru)
+        np.testing.assert_allclose(lh[s], rl, rtol=0, atol=4e-6 * (1 + np.abs(rl)).max())
+        np.testing.assert_allclose(uh[s], ru, rtol=0, atol=4e-6 * (1 + np.abs(ru)).max())
+    box = binding.context_for(dict(prob, ball=False), binding.default_options(graph_chunk=0))
+    assert np.all(lh >= box.get_state(binding.ST_LHAT).reshape(S, -1))
+
+
+CASES = [
+    ("mlp_tiny", 1, dict(bigm_iters=5, as_iters=40, omega=3, max_cuts=5), 3, 0),     # Big-M
+    ("mlp_tiny", 1, dict(bigm_iters=5, as_iters=40, omega=3, max_cuts=5), 8, 2),     # adds slot 2
+    ("small_conv", 3, dict(bigm_iters=5, as_iters=40, omega=3, max_cuts=5), 12, 4),  # adds slot 4
+    ("mlp_5_7_6_3", 4, dict(bigm_iters=2, as_iters=30, omega=4, max_cuts=8), 16, 6),  # adds slot 6
+]
+
+
+@pytest.mark.parametrize("name,S,kw,it,nslots", CASES)
+def test_one_iteration_lockstep(name, S, kw, it, nslots):
+    prob = _ball(name, S)
+    Ps0 = nw.problems(prob)
+    lh, uh = oracle_bounds_f32(Ps0)
+    Ps = nw.problems(prob, bounds=[(split_hidden(lh[s].astype(np.float64), Ps0[0].widths)[1:],
+                                    split_hidden(uh[s].astype(np.float64), Ps0[0].widths)[1:])
+                                   for s in range(S)])
+    ctx = binding.context_for(prob, _opts(**kw), bounds=(lh, uh))
+    solvers = draw_state(Ps, ctx, kw, it, nslots, seed=200 + it, interior0=True)
+    gb = ctx.bound()
+    for s, sv in enumerate(solvers):
+        assert gb[s] == pytest.approx(du.evaluate(sv.P, sv.st)[0], abs=1e-4, rel=1e-5)
+    ctx.as_step(1)
+    xstar = ctx.get_state(binding.ST_XSTAR).reshape(S, -1)
+    zstar = ctx.get_state(binding.ST_ZSTAR, np.uint8).reshape(S, -1)
+    al = ctx.get_state(binding.ST_ALPHA).reshape(S, -1)
+    b0 = ctx.get_state(binding.ST_BETA0).reshape(S, -1)
+    b1 = ctx.get_state(binding.ST_BETA1).reshape(S, -1)
+    sb = ctx.get_state(binding.ST_SLOT_BETA).reshape(S, ctx.cap, -1)
+    lam = ctx.get_state(binding.ST_LAMBDA).reshape(S, ctx.cap, -1)
+    kap = ctx.get_state(binding.ST_KAPPA).reshape(S, ctx.cap, -1)
+    n0 = Ps[0].widths[0]
+    for s, sv in enumerate(solvers):
+        P = sv.P
+        _, f, g, x, z = du.evaluate(P, sv.st)
+        grads = du.supergradient(P, sv.st, x, z)
+        before = len(sv.st.slots[1])
+        sv.step(1)
+        np.testing.assert_allclose(xstar[s, :n0], x[0], rtol=1e-5, atol=1e-6)
+        np.testing.assert_array_equal(xstar[s, n0:], np.concatenate([x[k] for k in range(1, P.n)]).astype(np.float32))
+        np.testing.assert_array_equal(zstar[s], hidden_concat(z).astype(np.uint8))
+        if len(sv.st.slots[1]) > before:   # the new slot's lambda, kappa (float32 recompute)
+            b = before
+            ref_l = hidden_concat([None] + [sv.st.slots[k][b].lam for k in range(1, P.n)])
+            ref_k = hidden_concat([None] + [sv.st.slots[k][b].lam + sv.st.slots[k][b].mu + P.b[k]
+                                            for k in range(1, P.n)])
+            np.testing.assert_allclose(lam[s, b], ref_l, rtol=1e-5, atol=1e-5)
+            np.testing.assert_allclose(kap[s, b], ref_k, rtol=1e-5, atol=1e-5)
+            I1 = sv.st.slots[1][b].I   # interior x_0*: the layer-1 mask is z (or 1 where W = 0)
+            np.testing.assert_array_equal(I1, (z[1][:, None] > 0) | (P.W[1] == 0) | (P.lo[0] == P.hi[0])[None, :])
+
+        def check(gpu, ref, gref):
+            decided = (np.abs(gref) > 1e-4) | (gref == 0)
+            np.testing.assert_allclose(gpu[decided], ref[decided], rtol=1e-5, atol=1e-7)
+            assert (gpu >= 0).all() and decided.mean() > 0.9
+        check(al[s], hidden_concat(sv.st.alpha), hidden_concat(grads["galpha"]))
+        check(b0[s], hidden_concat(sv.st.beta0), hidden_concat(grads["gbeta0"]))
+        check(b1[s], hidden_concat(sv.st.beta1), hidden_concat(grads["gbeta1"]))
+        for b in range(before):
+            check(sb[s, b], hidden_concat([None] + [sv.st.slots[k][b].beta for k in range(1, P.n)]),
+                  hidden_concat([None] + [grads["gslots"][k][b] for k in range(1, P.n)]))
+
+
+def _as_margin(sv):
+    _, f, g, x, z = du.evaluate(sv.P, sv.st)
+    m = min(np.abs(fk).min() for fk in f[1:]) if len(f) > 1 else np.inf
+    for gk in g[1:]:
+        nz = gk[gk != 0]
+        if nz.size:
+            m = min(m, np.abs(nz).min())
+    return m
+
+
+@pytest.mark.parametrize("name,S,kw,iters", [
+    ("mlp_tiny", 1, dict(bigm_iters=20, as_iters=80, omega=24, max_cuts=5), 100),
+    ("mlp_5_7_6_3", 4, dict(bigm_iters=30, as_iters=60, omega=20, max_cuts=4), 90),
+    ("small_conv", 3, dict(bigm_iters=20, as_iters=40, omega=12, max_cuts=5), 60),
+])
+def test_free_running_active_set_matches_oracle(name, S, kw, iters):
+    """Iteration by iteration from zero duals: bounds within 1e-4 until the oracle takes a decision
+    within 1e-3 of a tie (then both runs go on as different valid runs); every bound lies below
+    the sampled minimum over the ellipsoid."""
+    prob = _ball(name, S)
+    Ps0 = nw.problems(prob)
+    lh, uh = oracle_bounds_f32(Ps0)
+    Ps = nw.problems(prob, bounds=[(split_hidden(lh[s].astype(np.float64), Ps0[0].widths)[1:],
+                                    split_hidden(uh[s].astype(np.float64), Ps0[0].widths)[1:])
+                                   for s in range(S)])
+    ctx = binding.context_for(prob, _opts(track_best=1, **kw), bounds=(lh, uh))
+    sol = [AS.ActiveSet(P, AS.Options(**kw)) for P in Ps]
+    live = [True] * S
+    for it in range(iters):
+        margins = [_as_margin(sv) for sv in sol]
+        ctx.as_step(1)
+        gb = ctx.bound()
+        for s, sv in enumerate(sol):
+            if not live[s]:
+                continue
+            sv.step(1)
+            if abs(gb[s] - du.evaluate(sv.P, sv.st)[0]) > 1e-4:
+                assert margins[s] < 1e-3, f"divergence at iteration {it} without a near-tie"
+                assert it >= 10
+                live[s] = False
+    b, best = ctx.bound(best=True)
+    dense = nw.dense_layers(prob["net"])
+    rng = synth.SplitMix64(4)
+    for s, P in enumerate(Ps):
+        lo, hi = P.lo[0], P.hi[0]
+        c, e = 0.5 * (lo + hi), 0.5 * (hi - lo)
+        g = rng.normal(2000 * lo.size).reshape(2000, lo.size)
+        g /= np.linalg.norm(g, axis=1, keepdims=True)
+        X = c + e * g * (rng.uniform(2000) ** (1.0 / lo.size))[:, None]
+        m = min(float(prob["C"][s] @ bab.forward(dense, x)) for x in X)
+        assert best[s] <= m + 1e-5
+
+
+def test_backward_gives_dW_db_and_refuses_the_box_gradients():
+    name, S = "mlp_5_7_6_3", 3
+    prob = _ball(name, S)
+    Ps0 = nw.problems(prob)
+    lh, uh = oracle_bounds_f32(Ps0)
+    Ps = nw.problems(prob, bounds=[(split_hidden(lh[s].astype(np.float64), Ps0[0].widths)[1:],
+                                    split_hidden(uh[s].astype(np.float64), Ps0[0].widths)[1:])
+                                   for s in range(S)])
+    kw = dict(bigm_iters=2, as_iters=30, omega=3, max_cuts=4)
+    ctx = binding.context_for(prob, _opts(**kw), bounds=(lh, uh))
+    solvers = draw_state(Ps, ctx, kw, it=9, nslots=4, seed=7, interior0=True)
+    gb = synth.SplitMix64(3).uniform(S) + 0.5
+    net = prob["net"]
+    dW = [np.zeros_like(L["W"]) for L in net]
+    db = [np.zeros_like(L["b"]) for L in net]
+    ctx.backward(gb, dW, db)
+    refW = [np.zeros(L["W"].shape) for L in net]
+    refb = [np.zeros(L["b"].shape) for L in net]
+    for s, sv in enumerate(solvers):
+        g = ev.envelope_gradient(sv.P, sv.st)
+        for k in range(1, len(net)):
+            refW[k - 1] += gb[s] * g["dW"][k]
+            refb[k - 1] += gb[s] * g["db"][k]
+        refW[-1] += gb[s] * np.outer(prob["C"][s], g["dW"][sv.P.n][0])
+        refb[-1] += gb[s] * prob["C"][s]
+    for k in range(len(net)):
+        np.testing.assert_allclose(dW[k], refW[k], rtol=1e-4, atol=1e-5)
+        np.testing.assert_allclose(db[k], refb[k], rtol=1e-4, atol=1e-5)
+    with pytest.raises(binding.CBError):
+        ctx.backward(gb, dW, db, np.zeros_like(prob["lo"]), None)
+
+
+def test_unsupported_combinations_are_refused():
+    prob = _ball("mlp_tiny", 1)
+    ctx = binding.context_for(prob, _opts(bigm_iters=5, as_iters=5))
+    ctx.as_step(3)
+    with pytest.raises(binding.CBError):
+        ctx.sp_step(1)
+    with pytest.raises(binding.CBError):
+        binding.context_for(prob, _opts(precision=16))
