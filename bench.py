@@ -489,6 +489,38 @@ def bab_run(binding, torch, dev, stream, rank, time_limit):
             "seconds": secs, "properties": rows}
 
 
+def l2_run(binding, torch, dev, stream, rank):
+    """The headline's Active Set schedule on the wide conv net's 9 properties with the input set the
+    l2 ball inscribed in the box (radius eps, as_options.input_l2), timed after a warm-up run,
+    beside the same run over the box: subproblem-iterations/s and the final bounds."""
+    import numpy as np
+    from paper_2101_05844_gb300 import synth
+    prob = synth.problem("wide_conv", seed=rank)
+    S = prob["lo"].shape[0]
+    iters = AS_BIGM + AS_ITERS
+    out = {}
+    for tag, l2 in (("l2_ball", 1), ("box", 0)):
+        opt = binding.default_options(bigm_iters=AS_BIGM, as_iters=AS_ITERS, omega=round(0.3 * AS_ITERS),
+                                      max_cuts=5, graph_chunk=25, autotune=1, input_l2=l2)
+        ctx = binding.Context(prob["net"], prob["lo"], prob["hi"], prob["C"], options=opt, stream=stream)
+        ctx.as_step(iters)
+        ctx.reset(prob["lo"], prob["hi"], prob["C"])
+        torch.cuda.synchronize()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        e[0].record()
+        ctx.as_step(iters)
+        e[1].record()
+        e[1].synchronize()
+        ms = e[0].elapsed_time(e[1])
+        b = ctx.bound()
+        ctx.close()
+        out[tag] = {"value": S * iters / (ms / 1e3), "ms": ms, "mean_final_bound": float(np.mean(b)),
+                    "final_bounds": [float(v) for v in b]}
+    return {"workload": {"net": "wide_conv 3x32x32 conv16-conv32-FC100-FC10", "subproblems": S,
+                         "iterations": iters, "input_set": "l2 ball of radius 2/255 inscribed in the l_inf box"},
+            "unit": UNIT, **out}
+
+
 def captured_traffic(workload, kernel):
     """DRAM bytes per launch of `kernel` from the committed ncu capture of this workload, or None
     when there is none or the kernel source has changed since it was taken."""
@@ -594,6 +626,8 @@ def main():
     ap.add_argument("--bab", action="store_true",
                     help="also run branch and bound with stratified bounding on the wide conv net's 9 properties")
     ap.add_argument("--bab-time", type=float, default=10.0, help="time limit per property of --bab (seconds)")
+    ap.add_argument("--l2", action="store_true",
+                    help="also time the headline Active Set schedule over the l2 ball inscribed in each box")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)
@@ -726,6 +760,8 @@ def main():
         line["batched"] = batched_run(binding, torch, dev, stream, rank)
     if args.differentiation:
         line["differentiation"] = differentiation_run(binding, torch, dev, stream, rank)
+    if args.l2:
+        line["l2"] = l2_run(binding, torch, dev, stream, rank)
     if args.bab:
         line["bab"] = bab_run(binding, torch, dev, stream, rank, args.bab_time)
     if args.intermediate:

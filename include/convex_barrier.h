@@ -222,7 +222,8 @@ long long as_launch_count(as_ctx* ctx);
 #define AS_K_TC_COL 8  /* BF16 form: tensor-core products of the col pass              */
 #define AS_K_TC_ROW 9  /* BF16 form: tensor-core products of the row pass              */
 #define AS_K_SLOT_SUMS 10 /* BF16 form: float32 lambda, kappa after an addition        */
-#define AS_K_COUNT 11
+#define AS_K_BALL_X0 11   /* ellipsoid input set: x_0*, its bound terms and records       */
+#define AS_K_COUNT 12
 
 /* With as_options.profile set: total device time (CUDA events on the context's stream) and
  * launch count of one kernel over the context's life so far. Synchronises the stream. */

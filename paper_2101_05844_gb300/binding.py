@@ -29,7 +29,7 @@ EXPORTS = ["as_default_options", "as_init", "as_reset", "as_step", "sp_step", "a
            "as_kernel_times", "as_destroy", "as_last_error", "as_ibp_noalloc", "as_gemm_bf16",
            "as_team_targets", "as_intermediate_bounds", "as_bab", "as_bab_default_options", "as_bound_backward_ibp"]
 KERNELS = ["as_colA", "as_rowB", "reduce", "sp_colA", "sp_rowB", "sp_colC", "spi_row", "spi_col", "tc_col",
-           "tc_row", "slot_sums"]
+           "tc_row", "slot_sums", "ball_x0"]
 
 
 class Layer(ct.Structure):

@@ -10,7 +10,8 @@
 
 // Kernel ids for per-kernel timing (as_kernel_times).
 enum { CB_K_AS_COLA = 0, CB_K_AS_ROWB, CB_K_REDUCE, CB_K_SP_COLA, CB_K_SP_ROWB, CB_K_SP_COLC,
-       CB_K_SPI_ROW, CB_K_SPI_COL, CB_K_TC_COL, CB_K_TC_ROW, CB_K_SLOT_SUMS, CB_NPROF };
+       CB_K_SPI_ROW, CB_K_SPI_COL, CB_K_TC_COL, CB_K_TC_ROW, CB_K_SLOT_SUMS, CB_K_BALL_X0,
+       CB_NPROF };
 
 // One affine layer k (1-based in the paper; stored at index k-1).
 struct DLayer {
@@ -92,6 +93,9 @@ struct DState {
     float *xin;                      // [S][XT] input records of each layer, one float2 per position:
                                      // {x*, p_b bits | q_b bits << 8}
     float *lz;                       // [S][NH] sum_j W_ij Lcheck_ij (the all-ones mask's lambda)
+    float *uz;                       // [S][NH] sum_j W_ij Ucheck_ij (kappa - b of a z = 0 row whose
+                                     // inputs are all interior: the mask is then empty but for
+                                     // fixed inputs, where Lcheck = Ucheck)
     uint8_t* efix;                   // [S][NT] l == u
     float *xval;                     // x* of the last evaluation [S][NT]
     float *fval;                     // f of the last evaluation [S][NT]

@@ -395,38 +395,53 @@ __device__ __forceinline__ void as_colA_body(const DNet& net, const DState& st, 
 // half-widths; an l2 ball for equal half-widths), one block per subproblem, after the col pass has
 // written f_0: the x_0 part of the inner minimisation, min -f_0^T x_0, is attained at
 // x_0* = c + e^2 f_0 / |e f_0|_2 (c where f_0 = 0) with value -f_0^T c - |e f_0|_2 (Sec. 2 needs only
-// this closed form of the input set). Writes x_0*, the per-input bound terms of that value (-f c -
-// e^2 f^2 / |e f|, summing to it exactly whatever the rounding of x_0*), and the row-pass records:
+// this closed form of the input set). Writes x_0*, that value as the layer's bound term (the
+// closed form, not -f_0^T x_0* at a rounded x_0*), and the row-pass records:
 // x_0* lies strictly inside the box, so the mask bits of eq. (3) are z alone (cb_slot_mask,
 // interior) and the producer bits p_b, q_b are set only for fixed inputs.
-__global__ void __launch_bounds__(CB_THREADS) k_ball_x0(DNet net, DState st) {
+constexpr int CB_BALL_THREADS = 1024;
+__global__ void __launch_bounds__(CB_BALL_THREADS) k_ball_x0(DNet net, DState st) {
+    // float32 per input (the float64 pipe is narrow); the two sums cross threads in float64, and
+    // the layer's whole bound term, -f c - |e f|, goes to its first input (the others hold 0)
     const int s = blockIdx.x;
     const DLayer& L = net.L[0];
     const size_t base = (size_t)s * net.NT + L.in_off;
-    double acc = 0.0;
-    for (int j = threadIdx.x; j < L.n_in; j += blockDim.x) {
-        const double e = 0.5 * ((double)st.hi[base + j] - (double)st.lo[base + j]);
-        const double f = st.fval[base + j];
-        acc += e * e * f * f;
+    float p2 = 0.f, pc = 0.f;
+    for (int j = threadIdx.x; j < L.n_in; j += CB_BALL_THREADS) {
+        const float lo = st.lo[base + j], hi = st.hi[base + j], f = st.fval[base + j];
+        const float ef = 0.5f * (hi - lo) * f;
+        p2 = fmaf(ef, ef, p2);
+        pc = fmaf(f, 0.5f * (lo + hi), pc);
     }
-    __shared__ double red[CB_THREADS];
-    red[threadIdx.x] = acc;
+    __shared__ double red[2][CB_BALL_THREADS / 32];
+    const double a2 = warp_sum((double)p2), ac = warp_sum((double)pc);
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = a2;
+        red[1][threadIdx.x >> 5] = ac;
+    }
     __syncthreads();
-    for (int h = CB_THREADS / 2; h > 0; h >>= 1) {
-        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
-        __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < CB_BALL_THREADS / 32 ? red[0][threadIdx.x] : 0.0;
+        double w = threadIdx.x < CB_BALL_THREADS / 32 ? red[1][threadIdx.x] : 0.0;
+        v = warp_sum(v);
+        w = warp_sum(w);
+        if (threadIdx.x == 0) {
+            red[0][0] = v;
+            red[1][0] = w;
+        }
     }
-    const double nrm = sqrt(red[0]);
+    __syncthreads();
+    const double nrm = sqrt(red[0][0]);
+    const float inv = nrm > 0.0 ? (float)(1.0 / nrm) : 0.f;
+    if (threadIdx.x == 0) st.terms[base] = -red[1][0] - nrm;
     float2* rec = reinterpret_cast<float2*>(st.xin + (size_t)s * net.XT + L.xo);
-    for (int j = threadIdx.x; j < L.n_in; j += blockDim.x) {
+    for (int j = threadIdx.x; j < L.n_in; j += CB_BALL_THREADS) {
         const size_t xo = base + j;
         const float lo = st.lo[xo], hi = st.hi[xo];
-        const double c = 0.5 * ((double)lo + (double)hi), e = 0.5 * ((double)hi - (double)lo);
-        const double f = st.fval[xo];
-        const double d = nrm > 0.0 ? e * e * f / nrm : 0.0;
-        const float xv = fminf(fmaxf((float)(c + d), lo), hi);
+        const float c = 0.5f * (lo + hi), e = 0.5f * (hi - lo);
+        const float xv = fminf(fmaxf(c + e * e * st.fval[xo] * inv, lo), hi);
         st.xval[xo] = xv;
-        st.terms[xo] = -f * c - f * d;
+        if (j) st.terms[xo] = 0.0;
         const unsigned fxm = st.efix[xo] ? 0xFFu : 0u;
         rec[xin_pos(L, j)] = make_float2(xv, __uint_as_float(fxm | (fxm << 8)));
     }
@@ -637,7 +652,9 @@ __device__ __forceinline__ void as_rowB_body(const DNet& net, const DState& st, 
                     if (ADD && b == newb) {
                         const float lzh = st.lz[h];
                         lam = zb ? lzh : acc[b];
-                        kap = zb ? lzh + bi : xhat;
+                        // kappa = lambda + sum W (1 - I) Ucheck + b: W x* + b at box vertices; over
+                        // interior inputs (layer 0, ellipsoid) the z = 0 mask holds fixed inputs only
+                        kap = zb ? lzh + bi : (net.ball && L.in_off == 0 ? st.uz[h] + bi : xhat);
                         st.lam[hs] = lam;
                         st.kap[hs] = kap;
                     }
@@ -679,7 +696,7 @@ __device__ __forceinline__ void as_rowB_body(const DNet& net, const DState& st, 
                 if (ADD && b == newb) {
                     const float lzh = st.lz[h];
                     lam = zb ? lzh : ab;
-                    kap = zb ? lzh + bi : xhat;
+                    kap = zb ? lzh + bi : (net.ball && L.in_off == 0 ? st.uz[h] + bi : xhat);
                     st.lam[hs] = lam;
                     st.kap[hs] = kap;
                 } else {
@@ -818,16 +835,19 @@ __global__ void k_lz(DNet net, DState st, int li) {
     const int s = warp / L.n_out, i = warp - s * L.n_out;
     const float* lo = st.lo + (size_t)s * net.NT + L.in_off;
     const float* hi = st.hi + (size_t)s * net.NT + L.in_off;
-    double a = 0.0;
+    double a = 0.0, c = 0.0;
     int nf = 0;
     row_walk(L, i, lane, [&](int j, float w) {
         a += (double)w * (w >= 0.f ? lo[j] : hi[j]);
+        c += (double)w * (w >= 0.f ? hi[j] : lo[j]);
         nf += (w != 0.f && lo[j] != hi[j]) ? 1 : 0;
     });
     a = warp_sum(a);
+    c = warp_sum(c);
     for (int o = 16; o > 0; o >>= 1) nf += __shfl_xor_sync(0xffffffffu, nf, o);
     if (lane == 0) {
         st.lz[(size_t)s * net.NH + L.h_out + i] = (float)a;
+        st.uz[(size_t)s * net.NH + L.h_out + i] = (float)c;
         st.nfree[(size_t)s * net.NH + L.h_out + i] = nf;
     }
 }

@@ -496,6 +496,7 @@ static int alloc_state(as_ctx* c) {
         }
         st.zcur = o.take<uint8_t>(NHS);
         st.lz = o.take<float>(NHS);
+        st.uz = o.take<float>(NHS);
         st.efix = o.take<uint8_t>(NTS);
         st.arow = o.take<float>(NHS);
         st.nfree = o.take<int>(NHS);
@@ -864,15 +865,10 @@ static int launch_as_iter(as_ctx* c, cudaStream_t s) {
     // the per-neuron bound terms are only summed when the best bound is tracked
     const int mode = c->opt.track_best ? 0 : 2;
     LAUNCH(c, s, CB_K_AS_COLA, (k_as_colA_t<<<c->blocksTA, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->tA, mode, 0)));
-    if (c->net.ball) LAUNCH(c, s, CB_K_AS_COLA, (k_ball_x0<<<c->net.S, CB_THREADS, 0, s>>>(c->net, c->st)));
+    if (c->net.ball) LAUNCH(c, s, CB_K_BALL_X0, (k_ball_x0<<<c->net.S, CB_BALL_THREADS, 0, s>>>(c->net, c->st)));
     if (c->opt.track_best)
         LAUNCH(c, s, CB_K_REDUCE, (k_reduce<<<c->net.S, CB_THREADS, 0, s>>>(c->net, c->st, 64, nullptr, 1)));
     LAUNCH(c, s, CB_K_AS_ROWB, (k_as_rowB_t<<<c->blocksTB, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->tB, 0)));
-    // an interior x_0* breaks the row pass's kappa = W x* + b of a new slot's z = 0 rows (it holds at
-    // box vertices only; kappa is multiplied by z = 0 in that iteration): recompute it in float32
-    if (c->net.ball)
-        LAUNCH(c, s, CB_K_SLOT_SUMS,
-               (k_slot_sums_after_add<<<c->blocksB, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->segB)));
     return check_launch(c, "Active Set iteration");
 }
 
@@ -991,7 +987,7 @@ extern "C" int as_bound(as_ctx* c, int precision, double* out, double* best) {
         // the BF16 form's iterates give a bound through float32 lambda, kappa and records
         if (c->opt.precision == 16) TRY(recompute_slot_sums(c));
         LAUNCH(c, s, CB_K_AS_COLA, (k_as_colA_t<<<c->blocksTA, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->tA, 1, 0)));
-        if (c->net.ball) LAUNCH(c, s, CB_K_AS_COLA, (k_ball_x0<<<S, CB_THREADS, 0, s>>>(c->net, c->st)));
+        if (c->net.ball) LAUNCH(c, s, CB_K_BALL_X0, (k_ball_x0<<<S, CB_BALL_THREADS, 0, s>>>(c->net, c->st)));
     }
     double* dout = c->bound_out;
     LAUNCH(c, s, CB_K_REDUCE, (k_reduce<<<S, CB_THREADS, 0, s>>>(c->net, c->st, precision, dout, 1)));
