@@ -120,7 +120,7 @@ def forward(dense, x):
 
 
 class BaB:
-    def __init__(self, net, lo0, hi0, crow, opt: BabOptions, root_bounds=None):
+    def __init__(self, net, lo0, hi0, crow, opt: BabOptions, root_bounds=None, ball=False):
         self.net, self.opt = net, opt
         self.lo0, self.hi0 = np.asarray(lo0, np.float64), np.asarray(hi0, np.float64)
         self.crow = np.asarray(crow, np.float64)
@@ -129,6 +129,7 @@ class BaB:
         self.bs = [d[1] for d in self.dense[:-1]]
         self.NH = sum(W.shape[0] for W in self.Ws)
         self.root_bounds = root_bounds
+        self.ball = ball   # the input set is the ellipsoid inscribed in the box
         self.ub, self.x_ub = math.inf, None
         self.bounded = 0
         self.seq = 0
@@ -136,7 +137,7 @@ class BaB:
         self.hard_bounded = 0
 
     def _bounds(self, splits):
-        lh, uh, _, _ = nw.ibp(self.Ws, self.bs, self.lo0, self.hi0, splits)
+        lh, uh, _, _ = nw.ibp(self.Ws, self.bs, self.lo0, self.hi0, splits, self.ball)
         lh, uh = [None] + list(lh[1:]), [None] + list(uh[1:])
         if self.root_bounds is not None:
             rl, ru = self.root_bounds
@@ -146,7 +147,8 @@ class BaB:
 
     def _solve(self, splits, alg, warm=None):
         lh, uh = self._bounds(splits)
-        P = nw.Problem(self.net, self.lo0, self.hi0, self.crow, bounds=(lh[1:], uh[1:]), dense=self.dense)
+        P = nw.Problem(self.net, self.lo0, self.hi0, self.crow, bounds=(lh[1:], uh[1:]), dense=self.dense,
+                       ball=self.ball)
         opt = self.opt.loose if alg == "l" else self.opt.tight
         st = None
         if warm is not None and self.opt.warm_start:

@@ -26,18 +26,18 @@ from . import active_set as AS
 from . import network as nw
 
 
-def intermediate_bounds(net: list, lo0, hi0, opt: AS.Options, splits=None, dense=None):
+def intermediate_bounds(net: list, lo0, hi0, opt: AS.Options, splits=None, dense=None, ball=False):
     """1-based lists (lhat, uhat) of every hidden layer's pre-activation bounds for one box.
 
     net: layer dicts of the whole network (the last layer linear); lo0, hi0: the input box;
     opt: the iteration schedule of each sub-network solve; splits: int8 over the hidden neurons,
-    layer-major, or None.
+    layer-major, or None; ball: the input set is the ellipsoid inscribed in the box.
     """
     dense = dense if dense is not None else nw.dense_layers(net)
     n = len(net)
     Ws = [d[0] for d in dense[:-1]]
     bs = [d[1] for d in dense[:-1]]
-    lhat, uhat, _, _ = nw.ibp(Ws, bs, lo0, hi0, splits)
+    lhat, uhat, _, _ = nw.ibp(Ws, bs, lo0, hi0, splits, ball)
     lhat = [None] + [v.copy() for v in lhat[1:]]
     uhat = [None] + [v.copy() for v in uhat[1:]]
     for k in range(2, n):
@@ -49,7 +49,7 @@ def intermediate_bounds(net: list, lo0, hi0, opt: AS.Options, splits=None, dense
             for sign in (1.0, -1.0):
                 crow = np.zeros(nk)
                 crow[i] = sign
-                P = nw.Problem(sub, lo0, hi0, crow, bounds=bounds, dense=dsub)
+                P = nw.Problem(sub, lo0, hi0, crow, bounds=bounds, dense=dsub, ball=ball)
                 final, _, _ = AS.solve(P, opt)
                 vals.append(final)
             l = max(lhat[k][i], vals[0])
@@ -66,7 +66,8 @@ def batch(prob: dict, opt: AS.Options):
     L, U = [], []
     for s in range(prob["lo"].shape[0]):
         sp = None if prob.get("splits") is None else prob["splits"][s]
-        lh, uh = intermediate_bounds(prob["net"], prob["lo"][s], prob["hi"][s], opt, sp, dense)
+        lh, uh = intermediate_bounds(prob["net"], prob["lo"][s], prob["hi"][s], opt, sp, dense,
+                                     bool(prob.get("ball", False)))
         L.append(np.concatenate(lh[1:]))
         U.append(np.concatenate(uh[1:]))
     return np.array(L), np.array(U)

@@ -123,3 +123,55 @@ def test_ball_bound_is_above_the_box_lp():
     dense = nw.dense_layers(prob["net"])
     X = _ellipsoid_points(P.lo[0], P.hi[0], 4000, 4)
     assert best <= min(float(bab.forward(dense, x)[0]) for x in X) + 1e-9
+
+
+def test_intermediate_bounds_over_the_ellipsoid():
+    """App. E's staged solves over the ellipsoid: zero iterations give its interval propagation;
+    solves tighten it and still contain the pre-activations of sampled inputs."""
+    from oracle import intermediate as IM
+    prob = _ball_prob("mlp_4_3_3_3_1", 2)
+    lo, hi = prob["lo"][0].astype(np.float64), prob["hi"][0].astype(np.float64)
+    dense = nw.dense_layers(prob["net"])
+    Ws, bs = [d[0] for d in dense[:-1]], [d[1] for d in dense[:-1]]
+    il, iu, _, _ = nw.ibp(Ws, bs, lo, hi, ball=True)
+    l0, u0 = IM.intermediate_bounds(prob["net"], lo, hi, AS.Options(), dense=dense, ball=True)
+    for k in range(1, len(l0)):
+        np.testing.assert_allclose(l0[k], il[k], atol=1e-12)
+        np.testing.assert_allclose(u0[k], iu[k], atol=1e-12)
+    lh, uh = IM.intermediate_bounds(prob["net"], lo, hi, AS.Options(bigm_iters=200), dense=dense, ball=True)
+    X = _ellipsoid_points(lo, hi, 3000, 6)
+    h = X.T
+    gain = 0.0
+    for k, (W, b) in enumerate(zip(Ws, bs), start=1):
+        a = W @ h + b[:, None]
+        assert np.all(a.min(axis=1) >= lh[k] - 1e-9) and np.all(a.max(axis=1) <= uh[k] + 1e-9)
+        gain += np.sum(iu[k] - il[k]) - np.sum(uh[k] - lh[k])
+        h = np.maximum(a, 0.0)
+    assert gain > 0
+
+
+@pytest.mark.parametrize("seed,verdict", [(4, "verified"), (4, "falsified"), (7, "verified")])
+def test_branch_and_bound_over_the_ellipsoid(seed, verdict):
+    """The property f(x) - t > 0 over the ellipsoid, t below every sampled value by a tenth of the
+    sampled range (verified), or midway through the sampled range (falsified, the point found lies
+    in the ellipsoid and has a negative value)."""
+    prob = _ball_prob("mlp_4_5_5_1", seed)
+    lo, hi = prob["lo"][0].astype(np.float64), prob["hi"][0].astype(np.float64)
+    dense = nw.dense_layers(prob["net"])
+    vals = np.array([bab.forward(dense, x)[0] for x in _ellipsoid_points(lo, hi, 4000, seed)])
+    t = vals.min() - 0.1 * np.ptp(vals) if verdict == "verified" else 0.5 * (vals.min() + vals.max())
+    net = [dict(L) for L in prob["net"]]
+    net[-1]["b"] = (net[-1]["b"].astype(np.float64) - t).astype(np.float32)
+    opt = bab.BabOptions(loose=AS.Options(bigm_iters=100),
+                         tight=AS.Options(bigm_iters=50, as_iters=100, omega=30, max_cuts=3),
+                         batch=8, max_domains=600)
+    res = bab.BaB(net, lo, hi, np.ones(1), opt, ball=True).run()
+    assert res["status"] == verdict
+    if verdict == "falsified":
+        x = res["x"]
+        c, e = 0.5 * (lo + hi), 0.5 * (hi - lo)
+        assert np.sum(((x - c) / e) ** 2) <= 1 + 1e-9
+        assert bab.forward(nw.dense_layers(net), x)[0] < 0
+    else:
+        vals_t = np.array([bab.forward(nw.dense_layers(net), x)[0] for x in _ellipsoid_points(lo, hi, 2000, 1)])
+        assert 0 < res["lower"] <= vals_t.min()
