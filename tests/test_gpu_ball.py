@@ -210,3 +210,68 @@ def test_unsupported_combinations_are_refused():
         ctx.sp_step(1)
     with pytest.raises(binding.CBError):
         binding.context_for(prob, _opts(precision=16))
+
+
+def test_intermediate_bounds_over_the_ellipsoid_match_oracle():
+    """Layer 2 (solves over the interval bounds of layer 1, the same on both sides) within
+    1e-4 (1 + max |v|). Over an ellipsoid x_0* moves continuously with f_0, so the float32 runs drift
+    from the FP64 ones by the float32 rounding of f_0 at every iteration, where box vertices absorb
+    it; deeper layers start from layer-2 bounds that already carry that drift, amplified by the
+    weights (sum |w| about 8 on the conv net's FC layer): 5e-3 (1 + max |v|) there. Every bound
+    holds the pre-activations of inputs sampled in the ellipsoid."""
+    from oracle import intermediate as IM
+    kw = dict(bigm_iters=12, as_iters=8, omega=4, max_cuts=3)
+    for name, S in (("mlp_4_3_3_3_1", 2), ("small_conv", 2)):
+        prob = _ball(name, S, seed=3)
+        lh, uh = binding.intermediate_bounds(prob["net"], prob["lo"], prob["hi"], None, _opts(**kw))
+        rl, ru = IM.batch(prob, AS.Options(**kw))
+        widths = [L["n_out"] for L in prob["net"][:-1]]
+        o1, o2 = widths[0], widths[0] + widths[1]
+        for g, r in ((lh, rl), (uh, ru)):
+            np.testing.assert_allclose(g[:, :o2], r[:, :o2], rtol=0, atol=1e-4 * (1 + np.abs(r[:, :o2])).max())
+            np.testing.assert_allclose(g[:, o2:], r[:, o2:], rtol=0, atol=5e-3 * (1 + np.abs(r[:, o2:])).max())
+        dense = nw.dense_layers(prob["net"])
+        rng = synth.SplitMix64(9)
+        for s in range(S):
+            lo, hi = prob["lo"][s].astype(np.float64), prob["hi"][s].astype(np.float64)
+            c, e = 0.5 * (lo + hi), 0.5 * (hi - lo)
+            g = rng.normal(1000 * lo.size).reshape(1000, lo.size)
+            g /= np.linalg.norm(g, axis=1, keepdims=True)
+            h = (c + e * g * (rng.uniform(1000) ** (1.0 / lo.size))[:, None]).T
+            pre = []
+            for W, b, _ in dense[:-1]:
+                a = W @ h + b[:, None]
+                pre.append(a)
+                h = np.maximum(a, 0.0)
+            a = np.concatenate(pre)
+            assert np.all(a.min(axis=1) >= lh[s] - 1e-5) and np.all(a.max(axis=1) <= uh[s] + 1e-5)
+
+
+@pytest.mark.parametrize("seed,verdict", [(4, "verified"), (4, "falsified"), (7, "verified")])
+def test_branch_and_bound_over_the_ellipsoid_matches_oracle(seed, verdict):
+    prob = _ball("mlp_4_5_5_1", 1, seed=seed)
+    lo, hi = prob["lo"][0].astype(np.float64), prob["hi"][0].astype(np.float64)
+    dense = nw.dense_layers(prob["net"])
+    rng = synth.SplitMix64(seed)
+    c, e = 0.5 * (lo + hi), 0.5 * (hi - lo)
+    g = rng.normal(4000 * lo.size).reshape(4000, lo.size)
+    g /= np.linalg.norm(g, axis=1, keepdims=True)
+    X = c + e * g * (rng.uniform(4000) ** (1.0 / lo.size))[:, None]
+    vals = np.array([bab.forward(dense, x)[0] for x in X])
+    t = vals.min() - 0.1 * np.ptp(vals) if verdict == "verified" else 0.5 * (vals.min() + vals.max())
+    net = [dict(L) for L in prob["net"]]
+    net[-1]["b"] = (net[-1]["b"].astype(np.float64) - t).astype(np.float32)
+    loose = dict(bigm_iters=100, as_iters=0, input_l2=1)
+    tight = dict(bigm_iters=50, as_iters=100, omega=30, max_cuts=3, input_l2=1)
+    res = binding.bab(net, prob["lo"][0], prob["hi"][0], None,
+                      binding.bab_default_options(loose=loose, tight=tight, batch=8, max_domains=600, cost_ratio=4.0))
+    ref = bab.BaB(net, lo, hi, np.ones(1), bab.BabOptions(
+        loose=AS.Options(bigm_iters=100), tight=AS.Options(bigm_iters=50, as_iters=100, omega=30, max_cuts=3),
+        batch=8, max_domains=600), ball=True).run()
+    assert ref["status"] == verdict and res["status"] == verdict
+    if verdict == "falsified":
+        x = res["x"].astype(np.float64)
+        assert np.sum(((x - c) / e) ** 2) <= 1 + 1e-5
+        assert bab.forward(nw.dense_layers(net), x)[0] < 0
+    else:
+        assert res["lower"] > 0
