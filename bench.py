@@ -521,6 +521,27 @@ def l2_run(binding, torch, dev, stream, rank):
             "unit": UNIT, **out}
 
 
+def hbm_rooflines(workload, kt):
+    """The HBM side of the roofline for every kernel with a committed DRAM capture: measured DRAM
+    bytes per launch (ncu, the captured build) over this run's mean launch duration (CUDA events),
+    against the measured copy bandwidth of MEASURED_PEAKS.json."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak, src = float(json.load(f)["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (of measured)"
+    except (OSError, KeyError, ValueError):
+        peak, src = 6800.0, "fallback 6.8 TB/s"
+    out = {}
+    for k, (tms, n) in kt.items():
+        t = captured_traffic(workload, k)
+        if t is None or not n or tms <= 0:
+            continue
+        us = tms / n * 1e3
+        gbs = t / (us * 1e-6) / 1e9
+        out[k] = {"dram_bytes_per_launch": t, "launch_us": us, "achieved": gbs, "peak": peak, "unit": "GB/s",
+                  "frac": gbs / peak, "peak_source": src}
+    return out
+
+
 def captured_traffic(workload, kernel):
     """DRAM bytes per launch of `kernel` from the committed ncu capture of this workload, or None
     when there is none or the kernel source has changed since it was taken."""
@@ -555,10 +576,8 @@ def job_throughput(S_per_rank, world, ms_per_step):
     return S_per_rank * iterations_per_step() * world / (ms_per_step / 1e3)
 
 
-def cpu_baseline(prob_name, seconds_budget=20.0):
-    """Times the CPU oracle, single-threaded, on a bounded sample of the workload: one subproblem,
-    a few Big-M then Active Set iterations (with the two first mask additions)."""
-    code = f"""
+def _oracle_sample_code(prob_name, s, seconds_budget):
+    return f"""
 import os, sys, time, json
 sys.path.insert(0, {ROOT!r})
 from oracle import active_set as AS, network as nw
@@ -566,26 +585,51 @@ from paper_2101_05844_gb300 import synth
 prob = synth.problem({prob_name!r}, seed=0)
 t0 = time.time()
 dense = nw.dense_layers(prob["net"])
-P = nw.Problem(prob["net"], prob["lo"][0], prob["hi"][0], prob["C"][0], dense=dense)
+P = nw.Problem(prob["net"], prob["lo"][{s}], prob["hi"][{s}], prob["C"][{s}], dense=dense)
 setup = time.time() - t0
 opt = AS.Options(bigm_iters=4, as_iters=200, omega=15, max_cuts=5)
-s = AS.ActiveSet(P, opt)
+st = AS.ActiveSet(P, opt)
 t0 = time.time(); n = 0
 while n < 40 and (time.time() - t0) < {seconds_budget}:
-    s.step(1); n += 1
+    st.step(1); n += 1
 dt = time.time() - t0
 print(json.dumps({{"iters": n, "seconds": dt, "setup_s": setup}}))
 """
+
+
+def cpu_baseline(prob_name, seconds_budget=20.0):
+    """Times the CPU oracle, single-threaded, on a bounded sample of the workload: one subproblem,
+    a few Big-M then Active Set iterations (with the two first mask additions). As context, the
+    same sample on every subproblem at once, one single-threaded process each on the host's cores
+    (fresh interpreters, started after the GPU work: nothing is forked from a CUDA process)."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
+    r = subprocess.run([sys.executable, "-c", _oracle_sample_code(prob_name, 0, seconds_budget)],
+                       capture_output=True, text=True, env=env, timeout=600)
     if r.returncode != 0:
         return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": r.stderr[-300:]}
     d = json.loads(r.stdout.strip().splitlines()[-1])
-    return {"value": d["iters"] / d["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"1 of the 9 subproblems, {d['iters']} iterations (4 Big-M, then Active Set, masks "
-                      f"added at Active Set iterations 0, 1, 15, 16, 30), FP64 numpy, dense conv "
-                      f"operators, single thread; {d['seconds']:.1f} s"}
+    out = {"value": d["iters"] / d["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"1 of the 9 subproblems, {d['iters']} iterations (4 Big-M, then Active Set, masks "
+                     f"added at Active Set iterations 0, 1, 15, 16, 30), FP64 numpy, dense conv "
+                     f"operators, single thread; {d['seconds']:.1f} s"}
+    from paper_2101_05844_gb300 import synth
+    S = synth.problem(prob_name, seed=0)["lo"].shape[0]
+    k = max(1, min(os.cpu_count() or 1, S))
+    procs = [subprocess.Popen([sys.executable, "-c", _oracle_sample_code(prob_name, q, seconds_budget / 2)],
+                              stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env)
+             for q in range(k)]
+    rates = []
+    for p in procs:
+        so, _ = p.communicate(timeout=600)
+        if p.returncode == 0:
+            e = json.loads(so.strip().splitlines()[-1])
+            rates.append(e["iters"] / e["seconds"])
+    if len(rates) == k:
+        out["all_cores"] = {"value": sum(rates), "unit": UNIT, "cores": k, "host_cores": os.cpu_count(),
+                            "sample": f"the same sample on {k} subproblems at once, one single-threaded "
+                                      f"process each; the sum of their rates"}
+    return out
 
 
 def reference_arm(args):
@@ -752,6 +796,7 @@ def main():
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (derived)",
                      "traffic": captured_traffic(args.workload, top), "launches": n, "kernel_ms": tms,
                      "share_of_kernel_time": tms / step_kernel_ms if step_kernel_ms else None},
+        "roofline_hbm": hbm_rooflines(args.workload, kt),
         "kernel_ms_per_step": {k: v[0] for k, v in kt.items() if v[1]},
         "clocks": clk.summary(),
         "bounds": {"active_set": [float(v) for v in bounds_as], "saddle_point": [float(v) for v in bounds_sp]},
