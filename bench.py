@@ -182,7 +182,7 @@ def slots_schedule(opt):
 
 
 def batched_run(binding, torch, dev, stream, rank):
-    """BASELINE's batching form: the Wide conv net on 4096 branch-and-bound subdomains (random
+    """The batching workload: the Wide conv net on 4096 branch-and-bound subdomains (random
     ReLU splits, caps of 1-5 masks), 100 Big-M + 400 Active Set iterations, one timed run after a
     warm-up, and a profiled run for the dominant kernel's rate."""
     from paper_2101_05844_gb300 import synth
@@ -244,7 +244,7 @@ def batched_run(binding, torch, dev, stream, rank):
 
 
 def precision_run(binding, torch, dev, stream, rank, S=1024, chunk=25):
-    """BASELINE's precision form: the conv net 3x32x32 -> 4 conv 3x3 -> FC512 -> FC10 on S boxes of
+    """The precision workload: the conv net 3x32x32 -> 4 conv 3x3 -> FC512 -> FC10 on S boxes of
     half-width 8/255, 100 Big-M + 400 Active Set iterations, once in float32 and once in the BF16
     form (tensor-core products, precision 16), same schedule, same GPU. Reports each form's
     subproblem-iterations/s (one timed run after a warm-up) and the time to bound: iteration time
@@ -353,7 +353,7 @@ def precision_run(binding, torch, dev, stream, rank, S=1024, chunk=25):
 
 
 def differentiation_run(binding, torch, dev, stream, rank):
-    """BASELINE's differentiation form: MLP 784-1024-1024-1024-10 on 256 boxes of half-width 0.1,
+    """The differentiation workload: MLP 784-1024-1024-1024-10 on 256 boxes of half-width 0.1,
     60 Big-M + 240 Active Set iterations in float32 (timed after a warm-up), then the bound and its
     envelope gradient with respect to W, b and the box endpoints (as_bound_backward, timed)."""
     from paper_2101_05844_gb300 import synth
@@ -655,15 +655,15 @@ def main():
     ap.add_argument("--workload", default="wide_conv")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", action="store_true",
-                    help="also time BASELINE's precision form: conv4 on 1024 boxes, float32 against the "
+                    help="also time the precision workload: conv4 on 1024 boxes, float32 against the "
                          "BF16 form, subproblem-iterations/s and time to the float32 bound")
     ap.add_argument("--precision-subproblems", type=int, default=1024,
-                    help="boxes of the precision form (1024 as BASELINE's; fewer for a profiler capture)")
+                    help="boxes of the precision form (1024 by default; fewer for a profiler capture)")
     ap.add_argument("--differentiation", action="store_true",
-                    help="also time BASELINE's differentiation form: MLP 784-1024x3-10, 256 boxes, 300 "
+                    help="also time the differentiation workload: MLP 784-1024x3-10, 256 boxes, 300 "
                          "Active Set iterations, then the bound and its envelope gradient")
     ap.add_argument("--batched", action="store_true",
-                    help="also time BASELINE's batching form: 4096 subdomains, 500 Active Set iterations")
+                    help="also time the batching workload: 4096 subdomains, 500 Active Set iterations")
     ap.add_argument("--intermediate", action="store_true",
                     help="also time intermediate bounds by batched sub-network solves on the wide conv "
                          "net (one box, layers 2 and 3) and the final bounds they give")

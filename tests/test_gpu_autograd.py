@@ -1,4 +1,4 @@
-"""Differentiation (BASELINE config 5 form): the envelope gradient through torch.autograd.
+"""Differentiation (the MLP 784-1024x3-10 workload): the envelope gradient through torch.autograd.
 
 1. Finite differences through the GPU path itself: the bound at fixed duals and masks is linear
    in each weight where the primal minimiser does not change, so a central difference of two

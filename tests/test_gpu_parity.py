@@ -3,10 +3,10 @@
 Tolerances (float32 GPU arithmetic against FP64):
   * interval bounds: the float32 interval contains the FP64 one and is within 4e-6 (1 + |v|) of it
     (FP64 accumulation per layer, outward rounding to float32 at every layer);
-  * one-iteration lockstep of the duals: 1e-5 relative, 1e-7 absolute floor (the benchmark spec), on every
+  * one-iteration lockstep of the duals: 1e-5 relative, 1e-7 absolute floor, on every
     entry whose update direction is decided: entries where the oracle's gradient is within
     1e-4 of zero are checked for validity only (both signs give a valid Adam step);
-  * bounds: 1e-4 absolute (north star), 1e-5 relative where values are large;
+  * bounds: 1e-4 absolute, 1e-5 relative where values are large;
   * masks and snapshot bits: bit-exact.
 """
 import numpy as np
@@ -515,7 +515,7 @@ def test_full_size_wide_conv_lockstep_on_sampled_subproblems(it, nslots):
 
 
 def test_batched_subdomains_lockstep_with_splits_and_caps():
-    """BASELINE's batching form at full size: 4096 branch-and-bound subdomains of the Wide conv
+    """The batching workload at full size: 4096 branch-and-bound subdomains of the Wide conv
     net with random ReLU splits and per-subdomain caps of 1-5 masks, in the bench's graph launch
     configuration. Interval bounds with the splits, and one Active Set iteration (an addition
     iteration, so that capped subdomains must skip the new slot) from a drawn state, checked on
