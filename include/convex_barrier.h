@@ -65,7 +65,7 @@ typedef struct as_net {
 
 /* Solver options; as_default_options() fills the paper's values (Sec. 8.1, App. C). */
 typedef struct as_options {
-    int bigm_iters;      /* T_M: Big-M iterations before Active Set (Alg. 1 line 2, App. B)   */
+    int bigm_iters;      /* T_M: Big-M iterations before Active Set (its initialisation, App. B) */
     int as_iters;        /* T_A: Active Set iterations (sets the learning-rate schedule)      */
     double bigm_lr0, bigm_lr1; /* Big-M step size, linear from lr0 to lr1 (1e-2 -> 1e-4)       */
     double as_lr0, as_lr1;     /* Active Set step size after reset (1e-3 -> 1e-6)              */
@@ -106,7 +106,7 @@ typedef struct as_ctx as_ctx;
 /* Fills *opt with the defaults above. */
 void as_default_options(as_options* opt);
 
-/* Creates a context for S subproblems (Alg. 1 line 2 / Alg. 3 line 2).
+/* Creates a context for S subproblems (the initialisation of Alg. 1 and Alg. 3).
  *  x_lo, x_hi: [S][n_0] input boxes, host or device; x_lo <= x_hi elementwise (AS_ERR_ARG).
  *  C:          [S][n_out] property rows, host or device; subproblem s bounds C[s] . x_hat_n.
  *              NULL allowed only when n_out == 1 (then C[s] = 1).
