@@ -453,6 +453,7 @@ def intermediate_run(binding, torch, dev, stream, rank):
                          "subproblems": {"layer2": 2 * widths[1], "layer3": 2 * widths[2]},
                          "iterations": {"bigm": ib_bigm, "active_set": ib_as, "max_cuts": 3}},
             "value": units / (ms / 1e3), "unit": UNIT, "ms": ms,
+            "cpu_baseline": oracle_rate("wide_conv", "layer2") if rank == 0 else None,
             "width_over_interval_width": width_ratio,
             "final_bound_9_properties": {"schedule": f"{AS_BIGM} Big-M + {AS_ITERS} Active Set",
                                          "interval_bounds_mean": float(np.mean(final["interval"])),
@@ -518,7 +519,7 @@ def l2_run(binding, torch, dev, stream, rank):
                     "final_bounds": [float(v) for v in b]}
     return {"workload": {"net": "wide_conv 3x32x32 conv16-conv32-FC100-FC10", "subproblems": S,
                          "iterations": iters, "input_set": "l2 ball of radius 2/255 inscribed in the l_inf box"},
-            "unit": UNIT, **out}
+            "unit": UNIT, "cpu_baseline": oracle_rate("wide_conv", "l2") if rank == 0 else None, **out}
 
 
 def hbm_rooflines(workload, kt):
@@ -576,16 +577,26 @@ def job_throughput(S_per_rank, world, ms_per_step):
     return S_per_rank * iterations_per_step() * world / (ms_per_step / 1e3)
 
 
-def _oracle_sample_code(prob_name, s, seconds_budget):
+def _oracle_sample_code(prob_name, s, seconds_budget, variant=""):
+    """A bounded oracle run on subproblem s: variant "" the workload itself, "l2" over the l2 ball
+    inscribed in its box, "layer2" the intermediate-bounds subproblem of layer 2's first neuron
+    (the sub-network up to the second layer, property row +e_0)."""
     return f"""
 import os, sys, time, json
+import numpy as np
 sys.path.insert(0, {ROOT!r})
 from oracle import active_set as AS, network as nw
 from paper_2101_05844_gb300 import synth
 prob = synth.problem({prob_name!r}, seed=0)
 t0 = time.time()
-dense = nw.dense_layers(prob["net"])
-P = nw.Problem(prob["net"], prob["lo"][{s}], prob["hi"][{s}], prob["C"][{s}], dense=dense)
+net = prob["net"]
+if {variant!r} == "layer2":
+    net = net[:2]
+    crow = np.zeros(net[1]["n_out"]); crow[0] = 1.0
+else:
+    crow = prob["C"][{s}]
+dense = nw.dense_layers(net)
+P = nw.Problem(net, prob["lo"][{s}], prob["hi"][{s}], crow, dense=dense, ball={variant!r} == "l2")
 setup = time.time() - t0
 opt = AS.Options(bigm_iters=4, as_iters=200, omega=15, max_cuts=5)
 st = AS.ActiveSet(P, opt)
@@ -595,6 +606,19 @@ while n < 40 and (time.time() - t0) < {seconds_budget}:
 dt = time.time() - t0
 print(json.dumps({{"iters": n, "seconds": dt, "setup_s": setup}}))
 """
+
+
+def oracle_rate(prob_name, variant, seconds_budget=10.0):
+    """subproblem-iterations/s of one single-threaded oracle run of _oracle_sample_code."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, "-c", _oracle_sample_code(prob_name, 0, seconds_budget, variant)],
+                       capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        return {"value": None, "kind": "oracle", "error": r.stderr[-300:]}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": d["iters"] / d["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one subproblem, {d['iters']} iterations, FP64 numpy, single thread; {d['seconds']:.1f} s"}
 
 
 def cpu_baseline(prob_name, seconds_budget=20.0):
