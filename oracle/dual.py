@@ -85,6 +85,29 @@ def coefficients(P, st: DualState):
     return f, g
 
 
+def x0_vertex(P, f0):
+    """argmin of -f0^T x_0 over the input set: the box vertex (u_0 where f0 >= 0), or over the
+    ellipsoid inscribed in the box (P.ball) c + e^2 f0 / |e f0|_2 (c where f0 = 0)."""
+    if not getattr(P, "ball", False):
+        return np.where(f0 >= 0, P.hi[0], P.lo[0])
+    c = 0.5 * (P.lo[0] + P.hi[0])
+    e = 0.5 * (P.hi[0] - P.lo[0])
+    nrm = float(np.sqrt(((e * f0) ** 2).sum()))
+    return c + (e * e * f0 / nrm if nrm > 0 else 0.0)
+
+
+def retract_x0(P, x0):
+    """Into the input set: the box clip, or over the ellipsoid the radial retraction
+    c + (x - c) / max(1, |(x - c) / e|_2) (its exact projection when the half-widths are equal)."""
+    if not getattr(P, "ball", False):
+        return np.clip(x0, P.lo[0], P.hi[0])
+    c = 0.5 * (P.lo[0] + P.hi[0])
+    e = 0.5 * (P.hi[0] - P.lo[0])
+    free = e > 0
+    r = float(np.sqrt((((x0 - c)[free] / e[free]) ** 2).sum()))
+    return np.where(free, c + (x0 - c) / max(1.0, r), c)
+
+
 def closed_form(P, f, g):
     """Inner minimisation, eqs. (7)-(8): x_k* at the upper end of its box where f_k >= 0.
 
@@ -92,11 +115,7 @@ def closed_form(P, f, g):
     min -f_0^T x_0, is attained at x_0* = c + e^2 f_0 / |e f_0|_2 (c where f_0 = 0), value
     -f_0^T c - |e f_0|_2 (Sec. 2: the input set needs only a closed-form linear minimisation)."""
     x = [np.where(f[k] >= 0, P.hi[k], P.lo[k]) for k in range(P.n)]
-    if getattr(P, "ball", False):
-        c = 0.5 * (P.lo[0] + P.hi[0])
-        e = 0.5 * (P.hi[0] - P.lo[0])
-        nrm = float(np.sqrt(((e * f[0]) ** 2).sum()))
-        x[0] = c + (e * e * f[0] / nrm if nrm > 0 else 0.0)
+    x[0] = x0_vertex(P, f[0])
     z = [None] + [np.where(g[k] >= 0, 1.0, 0.0) for k in range(1, P.n)]
     return x, z
 

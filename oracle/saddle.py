@@ -31,7 +31,11 @@ Readings (Sec. 5.2, 8.1, App. C):
     separately from E_k. Their gradient never exceeds that of beta_0 (resp. beta_1) in exact
     arithmetic, and equals it when the intermediate bounds are interval bounds, so such a row does
     not compete in the choice of eq. (12) (in exact arithmetic this changes no choice, since ties
-    go to beta_0 and beta_1).
+    go to beta_0 and beta_1);
+  * over an ellipsoid input set (P.ball) x_bar_0 is its closed-form vertex (dual.x0_vertex), and
+    the primal initialisation's steps on x_0 end in the radial retraction into it
+    (dual.retract_x0: the exact projection for a ball, a feasible point for any ellipsoid; App.
+    C.2 asks only for a feasible start, and the bound is valid for any primal iterate).
 """
 from __future__ import annotations
 
@@ -85,6 +89,7 @@ class SaddlePoint:
                               for k in range(1, n)]
         f = self.coefficients()
         self.x = [np.where(f[k] >= 0, P.hi[k], P.lo[k]) for k in range(n)]
+        self.x[0] = du.x0_vertex(P, f[0])
         self.z = [None] + [np.where(self.G[k] >= 0, 1.0, 0.0) for k in range(1, n)]
         self._primal_init()
         self.t = 0
@@ -186,6 +191,7 @@ class SaddlePoint:
         P, n = self.P, self.P.n
         f = self.coefficients()
         xb = [np.where(f[k] >= 0, P.hi[k], P.lo[k]) for k in range(n)]
+        xb[0] = du.x0_vertex(P, f[0])
         zb = [None] + [np.where(self.G[k] >= 0, 1.0, 0.0) for k in range(1, n)]
         val = float(P.b[n][0])
         for k in range(1, n):
@@ -219,7 +225,10 @@ class SaddlePoint:
                     fk = fk + ab[k] - b0[k] - b1[k]
                 fs.append(fk)
             for k in range(n):
-                self.x[k] = np.clip(self.x[k] + eta * fs[k], P.lo[k], P.hi[k])
+                if k == 0:   # into the input set (a box, or the ellipsoid inscribed in it)
+                    self.x[0] = du.retract_x0(P, self.x[0] + eta * fs[0])
+                else:
+                    self.x[k] = np.clip(self.x[k] + eta * fs[k], P.lo[k], P.hi[k])
             for k in range(1, n):
                 gk = b0[k] * P.uhat[k] + b1[k] * P.lhat[k]
                 self.z[k] = np.clip(self.z[k] + eta * gk, 0.0, 1.0)

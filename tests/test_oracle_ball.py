@@ -175,3 +175,50 @@ def test_branch_and_bound_over_the_ellipsoid(seed, verdict):
     else:
         vals_t = np.array([bab.forward(nw.dense_layers(net), x)[0] for x in _ellipsoid_points(lo, hi, 2000, 1)])
         assert 0 < res["lower"] <= vals_t.min()
+
+
+@pytest.mark.parametrize("name,seed", [("mlp_5_7_6_3", 1), ("small_conv", 2)])
+def test_saddle_point_over_the_ellipsoid(name, seed):
+    """Saddle Point from Active Set duals over the ellipsoid: the primal iterate stays inside it
+    (its start is retracted, then convex combinations of points inside), x_bar_0 lies on its
+    surface, and every bound lies below the sampled minimum."""
+    from oracle import saddle as SPm
+    prob = _ball_prob(name, seed)
+    P = nw.problems(prob)[0]
+    opt = AS.Options(bigm_iters=40, as_iters=40, omega=10, max_cuts=3, sp_init_steps=20)
+    s = AS.ActiveSet(P, opt).step(80)
+    sp = SPm.SaddlePoint(P, opt, s.st)
+    c, e = 0.5 * (P.lo[0] + P.hi[0]), 0.5 * (P.hi[0] - P.lo[0])
+    dense = nw.dense_layers(prob["net"])
+    m = min(float(prob["C"][0] @ bab.forward(dense, x)) for x in _ellipsoid_points(P.lo[0], P.hi[0], 3000, 2))
+    for _ in range(30):
+        assert np.sum(((sp.x[0] - c) / e) ** 2) <= 1 + 1e-9
+        val, xb, _ = sp.evaluate()
+        assert np.sum(((xb[0] - c) / e) ** 2) == pytest.approx(1.0, abs=1e-9)
+        assert val <= m + 1e-9
+        sp.step(1)
+
+
+def test_saddle_point_approaches_the_affine_closed_form():
+    """On the small ellipsoid where the network is affine (see above), Saddle Point from Big-M duals
+    climbs towards the closed-form minimum f(c) - |D a|_2 and never passes it."""
+    from oracle import saddle as SPm
+    prob = _ball_prob("mlp_4_3_3_1", 2, scale=0.05)
+    P = nw.problems(prob)[0]
+    dense = nw.dense_layers(prob["net"])
+    lo, hi = P.lo[0], P.hi[0]
+    c, e = 0.5 * (lo + hi), 0.5 * (hi - lo)
+    A, h0 = np.eye(lo.size), c.copy()
+    for W, b, _ in dense[:-1]:
+        act = (W @ h0 + b) > 0
+        A, h0 = act[:, None] * (W @ A), np.maximum(W @ h0 + b, 0.0)
+    a = prob["C"][0] @ dense[-1][0] @ A
+    exact = float(prob["C"][0] @ (dense[-1][0] @ h0 + dense[-1][1])) - float(np.linalg.norm(e * a))
+    opt = AS.Options(bigm_iters=200, sp_init_steps=20)
+    s = AS.ActiveSet(P, opt).step(200)
+    sp = SPm.SaddlePoint(P, opt, s.st)
+    start = sp.bound()
+    sp.step(400)
+    assert sp.best <= exact + 1e-9
+    assert sp.best >= start - 1e-12
+    assert exact - sp.best < 0.5 * (exact - start) or exact - sp.best < 1e-4
