@@ -95,9 +95,10 @@ typedef struct as_options {
                           * {sum_j ((x_j - c_j) / e_j)^2 <= 1} with c, e the box's centre and half-widths
                           * (an l2 ball of radius e for equal half-widths; Sec. 2 needs only a closed-form
                           * linear minimisation over the input set): layer 1's interval bounds are its exact
-                          * range W c + b -+ |W D|_2 and x_0* = c + e^2 f_0 / |e f_0|_2. Big-M / Active Set in
-                          * float32 only (precision 16: AS_ERR_ARG; sp_step: AS_ERR_STATE), and
-                          * as_bound_backward gives dW, db only (dlo, dhi or the chain form: AS_ERR_STATE).
+                          * range W c + b -+ |W D|_2 and x_0* = c + e^2 f_0 / |e f_0|_2 (Saddle Point: the
+                          * same vertex, and its primal initialisation retracts x_0 radially into the
+                          * ellipsoid). Float32 only (precision 16: AS_ERR_ARG); as_bound_backward gives
+                          * dW, db only (dlo, dhi or the chain form: AS_ERR_STATE).
                           * 0 (default): the box itself.                                        */
 } as_options;
 

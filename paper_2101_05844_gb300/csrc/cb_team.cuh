@@ -936,6 +936,7 @@ __device__ __forceinline__ void sp_phaseA_epilogue(const DNet& net, const DState
     st.xbar[xo] = xb;
     term -= (double)f * xb;
     st.terms[xo] = term;
+    if (net.ball && L.in_off == 0) st.fval[xo] = f;   // for the ellipsoid vertex (k_ball_sp)
     const float x = init ? xb : st.spx[cur][xo];
     if (init) st.spx[cur][xo] = xb;
     if (k <= net.n - 1) {
@@ -1191,11 +1192,105 @@ __global__ void __launch_bounds__(CB_THREADS) k_spi_col_t(DNet net, DState st, D
             const float g = st.b0i[h] * st.uhat[h] + st.b1i[h] * st.lhat[h];
             st.spz[cur][h] = fminf(fmaxf(st.spz[cur][h] + eta * g, 0.f), 1.f);
         }
-        st.spx[cur][xo] = fminf(fmaxf(st.spx[cur][xo] + eta * f, st.lo[xo]), st.hi[xo]);
+        if (net.ball && L.in_off == 0)   // over an ellipsoid, k_ball_retract brings x_0 back into it
+            st.spx[cur][xo] = st.spx[cur][xo] + eta * f;
+        else
+            st.spx[cur][xo] = fminf(fmaxf(st.spx[cur][xo] + eta * f, st.lo[xo]), st.hi[xo]);
     }
     if (last_block(&st.done[2]) && threadIdx.x == 0) {
         st.ctr[2] = step + 1;
         st.done[2] = 0;
+    }
+}
+
+// Saddle Point over the ellipsoid input set, one block per subproblem after each phase A: the
+// conditional gradient x_bar_0 = c + e^2 f_0 / |e f_0|_2 and its closed-form bound term (as
+// k_ball_x0); at the start (init) the primal iterate x_0 takes x_bar_0 and its phase-B records.
+__global__ void __launch_bounds__(CB_BALL_THREADS) k_ball_sp(DNet net, DState st, int init) {
+    const int s = blockIdx.x;
+    const DLayer& L = net.L[0];
+    const size_t base = (size_t)s * net.NT + L.in_off;
+    float p2 = 0.f, pc = 0.f;
+    for (int j = threadIdx.x; j < L.n_in; j += CB_BALL_THREADS) {
+        const float lo = st.lo[base + j], hi = st.hi[base + j], f = st.fval[base + j];
+        const float ef = 0.5f * (hi - lo) * f;
+        p2 = fmaf(ef, ef, p2);
+        pc = fmaf(f, 0.5f * (lo + hi), pc);
+    }
+    __shared__ double red[2][CB_BALL_THREADS / 32];
+    const double a2 = warp_sum((double)p2), ac = warp_sum((double)pc);
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = a2;
+        red[1][threadIdx.x >> 5] = ac;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < CB_BALL_THREADS / 32 ? red[0][threadIdx.x] : 0.0;
+        double w = threadIdx.x < CB_BALL_THREADS / 32 ? red[1][threadIdx.x] : 0.0;
+        v = warp_sum(v);
+        w = warp_sum(w);
+        if (threadIdx.x == 0) {
+            red[0][0] = v;
+            red[1][0] = w;
+        }
+    }
+    __syncthreads();
+    const double nrm = sqrt(red[0][0]);
+    const float inv = nrm > 0.0 ? (float)(1.0 / nrm) : 0.f;
+    if (threadIdx.x == 0) st.terms[base] = -red[1][0] - nrm;
+    const int cur = st.ctr[1] & 1;
+    for (int j = threadIdx.x; j < L.n_in; j += CB_BALL_THREADS) {
+        const size_t xo = base + j;
+        const float lo = st.lo[xo], hi = st.hi[xo];
+        const float c = 0.5f * (lo + hi), e = 0.5f * (hi - lo);
+        const float xb = fminf(fmaxf(c + e * e * st.fval[xo] * inv, lo), hi);
+        st.xbar[xo] = xb;
+        if (j) st.terms[xo] = 0.0;
+        if (init) {
+            st.spx[cur][xo] = xb;
+            float tp = -INFINITY, tn = -INFINITY;
+            if (lo != hi) {
+                const float den = __fsub_rn(hi, lo);
+                tp = __fdiv_rn(__fsub_rn(xb, lo), den);
+                tn = __fdiv_rn(__fsub_rn(hi, xb), den);
+            }
+            float4* r = sp_iplane(net, st, L, s) + xin_pos(L, j);
+            r[0] = make_float4(xb, tp, lo, hi);
+            r[L.xpos] = make_float4(xb, tn, hi, lo);
+        }
+    }
+}
+
+// After a primal-initialisation step over an ellipsoid: x_0 <- c + (x_0 - c) / max(1, r) with
+// r = |(x_0 - c) / e|_2 over the free inputs (fixed ones stay at c), one block per subproblem: the
+// exact projection when the half-widths are equal, a point of the ellipsoid for any of them.
+__global__ void __launch_bounds__(CB_BALL_THREADS) k_ball_retract(DNet net, DState st) {
+    const int s = blockIdx.x;
+    const DLayer& L = net.L[0];
+    const size_t base = (size_t)s * net.NT + L.in_off;
+    float* x = st.spx[st.ctr[1] & 1] + base;
+    float p = 0.f;
+    for (int j = threadIdx.x; j < L.n_in; j += CB_BALL_THREADS) {
+        const float lo = st.lo[base + j], hi = st.hi[base + j];
+        if (lo != hi) {
+            const float q = (x[j] - 0.5f * (lo + hi)) / (0.5f * (hi - lo));
+            p = fmaf(q, q, p);
+        }
+    }
+    __shared__ double red[CB_BALL_THREADS / 32];
+    const double a = warp_sum((double)p);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < CB_BALL_THREADS / 32 ? red[threadIdx.x] : 0.0;
+        v = warp_sum(v);
+        if (threadIdx.x == 0) red[0] = v;
+    }
+    __syncthreads();
+    const float scale = (float)(1.0 / fmax(1.0, sqrt(red[0])));
+    for (int j = threadIdx.x; j < L.n_in; j += CB_BALL_THREADS) {
+        const float lo = st.lo[base + j], hi = st.hi[base + j], c = 0.5f * (lo + hi);
+        x[j] = lo != hi ? fminf(fmaxf(c + (x[j] - c) * scale, lo), hi) : c;
     }
 }
 

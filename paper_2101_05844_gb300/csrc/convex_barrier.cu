@@ -877,6 +877,7 @@ static int launch_as_iter(as_ctx* c, cudaStream_t s) {
 static int launch_sp_iter(as_ctx* c, cudaStream_t s) {
     LAUNCH(c, s, CB_K_SP_ROWB, (k_sp_rowB_t<<<c->blocksTB, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->tB)));
     LAUNCH(c, s, CB_K_SP_COLC, (k_sp_colCA_t<<<c->blocksTA, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->tA)));
+    if (c->net.ball) LAUNCH(c, s, CB_K_BALL_X0, (k_ball_sp<<<c->net.S, CB_BALL_THREADS, 0, s>>>(c->net, c->st, 0)));
     if (c->opt.track_best)
         LAUNCH(c, s, CB_K_REDUCE, (k_reduce<<<c->net.S, CB_THREADS, 0, s>>>(c->net, c->st, 64, nullptr, 1)));
     return check_launch(c, "Saddle Point iteration");
@@ -951,10 +952,13 @@ static int sp_start(as_ctx* c) {
     k_sp_prep<<<grid_for(NHS), CB_THREADS, 0, s>>>(c->net, c->st);
     k_sp_colA_t<<<c->blocksTA, CB_THREADS, 0, s>>>(c->net, c->st, c->tA, 1);
     c->launches += 4;
+    if (c->net.ball) LAUNCH(c, s, CB_K_BALL_X0, (k_ball_sp<<<c->net.S, CB_BALL_THREADS, 0, s>>>(c->net, c->st, 1)));
     TRY(check_launch(c, "Saddle Point conversion"));
     for (int t = 0; t < c->opt.sp_init_steps; ++t) {
         LAUNCH(c, s, CB_K_SPI_ROW, (k_spi_row_t<<<c->blocksTB, CB_THREADS, 0, s>>>(c->net, c->st, c->tB)));
         LAUNCH(c, s, CB_K_SPI_COL, (k_spi_col_t<<<c->blocksTA, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->tA)));
+        if (c->net.ball)
+            LAUNCH(c, s, CB_K_BALL_X0, (k_ball_retract<<<c->net.S, CB_BALL_THREADS, 0, s>>>(c->net, c->st)));
     }
     TRY(check_launch(c, "Saddle Point primal initialisation"));
     c->sp_started = true;
@@ -964,13 +968,13 @@ static int sp_start(as_ctx* c) {
 
 extern "C" int sp_step(as_ctx* c, int n_iters) {
     if (!c) return AS_ERR_ARG;
-    if (c->net.ball) return fail(c, AS_ERR_STATE, "Saddle Point runs over box inputs only");
     if (n_iters < 0) return fail(c, AS_ERR_ARG, "n_iters < 0");
     if (!c->sp_started) TRY(sp_start(c));
     if (n_iters == 0) return AS_OK;
     if (c->sp_need_phaseA) {
         cudaStream_t s = c->stream;
         LAUNCH(c, s, CB_K_SP_COLA, (k_sp_colA_t<<<c->blocksTA, CB_THREADS, 0, s>>>(c->net, c->st, c->tA, 0)));
+        if (c->net.ball) LAUNCH(c, s, CB_K_BALL_X0, (k_ball_sp<<<c->net.S, CB_BALL_THREADS, 0, s>>>(c->net, c->st, 0)));
         TRY(check_launch(c, "Saddle Point phase A"));
         c->sp_need_phaseA = false;
     }
@@ -982,8 +986,10 @@ extern "C" int as_bound(as_ctx* c, int precision, double* out, double* best) {
     if (precision != 32 && precision != 64) return fail(c, AS_ERR_ARG, "precision must be 32 or 64");
     const int S = c->net.S;
     cudaStream_t s = c->stream;
-    if (c->sp_started) LAUNCH(c, s, CB_K_SP_COLA, (k_sp_colA_t<<<c->blocksTA, CB_THREADS, 0, s>>>(c->net, c->st, c->tA, 0)));
-    else {
+    if (c->sp_started) {
+        LAUNCH(c, s, CB_K_SP_COLA, (k_sp_colA_t<<<c->blocksTA, CB_THREADS, 0, s>>>(c->net, c->st, c->tA, 0)));
+        if (c->net.ball) LAUNCH(c, s, CB_K_BALL_X0, (k_ball_sp<<<S, CB_BALL_THREADS, 0, s>>>(c->net, c->st, 0)));
+    } else {
         // the BF16 form's iterates give a bound through float32 lambda, kappa and records
         if (c->opt.precision == 16) TRY(recompute_slot_sums(c));
         LAUNCH(c, s, CB_K_AS_COLA, (k_as_colA_t<<<c->blocksTA, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->tA, 1, 0)));

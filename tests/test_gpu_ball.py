@@ -204,12 +204,53 @@ def test_backward_gives_dW_db_and_refuses_the_box_gradients():
 
 def test_unsupported_combinations_are_refused():
     prob = _ball("mlp_tiny", 1)
-    ctx = binding.context_for(prob, _opts(bigm_iters=5, as_iters=5))
-    ctx.as_step(3)
-    with pytest.raises(binding.CBError):
-        ctx.sp_step(1)
     with pytest.raises(binding.CBError):
         binding.context_for(prob, _opts(precision=16))
+
+
+@pytest.mark.parametrize("name,S", [("mlp_tiny", 1), ("small_conv", 2), ("mlp_5_7_6_3", 3)])
+def test_saddle_point_over_the_ellipsoid_tracks_oracle_until_a_tie(name, S):
+    """Big-M, conversion, primal initialisation (x_0 retracted into the ellipsoid) and Saddle Point
+    iterations on both sides: bounds agree to 1e-4 until the oracle meets a decision within 1e-3 of
+    a tie; x_0 stays in the ellipsoid and every bound below the sampled minimum over it."""
+    from oracle import saddle as SPm
+    prob = _ball(name, S)
+    Ps = nw.problems(prob)
+    kw = dict(bigm_iters=40, as_iters=0, sp_init_steps=20)
+    ctx = binding.context_for(prob, _opts(**kw))
+    ctx.as_step(40)
+    refs = [AS.ActiveSet(P, AS.Options(**kw)).step(40) for P in Ps]
+    ctx.sp_step(0)
+    sps = [SPm.SaddlePoint(r.P, r.opt, r.st) for r in refs]
+    n0 = Ps[0].widths[0]
+    xg = ctx.get_state(binding.ST_SP_X).reshape(S, -1)
+    live = [bool(np.abs(xg[s] - np.concatenate(sp.x)).max() <= 1e-4) for s, sp in enumerate(sps)]
+    assert any(live)
+    dense = nw.dense_layers(prob["net"])
+    rng = synth.SplitMix64(6)
+    mins = []
+    for s, P in enumerate(Ps):
+        c, e = 0.5 * (P.lo[0] + P.hi[0]), 0.5 * (P.hi[0] - P.lo[0])
+        g = rng.normal(2000 * n0).reshape(2000, n0)
+        g /= np.linalg.norm(g, axis=1, keepdims=True)
+        X = c + e * g * (rng.uniform(2000) ** (1.0 / n0))[:, None]
+        mins.append(min(float(prob["C"][s] @ bab.forward(dense, x)) for x in X))
+    for t in range(30):
+        margins = [sp.decision_margin() for sp in sps]
+        ctx.sp_step(1)
+        gb = ctx.bound()
+        xg = ctx.get_state(binding.ST_SP_X).reshape(S, -1)
+        for s, sp in enumerate(sps):
+            P = Ps[s]
+            c, e = 0.5 * (P.lo[0] + P.hi[0]), 0.5 * (P.hi[0] - P.lo[0])
+            assert np.sum(((xg[s, :n0] - c) / e) ** 2) <= 1 + 1e-4
+            assert gb[s] <= mins[s] + 1e-6
+            if not live[s]:
+                continue
+            sp.step(1)
+            if abs(gb[s] - sp.evaluate()[0]) > 1e-4:
+                assert margins[s] < 1e-3, f"divergence at SP iteration {t} without a near-tie ({margins[s]})"
+                live[s] = False
 
 
 def test_intermediate_bounds_over_the_ellipsoid_match_oracle():
