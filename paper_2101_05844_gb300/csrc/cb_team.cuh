@@ -444,6 +444,27 @@ __global__ void __launch_bounds__(CB_BALL_THREADS) k_ball_x0(DNet net, DState st
         if (j) st.terms[xo] = 0.0;
         const unsigned fxm = st.efix[xo] ? 0xFFu : 0u;
         rec[xin_pos(L, j)] = make_float2(xv, __uint_as_float(fxm | (fxm << 8)));
+        if (net.bf) {   // BF16 form: the row products' operand planes, x_0* on slot 0 and on the
+                        // slots whose masks hold the input (fixed inputs only, at interior x_0*)
+            const BfLayer& B = net.bf[0];
+            int c = j, y = 0, xx = 0;
+            if (L.kind == 1) {
+                const int hw = L.hi * L.wi;
+                c = j / hw;
+                const int rem = j - c * hw;
+                y = rem / L.wi;
+                xx = rem - y * L.wi;
+            }
+            const long long off = ((long long)(y + L.pd) * L.Wp + (xx + L.pd)) * B.Cip + c;
+            const __nv_bfloat16 xb = __float2bfloat16_rn(xv), zero = __float2bfloat16_rn(0.f);
+            __nv_bfloat16* X = reinterpret_cast<__nv_bfloat16*>(B.X);
+            for (int t = 0; t <= net.cap; ++t) {
+                const long long pl = ((long long)t * net.S + s) * 2;
+                const bool on = t == 0 || fxm != 0u;
+                X[pl * B.PX + off] = on ? xb : zero;
+                X[(pl + 1) * B.PX + off] = on ? xb : zero;
+            }
+        }
     }
 }
 

@@ -221,7 +221,6 @@ static int validate_opt(as_ctx* c, const as_options& o) {
     if (o.sp_init_steps < 0 || o.graph_chunk < 0) return fail(c, AS_ERR_ARG, "negative step counts");
     if (o.precision != 32 && o.precision != 16) return fail(c, AS_ERR_ARG, "precision must be 32 or 16");
     if (o.input_l2 != 0 && o.input_l2 != 1) return fail(c, AS_ERR_ARG, "input_l2 must be 0 or 1");
-    if (o.input_l2 && o.precision == 16) return fail(c, AS_ERR_ARG, "the ellipsoid input set runs in float32 only");
     return AS_OK;
 }
 

@@ -202,10 +202,36 @@ def test_backward_gives_dW_db_and_refuses_the_box_gradients():
         ctx.backward(gb, dW, db, np.zeros_like(prob["lo"]), None)
 
 
-def test_unsupported_combinations_are_refused():
-    prob = _ball("mlp_tiny", 1)
-    with pytest.raises(binding.CBError):
-        binding.context_for(prob, _opts(precision=16))
+@pytest.mark.parametrize("name,S,kw", [
+    ("mlp_5_7_6_3", 4, dict(bigm_iters=30, as_iters=60, omega=20, max_cuts=4)),
+    ("small_conv", 3, dict(bigm_iters=20, as_iters=40, omega=12, max_cuts=5)),
+])
+def test_bf16_form_over_the_ellipsoid(name, S, kw):
+    """The BF16 form over the ellipsoid: the bound (re-evaluated in float32) lies below the sampled
+    minimum over the ellipsoid and within 1e-2 (per unit of 1 + |bound|) of the oracle's FP64 run,
+    the bound the BF16 suite sets for the box; graph replay equals plain launches."""
+    prob = _ball(name, S)
+    Ps = nw.problems(prob)
+    iters = kw["bigm_iters"] + kw["as_iters"]
+    ctx = binding.context_for(prob, _opts(precision=16, **kw))
+    ctx.as_step(iters)
+    b = ctx.bound()
+    dense = nw.dense_layers(prob["net"])
+    rng = synth.SplitMix64(12)
+    for s, P in enumerate(Ps):
+        ref = AS.ActiveSet(P, AS.Options(**kw)).step(iters).bound()
+        assert abs(b[s] - ref) / (1 + abs(ref)) <= 1e-2
+        n0 = P.widths[0]
+        c, e = 0.5 * (P.lo[0] + P.hi[0]), 0.5 * (P.hi[0] - P.lo[0])
+        g = rng.normal(2000 * n0).reshape(2000, n0)
+        g /= np.linalg.norm(g, axis=1, keepdims=True)
+        X = c + e * g * (rng.uniform(2000) ** (1.0 / n0))[:, None]
+        assert b[s] <= min(float(prob["C"][s] @ bab.forward(dense, x)) for x in X) + 1e-6
+    g = binding.context_for(prob, binding.default_options(graph_chunk=10, input_l2=1, precision=16, **kw))
+    a = binding.context_for(prob, _opts(precision=16, **kw))
+    g.as_step(iters)
+    a.as_step(iters)
+    np.testing.assert_array_equal(a.bound(), g.bound())
 
 
 @pytest.mark.parametrize("name,S", [("mlp_tiny", 1), ("small_conv", 2), ("mlp_5_7_6_3", 3)])
