@@ -26,6 +26,22 @@ from . import dual as du
 from . import relaxation as rx
 
 
+def _x0_box_terms(P, f0, x0):
+    """d/dl_0, d/du_0 of the x_0 part of the bound, min over the input set of -f_0^T x_0. Box: x_0*
+    at an end of its interval (half to each end where l = u). Ellipsoid inscribed in the box
+    (P.ball), centre c = (l + u) / 2, half-widths e = (u - l) / 2: the value -f c - |e f|_2 gives
+    -f / 2 -+ e f^2 / (2 |e f|) (the norm's subgradient 0 where e f = 0)."""
+    if getattr(P, "ball", False):
+        e = 0.5 * (P.hi[0] - P.lo[0])
+        nrm = float(np.sqrt(((e * f0) ** 2).sum()))
+        d = e * f0 * f0 / (2.0 * nrm) if nrm > 0 else np.zeros_like(f0)
+        return -0.5 * f0 + d, -0.5 * f0 - d
+    same = P.lo[0] == P.hi[0]
+    dlo = np.where(same, -0.5 * f0, np.where(x0 == P.lo[0], -f0, 0.0))
+    dhi = np.where(same, -0.5 * f0, np.where(x0 == P.hi[0], -f0, 0.0))
+    return dlo, dhi
+
+
 def envelope_gradient(P, st: du.DualState):
     """Returns dict: dW[k] dense (k = 1..n), db[k], dlo0, dhi0 for one subproblem."""
     val, f, g, x, z = du.evaluate(P, st)
@@ -47,12 +63,8 @@ def envelope_gradient(P, st: du.DualState):
     db[n] = np.ones(1)
     W1 = P.W[1]
     pos = W1 >= 0
-    dlo = -f[0] * (x[0] == P.lo[0]) if n >= 1 else None
-    dhi = -f[0] * (x[0] == P.hi[0])
+    dlo, dhi = _x0_box_terms(P, f[0], x[0])
     # where l_0 = u_0 both indicators hold; the box then moves as one point and f_0 enters once
-    same = P.lo[0] == P.hi[0]
-    dlo = np.where(same, -f[0] * 0.5, dlo)
-    dhi = np.where(same, -f[0] * 0.5, dhi)
     if n >= 2:
         for sl in st.slots[1]:
             If = sl.I.astype(np.float64)
@@ -102,6 +114,8 @@ def chain_gradient(P, st: du.DualState, splits=None):
         same = lo == hi
         a = np.where(same, -0.5 * f[k], np.where(x[k] == lo, -f[k], 0.0))
         c = np.where(same, -0.5 * f[k], np.where(x[k] == hi, -f[k], 0.0))
+        if k == 0:
+            a, c = _x0_box_terms(P, f[0], x[0])
         if k + 1 <= n - 1:
             W = P.W[k + 1]
             pos = W >= 0
@@ -124,6 +138,21 @@ def chain_gradient(P, st: du.DualState, splits=None):
             Ah = np.where((sp > 0) & (lh == 0), 0.0, Ah)
             Uh = np.where((sp < 0) & (uh == 0), 0.0, Uh)
         W = P.W[k]
+        if k == 1 and getattr(P, "ball", False):
+            # lhat_1, uhat_1 = W c + b -+ r with r_i = |W_i o e|_2 over the ellipsoid; c = (l + u) / 2,
+            # e = (u - l) / 2
+            c = 0.5 * (P.lo[0] + P.hi[0])
+            e = 0.5 * (P.hi[0] - P.lo[0])
+            r = np.sqrt(((W * e[None, :]) ** 2).sum(axis=1))
+            q = np.where(r[:, None] > 0, W * W * e[None, :] / np.where(r > 0, r, 1.0)[:, None], 0.0)   # dr/de
+            dc = W.T @ (Ah + Uh)
+            de = q.T @ (Uh - Ah)
+            Lb[0] = Lb[0] + 0.5 * dc - 0.5 * de
+            Ub[0] = Ub[0] + 0.5 * dc + 0.5 * de
+            drdw = np.where(r[:, None] > 0, W * (e * e)[None, :] / np.where(r > 0, r, 1.0)[:, None], 0.0)
+            dW[1] = dW[1] + (Ah + Uh)[:, None] * c[None, :] + (Uh - Ah)[:, None] * drdw
+            db[1] = db[1] + Ah + Uh
+            continue
         Wp, Wn = np.maximum(W, 0.0), np.minimum(W, 0.0)
         Lb[k - 1] = Lb[k - 1] + Wp.T @ Ah + Wn.T @ Uh
         Ub[k - 1] = Ub[k - 1] + Wn.T @ Ah + Wp.T @ Uh

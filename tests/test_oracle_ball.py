@@ -222,3 +222,65 @@ def test_saddle_point_approaches_the_affine_closed_form():
     assert sp.best <= exact + 1e-9
     assert sp.best >= start - 1e-12
     assert exact - sp.best < 0.5 * (exact - start) or exact - sp.best < 1e-4
+
+
+def _fd_bound(P, st, mod, chain, splits=None):
+    """The bound at fixed duals and masks after mod(Q): intermediate bounds held (chain False) or
+    redone by interval propagation over the (perturbed) ellipsoid (chain True)."""
+    Q = nw.Problem.__new__(nw.Problem)
+    Q.__dict__.update(P.__dict__)
+    Q.W = [None if w is None else w.copy() for w in P.W]
+    Q.b = [None if w is None else w.copy() for w in P.b]
+    Q.lo = [v.copy() for v in P.lo]
+    Q.hi = [v.copy() for v in P.hi]
+    mod(Q)
+    if chain:
+        lh, uh, lo, hi = nw.ibp(Q.W[1:Q.n], Q.b[1:Q.n], Q.lo[0], Q.hi[0], splits, ball=True)
+        Q.lhat, Q.uhat, Q.lo, Q.hi = lh, uh, lo, hi
+    st2 = du.DualState(st.alpha, st.beta0, st.beta1, [[] for _ in range(P.n)])
+    for k in range(1, P.n):
+        for sl in st.slots[k]:
+            du.add_slot(Q, st2, k, sl.I, beta=sl.beta)
+    return du.evaluate(Q, st2)[0]
+
+
+@pytest.mark.parametrize("name,chain", [("mlp_4_5_5_1", False), ("mlp_4_5_5_1", True), ("small_conv", False),
+                                        ("small_conv", True)])
+def test_input_gradients_over_the_ellipsoid_match_finite_differences(name, chain):
+    """The envelope gradient over the ellipsoid (its endpoints parameterise c and e), with the
+    intermediate bounds held or carried through interval propagation (layer 1 over the
+    ellipsoid), against central differences; it differs from the box formula."""
+    from oracle import envelope as ev
+    prob = _ball_prob(name, 4)
+    P = nw.problems(prob)[0]
+    s = AS.ActiveSet(P, AS.Options(bigm_iters=30, as_iters=30, omega=10, max_cuts=3)).step(60)
+    g = ev.chain_gradient(P, s.st) if chain else ev.envelope_gradient(P, s.st)
+    h = 1e-6
+    rng = synth.SplitMix64(3)
+
+    def fd(mod):
+        return (_fd_bound(P, s.st, lambda Q: mod(Q, h), chain) - _fd_bound(P, s.st, lambda Q: mod(Q, -h), chain)) / (2 * h)
+    for j in range(min(6, P.widths[0])):
+        def ml(Q, d):
+            Q.lo[0][j] += d
+
+        def mh(Q, d):
+            Q.hi[0][j] += d
+        assert fd(ml) == pytest.approx(g["dlo0"][j], rel=1e-5, abs=1e-7)
+        assert fd(mh) == pytest.approx(g["dhi0"][j], rel=1e-5, abs=1e-7)
+    for k in range(1, P.n + 1):
+        for _ in range(4):
+            i = int(rng.integers(1, 0, P.W[k].shape[0] - 1)[0])
+            j = int(rng.integers(1, 0, P.W[k].shape[1] - 1)[0])
+            if abs(P.W[k][i, j]) < 10 * h:
+                continue
+
+            def mw(Q, d):
+                Q.W[k][i, j] += d
+            assert fd(mw) == pytest.approx(g["dW"][k][i, j], rel=1e-5, abs=1e-7)
+    P.ball = False
+    try:
+        gb = ev.envelope_gradient(P, s.st)
+    finally:
+        P.ball = True
+    assert np.abs(gb["dlo0"] - g["dlo0"]).max() > 1e-4
