@@ -97,8 +97,9 @@ typedef struct as_options {
                           * linear minimisation over the input set): layer 1's interval bounds are its exact
                           * range W c + b -+ |W D|_2 and x_0* = c + e^2 f_0 / |e f_0|_2 (Saddle Point: the
                           * same vertex, and its primal initialisation retracts x_0 radially into the
-                          * ellipsoid); the BF16 form takes x_0* into its operand planes. as_bound_backward
-                          * gives dW, db only (dlo, dhi or the chain form: AS_ERR_STATE).
+                          * ellipsoid); the BF16 form takes x_0* into its operand planes. The gradients of
+                          * as_bound_backward(_ibp) with respect to x_lo, x_hi treat them as giving c and
+                          * e (the value -f_0 c - |e f_0| and layer 1's interval above).
                           * 0 (default): the box itself.                                        */
 } as_options;
 

@@ -45,7 +45,12 @@ __device__ __forceinline__ float wgrad_term(const DNet& net, const DState& st, c
     }
     if (Ah) {   // interval propagation: lhat = W+ l + W- u + b, uhat = W+ u + W- l + b
         const float lo = st.lo[xo], hi = st.hi[xo];
-        g += Ah[h] * (w >= 0.f ? lo : hi) + Uh[h] * (w >= 0.f ? hi : lo);
+        if (net.ball && L.in_off == 0) {   // over the ellipsoid: W c + b -+ |W_i o e|
+            const float c = 0.5f * (lo + hi), e = 0.5f * (hi - lo), r = st.brad[h];
+            g += (Ah[h] + Uh[h]) * c + (r > 0.f ? (Uh[h] - Ah[h]) * w * e * e / r : 0.f);
+        } else {
+            g += Ah[h] * (w >= 0.f ? lo : hi) + Uh[h] * (w >= 0.f ? hi : lo);
+        }
     }
     return g;
 }
@@ -176,7 +181,12 @@ __global__ void k_grad_box(DNet net, DState st, GradCtx gc, float* dlo, float* d
     }
     const float f0 = st.fval[xo];
     const float x = st.xval[xo];
-    if (lo == hi) {
+    if (net.ball) {   // value -f c - |e f| over the ellipsoid, c = (l + u) / 2, e = (u - l) / 2
+        const double nrm = st.bnrm[s];
+        const float d = nrm > 0.0 ? (float)(0.5 * (0.5 * ((double)hi - lo)) * f0 * f0 / nrm) : 0.f;
+        al += -0.5f * f0 + d;
+        ah += -0.5f * f0 - d;
+    } else if (lo == hi) {
         al += -0.5f * f0;
         ah += -0.5f * f0;
     } else if (x == hi) {
@@ -222,7 +232,12 @@ __global__ void k_post_adj(DNet net, DState st, int li, GradCtx gc, float* Lb, f
         });
     }
     const float f = st.fval[xo], x = st.xval[xo];
-    if (lo == hi) {
+    if (net.ball && li == 0) {   // value -f c - |e f| over the ellipsoid (as k_grad_box)
+        const double nrm = st.bnrm[s];
+        const float d = nrm > 0.0 ? (float)(0.5 * (0.5 * ((double)hi - lo)) * f * f / nrm) : 0.f;
+        al += -0.5f * f + d;
+        ah += -0.5f * f - d;
+    } else if (lo == hi) {
         al += -0.5f * f;
         ah += -0.5f * f;
     } else if (x == hi) {
@@ -259,13 +274,25 @@ __global__ void k_hat_adj(DNet net, DState st, int li, const signed char* splits
 
 // Back through lhat = W+ l + W- u + b, uhat = W+ u + W- l + b of layer li: adds W+^T Ah + W-^T Uh
 // to Lb and W-^T Ah + W+^T Uh to Ub of its inputs (one thread per input, no atomics).
-__global__ void k_prop_adj(DNet net, int li, const float* Ah, const float* Uh, float* Lb, float* Ub) {
+__global__ void k_prop_adj(DNet net, DState st, int li, const float* Ah, const float* Uh, float* Lb, float* Ub) {
     const DLayer& L = net.L[li];
     const int u = blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= net.S * L.n_in) return;
     const int s = u / L.n_in, j = u - s * L.n_in;
     const size_t rb = (size_t)s * net.NH + L.h_out;
     float al = 0.f, au = 0.f;
+    if (net.ball && li == 0) {
+        // over the ellipsoid lhat, uhat = W c + b -+ r, r_i = |W_i o e|: d/dc = W, dr_i/de_j = W^2 e_j / r_i;
+        // d/dl = (d/dc - d/de) / 2, d/du = (d/dc + d/de) / 2
+        const size_t xo = (size_t)s * net.NT + L.in_off + j;
+        const float e = 0.5f * (st.hi[xo] - st.lo[xo]);
+        col_walk(L, j, [&](int i, float w) {
+            const float a = Ah[rb + i], b = Uh[rb + i], r = st.brad[rb + i];
+            const float dc = w * (a + b), de = r > 0.f ? w * w * e / r * (b - a) : 0.f;
+            al += 0.5f * (dc - de);
+            au += 0.5f * (dc + de);
+        });
+    } else
     col_walk(L, j, [&](int i, float w) {
         const float a = Ah[rb + i], b = Uh[rb + i];
         if (w >= 0.f) { al += w * a; au += w * b; }

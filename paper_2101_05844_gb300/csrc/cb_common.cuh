@@ -93,6 +93,8 @@ struct DState {
     float *xin;                      // [S][XT] input records of each layer, one float2 per position:
                                      // {x*, p_b bits | q_b bits << 8}
     float *lz;                       // [S][NH] sum_j W_ij Lcheck_ij (the all-ones mask's lambda)
+    float *brad;                     // [S][NH] ellipsoid inputs: |W_i o e|_2 of layer 1's rows
+    double *bnrm;                    // [S] ellipsoid inputs: |e o f_0|_2 of the last x_0* evaluation
     float *uz;                       // [S][NH] sum_j W_ij Ucheck_ij (kappa - b of a z = 0 row whose
                                      // inputs are all interior: the mask is then empty but for
                                      // fixed inputs, where Lcheck = Ucheck)

@@ -104,6 +104,7 @@ __global__ void k_ibp(DNet net, DState st, int li, const signed char* splits) {
     if (lane == 0) {
         if (ell) {   // the exact range of W_i x + b over {sum ((x - c) / e)^2 <= 1}: W_i c + b -+ |W_i D|
             const double r = sqrt(c);
+            st.brad[(size_t)s * net.NH + L.h_out + i] = (float)r;
             c = a + r;
             a = a - r;
         }

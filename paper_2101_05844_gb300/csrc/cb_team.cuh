@@ -433,7 +433,10 @@ __global__ void __launch_bounds__(CB_BALL_THREADS) k_ball_x0(DNet net, DState st
     __syncthreads();
     const double nrm = sqrt(red[0][0]);
     const float inv = nrm > 0.0 ? (float)(1.0 / nrm) : 0.f;
-    if (threadIdx.x == 0) st.terms[base] = -red[1][0] - nrm;
+    if (threadIdx.x == 0) {
+        st.terms[base] = -red[1][0] - nrm;
+        st.bnrm[s] = nrm;
+    }
     float2* rec = reinterpret_cast<float2*>(st.xin + (size_t)s * net.XT + L.xo);
     for (int j = threadIdx.x; j < L.n_in; j += CB_BALL_THREADS) {
         const size_t xo = base + j;

@@ -496,6 +496,8 @@ static int alloc_state(as_ctx* c) {
         st.zcur = o.take<uint8_t>(NHS);
         st.lz = o.take<float>(NHS);
         st.uz = o.take<float>(NHS);
+        st.brad = o.take<float>(NHS);
+        st.bnrm = o.take<double>(S);
         st.efix = o.take<uint8_t>(NTS);
         st.arow = o.take<float>(NHS);
         st.nfree = o.take<int>(NHS);

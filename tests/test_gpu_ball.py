@@ -170,7 +170,12 @@ def test_free_running_active_set_matches_oracle(name, S, kw, iters):
         assert best[s] <= m + 1e-5
 
 
-def test_backward_gives_dW_db_and_refuses_the_box_gradients():
+@pytest.mark.parametrize("chain", [False, True])
+def test_backward_over_the_ellipsoid_matches_oracle(chain):
+    """dW, db, dlo, dhi of the bound over the ellipsoid against the oracle's envelope gradient (the
+    box endpoints give c and e), with the intermediate bounds held (caller bounds) or carried
+    through interval propagation (the context's own bounds, layer 1 over the ellipsoid): 1e-4
+    relative, as for the box."""
     name, S = "mlp_5_7_6_3", 3
     prob = _ball(name, S)
     Ps0 = nw.problems(prob)
@@ -179,27 +184,28 @@ def test_backward_gives_dW_db_and_refuses_the_box_gradients():
                                     split_hidden(uh[s].astype(np.float64), Ps0[0].widths)[1:])
                                    for s in range(S)])
     kw = dict(bigm_iters=2, as_iters=30, omega=3, max_cuts=4)
-    ctx = binding.context_for(prob, _opts(**kw), bounds=(lh, uh))
+    ctx = binding.context_for(prob, _opts(**kw), bounds=None if chain else (lh, uh))
     solvers = draw_state(Ps, ctx, kw, it=9, nslots=4, seed=7, interior0=True)
     gb = synth.SplitMix64(3).uniform(S) + 0.5
     net = prob["net"]
     dW = [np.zeros_like(L["W"]) for L in net]
     db = [np.zeros_like(L["b"]) for L in net]
-    ctx.backward(gb, dW, db)
+    dlo, dhi = np.zeros_like(prob["lo"]), np.zeros_like(prob["hi"])
+    ctx.backward(gb, dW, db, dlo, dhi, through_bounds=chain)
     refW = [np.zeros(L["W"].shape) for L in net]
     refb = [np.zeros(L["b"].shape) for L in net]
     for s, sv in enumerate(solvers):
-        g = ev.envelope_gradient(sv.P, sv.st)
+        g = ev.chain_gradient(sv.P, sv.st) if chain else ev.envelope_gradient(sv.P, sv.st)
         for k in range(1, len(net)):
             refW[k - 1] += gb[s] * g["dW"][k]
             refb[k - 1] += gb[s] * g["db"][k]
         refW[-1] += gb[s] * np.outer(prob["C"][s], g["dW"][sv.P.n][0])
         refb[-1] += gb[s] * prob["C"][s]
+        np.testing.assert_allclose(dlo[s], gb[s] * g["dlo0"], rtol=1e-4, atol=1e-5)
+        np.testing.assert_allclose(dhi[s], gb[s] * g["dhi0"], rtol=1e-4, atol=1e-5)
     for k in range(len(net)):
         np.testing.assert_allclose(dW[k], refW[k], rtol=1e-4, atol=1e-5)
         np.testing.assert_allclose(db[k], refb[k], rtol=1e-4, atol=1e-5)
-    with pytest.raises(binding.CBError):
-        ctx.backward(gb, dW, db, np.zeros_like(prob["lo"]), None)
 
 
 @pytest.mark.parametrize("name,S,kw", [
