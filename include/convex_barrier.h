@@ -349,6 +349,19 @@ void as_bab_default_options(as_bab_options* opt);
 int as_bab(const as_net* net, const float* x_lo, const float* x_hi, const float* c, const as_bab_options* opt,
            as_bab_result* res, float* x_best, void* stream);
 
+/* Whole-state export and import (warm starts; as_get_state / as_set_state over every buffer a
+ * context needs to go on iterating): the iteration counters, alpha, beta_0, beta_1, the Adam
+ * moments, the slots' betas, moments and snapshots (Active Set), or the primal iterate, sufficient
+ * statistics and price caps (Saddle Point, once sp_step has started). Host memory of
+ * as_export_size bytes; the import checks each buffer's size against the context (AS_ERR_SHAPE for
+ * another net, batch size or max_cuts; AS_ERR_ARG for a blob this function did not write) and
+ * expects the batch (boxes, properties, bounds) to be loaded already. Lambda and kappa of the slots
+ * are recomputed in float32 from the imported snapshots, so an imported context continues the
+ * exporting one's iterations up to that rounding. */
+int as_export_size(as_ctx* ctx, long long* nbytes);
+int as_export_state(as_ctx* ctx, void* dst);
+int as_import_state(as_ctx* ctx, const void* src);
+
 /* The team-size targets of the float32 Active Set passes in effect (threads a layer segment of
  * the row and of the col pass aims for; the lanes per neuron follow from them): the defaults,
  * what as_options.autotune chose, or the values of the environment variables

@@ -27,7 +27,8 @@ MAX_LAYERS, MAX_CUTS = 10, 8
 EXPORTS = ["as_default_options", "as_init", "as_reset", "as_step", "sp_step", "as_bound",
            "as_bound_backward", "as_state_size", "as_get_state", "as_set_state", "as_launch_count",
            "as_kernel_times", "as_destroy", "as_last_error", "as_ibp_noalloc", "as_gemm_bf16",
-           "as_team_targets", "as_intermediate_bounds", "as_bab", "as_bab_default_options", "as_bound_backward_ibp"]
+           "as_team_targets", "as_intermediate_bounds", "as_bab", "as_bab_default_options", "as_bound_backward_ibp",
+           "as_export_size", "as_export_state", "as_import_state"]
 KERNELS = ["as_colA", "as_rowB", "reduce", "sp_colA", "sp_rowB", "sp_colC", "spi_row", "spi_col", "tc_col",
            "tc_row", "slot_sums", "ball_x0"]
 
@@ -115,6 +116,12 @@ def lib() -> ct.CDLL:
                                              ct.POINTER(Options), ct.c_longlong, ct.c_void_p, ct.c_void_p,
                                              ct.c_void_p]
         L.as_intermediate_bounds.restype = ct.c_int
+        L.as_export_size.argtypes = [ct.c_void_p, ct.POINTER(ct.c_longlong)]
+        L.as_export_size.restype = ct.c_int
+        L.as_export_state.argtypes = [ct.c_void_p, ct.c_void_p]
+        L.as_export_state.restype = ct.c_int
+        L.as_import_state.argtypes = [ct.c_void_p, ct.c_void_p]
+        L.as_import_state.restype = ct.c_int
         L.as_bab_default_options.argtypes = [ct.POINTER(BabOptions)]
         L.as_bab_default_options.restype = None
         L.as_bab.argtypes = [ct.POINTER(Net), ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.POINTER(BabOptions),
@@ -260,6 +267,18 @@ class Context:
         fn = lib().as_bound_backward_ibp if through_bounds else lib().as_bound_backward
         self._check(fn(self.h, _ptr(g), ct.cast(pw, ct.c_void_p) if pw else None,
                        ct.cast(pb, ct.c_void_p) if pb else None, _ptr(dlo), _ptr(dhi)))
+
+    def export_state(self) -> np.ndarray:
+        """as_export_state: the whole iteration state as one byte blob (host)."""
+        n = ct.c_longlong()
+        self._check(lib().as_export_size(self.h, ct.byref(n)))
+        out = np.zeros(n.value, np.uint8)
+        self._check(lib().as_export_state(self.h, _ptr(out)))
+        return out
+
+    def import_state(self, blob: np.ndarray):
+        """as_import_state: continue from a blob of export_state (same net, batch size, max_cuts)."""
+        self._check(lib().as_import_state(self.h, _ptr(np.ascontiguousarray(blob, np.uint8))))
 
     def state_size(self, which: int) -> int:
         n = ct.c_longlong()

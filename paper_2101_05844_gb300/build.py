@@ -7,13 +7,13 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRCS = [os.path.join(HERE, "csrc", f) for f in ("convex_barrier.cu", "noalloc.cu", "tc_gemm.cu",
-                                                           "ibounds.cu", "bab.cu")]
+                                                           "ibounds.cu", "bab.cu", "state.cu")]
 LIB = os.path.join(HERE, "libconvex_barrier.so")
 OBJDIR = os.path.join(HERE, "_build")
 DEPS = [os.path.join(HERE, "csrc", f) for f in
         ("convex_barrier.cu", "cb_common.cuh", "cb_kernels.cuh", "cb_backward.cuh", "cb_team.cuh",
          "cb_host_extra.inc", "noalloc.cu", "cb_walk.cuh", "cb_tc.cuh", "tc_gemm.cu", "cb_bf16.inc",
-         "ibounds.cu", "bab.cu")] + \
+         "ibounds.cu", "bab.cu", "state.cu")] + \
     [os.path.join(HERE, "..", "include", "convex_barrier.h")]
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
