@@ -3,6 +3,14 @@
 Every step of the method runs in the CUDA library; this module only converts arrays to pointers.
 Arrays may be numpy arrays (host memory) or torch tensors (host or CUDA). Loading fails loudly
 when the library has not been built: there is no CPU fallback.
+
+  Context                 as_init .. as_destroy: as_step, sp_step, bound, backward (fixed bounds or
+                          through interval propagation), get/set_state, export/import_state
+  intermediate_bounds     as_intermediate_bounds (App. E)
+  bab, bab_default_options  as_bab: branch and bound with stratified bounding (Sec. 6.2)
+  ibp_noalloc             as_ibp_noalloc
+  gemm_bf16               as_gemm_bf16
+  default_options(input_l2=1, precision=16, ...)  the ellipsoid input set, the BF16 form
 """
 from __future__ import annotations
 
