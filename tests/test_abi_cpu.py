@@ -34,28 +34,29 @@ def test_default_options_are_the_papers(built):
     assert (o.omega, o.vars_per_add, o.max_cuts, o.sp_gamma0, o.sp_init_steps) == (450, 2, 7, 10.0, 100)
 
 
+STRUCTS = [("as_options", binding.Options), ("as_layer", binding.Layer), ("as_net", binding.Net),
+           ("as_bab_options", binding.BabOptions), ("as_bab_result", binding.BabResult)]
+
+
 def test_struct_layouts_match_header(tmp_path):
-    """sizeof and field offsets of the ABI structs, from the C compiler, equal the binding's."""
+    """sizeof and field offsets of every ABI struct, from the C compiler, equal the binding's."""
     import subprocess
     src = tmp_path / "probe.c"
-    fields_o = [f for f, _ in binding.Options._fields_]
-    fields_l = [f for f, _ in binding.Layer._fields_]
     body = ['#include <stdio.h>', '#include <stddef.h>', '#include "convex_barrier.h"', 'int main(void){']
-    body.append('printf("%zu %zu\\n", sizeof(as_options), sizeof(as_layer));')
-    for f in fields_o:
-        body.append(f'printf("%zu\\n", offsetof(as_options, {f}));')
-    for f in fields_l:
-        body.append(f'printf("%zu\\n", offsetof(as_layer, {f}));')
+    for cname, py in STRUCTS:
+        body.append(f'printf("%zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            body.append(f'printf("%zu\\n", offsetof({cname}, {f}));')
     body.append('return 0;}')
     src.write_text("\n".join(body))
     exe = tmp_path / "probe"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
-    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
-    so, sl = int(out[0]), int(out[1])
-    assert so == ct.sizeof(binding.Options) and sl == ct.sizeof(binding.Layer)
-    offs = [int(v) for v in out[2:]]
-    assert offs[:len(fields_o)] == [getattr(binding.Options, f).offset for f in fields_o]
-    assert offs[len(fields_o):] == [getattr(binding.Layer, f).offset for f in fields_l]
+    out = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    expect = []
+    for _, py in STRUCTS:
+        expect.append(ct.sizeof(py))
+        expect += [getattr(py, f).offset for f, _ in py._fields_]
+    assert out == expect
 
 
 def test_generator_is_deterministic_and_seeded():
