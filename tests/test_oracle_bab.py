@@ -116,3 +116,33 @@ def test_unsplittable_domains_are_bounded_again_from_their_own_duals():
     assert once["status"] == bab.UNKNOWN and once["bounded"] == 2
     assert again["status"] == bab.VERIFIED and 2 < again["bounded"] <= 10
     assert 0 < again["lower"] <= m_t + 1e-9
+
+
+@pytest.mark.parametrize("seed,shift", [(3, False), (2, True)])
+def test_conv_net_verdicts_agree_with_sampled_points(seed, shift):
+    """The small conv net (every layer kind) with a three-output property row: a falsified verdict
+    comes with a point of the box whose float64 value is negative (seed 3 after branching). With
+    the property moved below a valid lower bound of a long solve (sampled values are no guide in
+    72 input dimensions: the search finds points far below them), it is verified."""
+    prob = synth.problem("small_conv", S=1, seed=seed)
+    net, lo, hi, c = prob["net"], prob["lo"][0], prob["hi"][0], prob["C"][0].astype(np.float64)
+    dense = nw.dense_layers(net)
+    rng = synth.SplitMix64(seed)
+    X = lo + rng.uniform(3000 * lo.size).reshape(3000, lo.size) * (hi - lo)
+    vals = np.array([c @ bab.forward(dense, x) for x in X])
+    if shift:
+        P = nw.Problem(net, lo, hi, c, dense=dense)
+        lb = AS.solve(P, AS.Options(bigm_iters=300, as_iters=300, omega=60, max_cuts=3))[1]
+        t = lb - 0.02 * abs(lb)
+        net = [dict(L) for L in net]
+        net[-1]["b"] = (net[-1]["b"].astype(np.float64) - t * c / (c @ c)).astype(np.float32)
+        dense = nw.dense_layers(net)
+        vals = np.array([c @ bab.forward(dense, x) for x in X])
+    res = bab.BaB(net, lo, hi, c, _opts(max_domains=200)).run()
+    if shift:
+        assert res["status"] == bab.VERIFIED and 0 < res["lower"] <= vals.min()
+    else:
+        assert res["status"] == bab.FALSIFIED and res["bounded"] > 2
+        x = res["x"]
+        assert np.all(x >= lo) and np.all(x <= hi) and c @ bab.forward(dense, x) < 0
+        assert res["lower"] <= vals.min()
