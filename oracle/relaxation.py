@@ -7,21 +7,25 @@ post-activation bounds l_{k-1}, u_{k-1}:
 and eq. (3), the linear-time oracle for the most violated constraint of the exponential family:
     I[i, j] = 1  iff  ((1 - z[i]) * Lcheck[i, j] + z[i] * Ucheck[i, j] - x[j]) * W[i, j] >= 0.
 
-Where floating point decides the bit, the decision is taken in float32, the precision of the
-paper's implementation and of the CUDA kernels, in the equivalent threshold form
-    W = 0 or l = u                   -> 1
-    W > 0  -> z >= (x - l) / (u - l)
-    W < 0  -> z >= (u - x) / (u - l)
-with the quotient rounded to nearest in float32 (each operation rounded). It equals the real-number
-rule of eq. (3) whenever z is 0 or 1 and x is l or u (every Active Set iterate), and whenever z is not
-within one float32 ulp of the quotient. When l = u the variable is fixed, x = l = u, and the
-coefficient is exactly zero, so the bit is 1. `mask_exact` evaluates eq. (3) in rational arithmetic.
+`mask` decides eq. (3) exactly for the given floating-point values (no rounding enters the
+decision). Multiplying out the sign of W (an exact rearrangement):
+    W = 0  -> 1 (the coefficient is 0)
+    W > 0  -> a = z (u - l) - (x - l) >= 0
+    W < 0  -> a = z (u - l) - (u - x) >= 0
+The sign of a is exact by comparisons alone where z is 0 or 1, where u = l or where the
+subtrahend vanishes (every Active Set iterate and every fixed input); elsewhere a float64
+evaluation decides when it clears its rounding-error bound, and rational arithmetic decides the
+few entries that it does not clear. `mask_literal` evaluates the printed formula in float64 (its
+rounding flips bits where the coefficient is exactly 0), `mask_exact` in rational arithmetic entry
+by entry (slow; small inputs only).
 """
 from __future__ import annotations
 
 from fractions import Fraction
 
 import numpy as np
+
+_EPS = 2.0 ** -53
 
 
 def interval_matrices(W: np.ndarray, l: np.ndarray, u: np.ndarray):
@@ -33,22 +37,52 @@ def interval_matrices(W: np.ndarray, l: np.ndarray, u: np.ndarray):
 
 
 def mask(W, l, u, x, z) -> np.ndarray:
-    """Eq. (3) with float32 decisions: bool [n_k, n_{k-1}]."""
-    l32 = np.asarray(l, np.float32)
-    u32 = np.asarray(u, np.float32)
-    x32 = np.asarray(x, np.float32)
-    z32 = np.asarray(z, np.float32)
-    fixed = l32 == u32
-    with np.errstate(divide="ignore", invalid="ignore"):
-        den = np.where(fixed, np.float32(1), u32 - l32)
-        tp = (x32 - l32) / den
-        tn = (u32 - x32) / den
-    tp = tp.astype(np.float32)
-    tn = tn.astype(np.float32)
-    zc = z32[:, None]
-    I = np.where(W > 0, zc >= tp[None, :], zc >= tn[None, :])
-    I = I | (W == 0) | fixed[None, :]
-    return I
+    """Eq. (3), decided exactly: bool [n_k, n_{k-1}]."""
+    W = np.asarray(W, np.float64)
+    l = np.asarray(l, np.float64)
+    u = np.asarray(u, np.float64)
+    x = np.asarray(x, np.float64)
+    z = np.asarray(z, np.float64)
+    n, m = W.shape
+    pos = W > 0
+    zc = np.broadcast_to(z[:, None], (n, m))
+    # subtrahend s = x - l (W > 0) or u - x (W < 0); its sign by comparison
+    s_pos = np.where(pos, x[None, :] > l[None, :], u[None, :] > x[None, :])    # s > 0
+    s_neg = np.where(pos, x[None, :] < l[None, :], u[None, :] < x[None, :])    # s < 0
+    s_zero = ~(s_pos | s_neg)
+    d_zero = np.broadcast_to((u == l)[None, :], (n, m))
+    # z = 0: a = -s; z = 1: a = (u - l) - s = u - x (W > 0) or x - l (W < 0)
+    a_one_ge = np.where(pos, u[None, :] >= x[None, :], x[None, :] >= l[None, :])
+    out = np.empty((n, m), bool)
+    decided = np.zeros((n, m), bool)
+    # a = z (u - l) - s with u - l = 0: a = -s
+    case = d_zero
+    out[case] = ~s_pos[case]
+    decided |= case
+    case = ~decided & (zc == 0.0)
+    out[case] = ~s_pos[case]
+    decided |= case
+    case = ~decided & (zc == 1.0)
+    out[case] = a_one_ge[case]
+    decided |= case
+    # s = 0: a = z (u - l), with u - l > 0 here: its sign is the sign of z
+    case = ~decided & s_zero
+    out[case] = zc[case] >= 0.0
+    decided |= case
+    rest = ~decided
+    if rest.any():
+        d = (u - l)[None, :]
+        s = np.where(pos, x[None, :] - l[None, :], u[None, :] - x[None, :])
+        a = zc * d - s
+        tol = 8.0 * _EPS * (np.abs(zc) * np.abs(d) + np.abs(s)) + 1e-300
+        sure = rest & (np.abs(a) > tol)
+        out[sure] = a[sure] >= 0.0
+        for i, j in zip(*np.nonzero(rest & ~sure)):
+            zi, lj, uj, xj = (Fraction(float(v)) for v in (z[i], l[j], u[j], x[j]))
+            sj = xj - lj if W[i, j] > 0 else uj - xj
+            out[i, j] = zi * (uj - lj) - sj >= 0
+    out |= W == 0
+    return out
 
 
 def mask_literal(W, l, u, x, z) -> np.ndarray:

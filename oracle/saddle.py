@@ -112,9 +112,10 @@ class SaddlePoint:
     def decision_margin(self, sums_only: bool = False) -> float:
         """Smallest gap, over every decision the next iteration takes, between the deciding value
         and its threshold: the sign of f (x_bar), of G (z_bar), of xhat - x (alpha_bar), the
-        top-two gap and the sign of the conditional-gradient choice, and |z - tau| of the float32
-        mask thresholds of ambiguous inputs. sums_only: only the decisions taken on sums (f,
-        xhat - x, the choice), the ones whose value depends on the summation's precision."""
+        top-two gap and the sign of the conditional-gradient choice, and |z - tau| of the mask
+        thresholds tau = (x - l) / (u - l) (W > 0), (u - x) / (u - l) (W < 0) of ambiguous
+        inputs. sums_only: only the decisions taken on sums (f, xhat - x, the choice), the ones
+        whose value depends on the summation's precision."""
         P, n = self.P, self.P.n
         m = min(np.abs(fk).min() for fk in self.coefficients())
         for k in range(1, n):
@@ -129,17 +130,15 @@ class SaddlePoint:
             vI = np.where(degenerate_rows(W, I, P.lo[k - 1], P.hi[k - 1]), -np.inf, vI)
             V = np.sort(np.stack([x - z * P.uhat[k], x - xhat + (1 - z) * P.lhat[k], vI]), axis=0)
             m = min(m, (V[2] - V[1]).min(), np.abs(V[2]).min())
-            l32, u32 = P.lo[k - 1].astype(np.float32), P.hi[k - 1].astype(np.float32)
-            amb = l32 != u32
+            lo, hi = P.lo[k - 1], P.hi[k - 1]
+            amb = lo != hi
             if amb.any() and not sums_only:
-                x32 = xp.astype(np.float32)[amb]
-                den = (u32 - l32)[amb]
-                tp = ((x32 - l32[amb]) / den).astype(np.float64)
-                tn = ((u32[amb] - x32) / den).astype(np.float64)
-                zz = z.astype(np.float32).astype(np.float64)[:, None]
+                den = (hi - lo)[amb]
+                tp = (xp[amb] - lo[amb]) / den
+                tn = (hi[amb] - xp[amb]) / den
                 Wa = W[:, amb]
-                dp = np.where(Wa > 0, np.abs(zz - tp[None, :]), np.inf)
-                dn = np.where(Wa < 0, np.abs(zz - tn[None, :]), np.inf)
+                dp = np.where(Wa > 0, np.abs(z[:, None] - tp[None, :]), np.inf)
+                dn = np.where(Wa < 0, np.abs(z[:, None] - tn[None, :]), np.inf)
                 m = min(m, dp.min(), dn.min())
         return float(m)
 

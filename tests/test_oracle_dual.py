@@ -140,12 +140,14 @@ def test_supergradient_is_directional_derivative(name):
 
 
 def test_weak_duality_against_sampled_outputs():
+    """Every bound (Big-M, Active Set, the best over the run) is at most the network's minimum over
+    10^6 uniform samples of the box and all its 2^8 vertices (weak duality, Sec. 3)."""
     prob = synth.problem("mlp_tiny", seed=7)
     P = nw.problems(prob)[0]
     opt = AS.Options(bigm_iters=60, as_iters=140, omega=40, max_cuts=5)
     fin, best, s = AS.solve(P, opt)
     assert max(s.trace + [fin]) == best
-    m = sample_min_output(P, 100_000, seed=3)
+    m = sample_min_output(P, 1_000_000, seed=3)
     assert best <= m + 1e-9
     assert best > P.ibp_output_bound()       # the solver tightened the interval bound
 
