@@ -251,13 +251,15 @@ const char* as_last_error(as_ctx* ctx);
  *  splits:     hidden vector of int8 ReLU splits as for as_init, device memory, or NULL.
  *  lhat, uhat: outputs, hidden vectors [S][n_1 + ... + n_{n-1}] of float, device memory.
  *  stream:     cudaStream_t the kernels are enqueued on; the call does not synchronise.
+ * Every pointer must be memory of the current device (or managed memory).
  * Returns AS_ERR_SCRATCH when 4 x S x (widest hidden layer) exceeds AS_NOALLOC_SCRATCH_FLOATS,
- * AS_ERR_ARG for a null or host pointer, AS_ERR_SHAPE for inconsistent layers.
- * The first call on each device looks up the scratch array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before any stream
- * capture. Every call on a device shares the one scratch array (nothing in it needs to start at
- * zero: each call writes every entry it reads), so calls whose kernels overlap on the GPU race;
- * issue them on one stream or otherwise order them. */
+ * AS_ERR_ARG for a null or host pointer or memory of another device, AS_ERR_SHAPE for
+ * inconsistent layers. Each call looks up the scratch array's device address on the current
+ * device (cudaGetSymbolAddress; a device reset therefore leaves no stale address behind); the
+ * first call on a device also loads the library's device code there, so make it before any
+ * stream capture. Every call on a device shares the one scratch array (nothing in it needs to
+ * start at zero: each call writes every entry it reads), so calls whose kernels overlap on the
+ * GPU race; issue them on one stream or otherwise order them. */
 #define AS_NOALLOC_SCRATCH_FLOATS (1u << 22)
 int as_ibp_noalloc(const as_net* net, int S, const float* x_lo, const float* x_hi,
                    const signed char* splits, float* lhat, float* uhat, void* stream);
@@ -353,11 +355,13 @@ int as_bab(const as_net* net, const float* x_lo, const float* x_hi, const float*
  * context needs to go on iterating): the iteration counters, alpha, beta_0, beta_1, the Adam
  * moments, the slots' betas, moments and snapshots (Active Set), or the primal iterate, sufficient
  * statistics and price caps (Saddle Point, once sp_step has started). Host memory of
- * as_export_size bytes; the import checks each buffer's size against the context (AS_ERR_SHAPE for
- * another net, batch size or max_cuts; AS_ERR_ARG for a blob this function did not write) and
- * expects the batch (boxes, properties, bounds) to be loaded already. Lambda and kappa of the slots
- * are recomputed in float32 from the imported snapshots, so an imported context continues the
- * exporting one's iterations up to that rounding. */
+ * as_export_size bytes; the import checks every buffer's size against the context before it
+ * writes any (AS_ERR_SHAPE for another net, batch size or max_cuts, with the context left as it
+ * was; AS_ERR_ARG for a blob this function did not write) and expects the batch (boxes,
+ * properties, bounds) to be loaded already. The context takes the blob's mode: an Active Set blob
+ * puts it in Active Set mode, a Saddle Point blob in Saddle Point mode (its initialisation
+ * skipped). Lambda and kappa of the slots are recomputed in float32 from the imported snapshots,
+ * so an imported context continues the exporting one's iterations up to that rounding. */
 int as_export_size(as_ctx* ctx, long long* nbytes);
 int as_export_state(as_ctx* ctx, void* dst);
 int as_import_state(as_ctx* ctx, const void* src);

@@ -314,68 +314,4 @@ __global__ void k_box_out(DNet net, GradCtx gc, const float* Lb, const float* Ub
     if (dhi) dhi[u] += (float)(gc.gb[s] * (double)Ub[xo]);
 }
 
-__device__ __forceinline__ void slot_sums_body(const DNet& net, const DState& st, const Segs& sg, int nadd, int bo,
-                                               int only);
-
-// lambda, kappa of every filled slot from the snapshot bits (after the caller replaced them).
-__global__ void __launch_bounds__(CB_THREADS) k_slot_sums(DNet net, DState st, Segs sg, int nadd, int bo) {
-    slot_sums_body(net, st, sg, nadd, bo, -1);
-}
-
-// lambda, kappa in float32 of the slot an Active Set iteration just added (BF16 form: the
-// iteration took them from its bf16 products); returns at once after other iterations.
-__global__ void __launch_bounds__(CB_THREADS) k_slot_sums_after_add(DNet net, DState st, DSched sc, Segs sg) {
-    const int it = st.ctr[0] - 1;   // the iteration that just ended
-    if (it < sc.TM) return;
-    const int b = cb_slot_at(it - sc.TM, sc);
-    if (b < 0) return;
-    const int nadd = cb_additions_before(it - sc.TM + 1, sc);
-    slot_sums_body(net, st, sg, nadd, nadd & 1, b);
-}
-
-// only >= 0: that slot alone.
-__device__ __forceinline__ void slot_sums_body(const DNet& net, const DState& st, const Segs& sg, int nadd, int bo,
-                                               int only) {
-    const int q = seg_of(sg, blockIdx.x);
-    const DLayer& L = net.L[sg.layer[q]];
-    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int u = (blockIdx.x - sg.start[q]) * CB_WARPS + wib;
-    if (u >= net.S * L.n_out) return;
-    const int s = u / L.n_out, i = u - s * L.n_out;
-    const int nsl = min(nadd, st.caps[s]);
-    const size_t NT = net.NT, NH = net.NH;
-    const size_t h = (size_t)s * NH + L.h_out + i;
-    const unsigned zs = st.zsnap[bo][h];
-    const size_t ib = (size_t)s * NT + L.in_off;
-    float lam[CB_MAXCUT], mu[CB_MAXCUT];
-#pragma unroll
-    for (int b = 0; b < CB_MAXCUT; ++b) lam[b] = mu[b] = 0.f;
-    row_walk(L, i, lane, [&](int j, float w) {
-        const float l = st.lo[ib + j], uu = st.hi[ib + j];
-        const unsigned I = cb_slot_mask(zs, st.xsnap[bo][ib + j], l == uu, w, net.ball && L.in_off == 0);
-        const float Lc = w >= 0.f ? l : uu, Uc = w >= 0.f ? uu : l;
-#pragma unroll
-        for (int b = 0; b < CB_MAXCUT; ++b)
-            if (b < nsl && (only < 0 || b == only)) {
-                if ((I >> b) & 1u) lam[b] += w * Lc;
-                else mu[b] += w * Uc;
-            }
-    });
-#pragma unroll
-    for (int b = 0; b < CB_MAXCUT; ++b)
-        if (b < nsl && (only < 0 || b == only)) {
-            lam[b] = warp_sum(lam[b]);
-            mu[b] = warp_sum(mu[b]);
-        }
-    if (lane < nsl && (only < 0 || lane == only)) {
-        float l = 0.f, m = 0.f;
-#pragma unroll
-        for (int b = 0; b < CB_MAXCUT; ++b)
-            if (b == lane) { l = lam[b]; m = mu[b]; }
-        const size_t hs = (size_t)s * net.cap * NH + (size_t)lane * NH + L.h_out + i;
-        st.lam[hs] = l;
-        st.kap[hs] = l + m + L.b[i];
-    }
-}
-
 }  // namespace cb

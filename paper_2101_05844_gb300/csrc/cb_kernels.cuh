@@ -28,11 +28,21 @@ __device__ __forceinline__ unsigned cb_slot_mask(unsigned zs, unsigned xs, bool 
     return zs | xm;
 }
 
-// Saddle Point oracle bit, eq. (3) with continuous (x, z), in the threshold form decided in
-// float32: W > 0 -> z >= (x - l)/(u - l); W < 0 -> z >= (u - x)/(u - l); W = 0 or l = u -> 1
-// (fixed inputs carry thresholds of -inf).
+// Saddle Point oracle bit, eq. (3) with continuous (x, z), in the threshold form: W > 0 ->
+// z (u - l) >= x - l, W < 0 -> z (u - l) >= u - x (eq. 3 with the sign of W multiplied out), i.e.
+// z >= tau for tau = (x - l) / (u - l), resp. (u - x) / (u - l); W = 0 or l = u -> 1 (fixed inputs
+// carry thresholds of -inf). The thresholds are cb_tau_up's, so each float32 compare is exact.
 __device__ __forceinline__ bool cb_sp_mask(float z, float tp, float tn, float w) {
     return w > 0.f ? (z >= tp) : (w < 0.f ? (z >= tn) : true);
+}
+
+// The smallest float32 at or above the real quotient (a - b) / (hi - lo), for float32 a, b, lo <
+// hi: the differences are exact in float64 (float32 operands whose magnitudes lie within 2^28 of
+// each other), the quotient is rounded up in float64 and again to float32. Rounding up twice
+// gives the float32 rounding up of the real quotient (a float32 is a float64), so for every
+// float32 z, z >= tau (real) exactly when z >= this value: the mask decision of eq. (3) is exact.
+__device__ __forceinline__ float cb_tau_up(float a, float b, float lo, float hi) {
+    return __double2float_ru(__ddiv_ru((double)a - (double)b, (double)hi - (double)lo));
 }
 
 // Block-to-segment lookup for launches that cover several layers.

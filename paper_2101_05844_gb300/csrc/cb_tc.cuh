@@ -15,8 +15,11 @@
 // to the stage's mbarrier; the stage is refilled once that barrier completes. The epilogue reads the
 // accumulator back with tcgen05.ld (each warp its 32 TMEM lanes) and stores it to global memory.
 //
-// Every wait is bounded: a barrier that does not complete within the limit sets *status and the
-// CTA stops issuing work, waits (bounded) for its last commit, frees its TMEM and returns.
+// Every wait is bounded: a stage barrier that does not complete within its limit (stage_limit)
+// sets *status and the CTA stops issuing work, then waits for its last commit with the full limit
+// (all of its MMAs are then complete), frees its TMEM and returns. Should that drain wait run out as
+// well, MMAs may still be writing the CTA's TMEM: the CTA then returns without freeing it (results
+// after AS_ERR_TIMEOUT are void either way).
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -51,9 +54,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0u;
 }
 
-// Bounded wait for the completion of phase `parity`; false if the limit ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    for (uint32_t i = 0; i < TC_WAIT_LIMIT; ++i)
+// Bounded wait for the completion of phase `parity`: at most `limit` try_wait rounds; false if the
+// limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit = TC_WAIT_LIMIT) {
+    for (uint32_t i = 0; i < limit; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -189,7 +193,7 @@ constexpr int tc_smem_bytes() {
 template <int BN>
 __device__ __forceinline__ void gemm_tile(const Gather& ga, const uint16_t* __restrict__ B, int ldb,
                                           float* __restrict__ D, int ldd, int M, int N, int K, int* status,
-                                          int dt_P = 0) {
+                                          int dt_P = 0, uint32_t stage_limit = TC_WAIT_LIMIT) {
     static_assert(BN == 32 || BN == 64 || BN == 128 || BN == 256, "BN");
     extern __shared__ __align__(128) uint8_t smem[];
     constexpr int A_BYTES = TC_BM * TC_BK * 2, B_BYTES = BN * TC_BK * 2, STAGE = A_BYTES + B_BYTES;
@@ -229,7 +233,8 @@ __device__ __forceinline__ void gemm_tile(const Gather& ga, const uint16_t* __re
         const int kn = kt + TC_STAGES - 1;   // the tile loaded this iteration
         bool w_ok = true;
         // its stage was last read by the MMAs of tile kt - 1
-        if (kn < KT && kt >= 1) w_ok = mbar_wait(&bars[(kt - 1) % TC_STAGES], ((kt - 1) / TC_STAGES) & 1u);
+        if (kn < KT && kt >= 1)
+            w_ok = mbar_wait(&bars[(kt - 1) % TC_STAGES], ((kt - 1) / TC_STAGES) & 1u, stage_limit);
         if (!__syncthreads_and(w_ok)) {   // the decision is the CTA's, so every thread leaves together
             ok = false;
             break;
@@ -261,7 +266,8 @@ __device__ __forceinline__ void gemm_tile(const Gather& ga, const uint16_t* __re
         const int last = issued - 1;
         f_ok = mbar_wait(&bars[last % TC_STAGES], (last / TC_STAGES) & 1u);
     }
-    ok = __syncthreads_and(ok && f_ok);
+    const bool drained = __syncthreads_and(f_ok);
+    ok = __syncthreads_and(ok && drained);
     if (!ok && tid == 0 && status) atomicExch(status, TC_ERR_TIMEOUT);
     tc_fence_after();
     if (ok) {
@@ -292,7 +298,7 @@ __device__ __forceinline__ void gemm_tile(const Gather& ga, const uint16_t* __re
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_free(tmem, BN);
+    if (warp == 0 && drained) tmem_free(tmem, BN);
 }
 
 template <int BN>
@@ -320,6 +326,8 @@ struct GemmGroup {
     const int* ctr;               // device iteration counter
     DSched sc;
     int row_pass;
+    uint32_t stage_limit;         // try_wait rounds of a stage wait (TC_WAIT_LIMIT; smaller only to
+                                  // exercise the timeout path)
 };
 
 template <int BN>
@@ -337,7 +345,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_group_bf16(GemmGroup gg, in
     const int M = want < gg.M[g] ? (int)want : gg.M[g];
     if ((int)blockIdx.x * TC_BM >= M) return;   // the whole CTA leaves together, before any barrier
     gemm_tile<BN>(gg.ga[g], gg.B[g], gg.ldb[g], gg.D[g], gg.ldd, M, gg.N, gg.K[g], status,
-                  gg.transposed && gg.ga[g].P > 1 ? gg.ga[g].P : 0);
+                  gg.transposed && gg.ga[g].P > 1 ? gg.ga[g].P : 0, gg.stage_limit);
 }
 
 }  // namespace tc

@@ -201,6 +201,20 @@ __device__ __forceinline__ void load_rec(const float4* q, int apos, float (&v)[1
     if (NV > 8) { const float4 c = q[2 * apos]; v[8] = c.x; v[9] = c.y; v[10] = c.z; v[11] = c.w; }
 }
 
+// Records of the float32 slot row sums (k_slot_sums_t below): per input {l, u, p bits | q bits
+// << 8} in the first Saddle Point input plane, which Active Set leaves unused.
+__device__ __forceinline__ float4* slot_rec_plane(const DNet& net, const DState& st, const DLayer& L, int s) {
+    return st.spin + (size_t)s * net.XT + (size_t)L.xo;
+}
+// The record of an input with box [lo, hi] and snapshot bits xs (bit b: at its upper end when slot b
+// was added); a fixed input (lo = hi) is selected by every mask, an interior one (layer 0 over an
+// ellipsoid) by none: its bit is z alone.
+__device__ __forceinline__ float4 slot_rec(float lo, float hi, unsigned xs, bool fixed, bool interior) {
+    const unsigned fxm = fixed ? 0xFFu : 0u;
+    const unsigned pm = (interior ? 0u : (~xs & 0xFFu)) | fxm, qm = (interior ? 0u : (xs & 0xFFu)) | fxm;
+    return make_float4(lo, hi, __uint_as_float(pm | (qm << 8)), 0.f);
+}
+
 // B taps of a lane's stride T starting at t (taps at or past tb read as {0, +0.f}: a zero weight
 // at the unit's base position, which adds nothing). Loading a whole batch of taps, then all of their
 // records, keeps B independent loads in flight per lane instead of one dependent pair at a time.
@@ -383,6 +397,10 @@ __device__ __forceinline__ void as_colA_body(const DNet& net, const DState& st, 
                 X[pl * B.PX + off] = p ? xb : zero;
                 X[(pl + 1) * B.PX + off] = qq ? xb : zero;
             }
+            // the new slot's float32 lambda, kappa (k_slot_sums_t after the row pass) walk these records
+            if (add_iter)
+                slot_rec_plane(net, st, L, s)[xin_pos(L, j)] =
+                    slot_rec(lo, hi, xs_new, fixed, net.ball && L.in_off == 0);
         } else {
             // row-pass input record: x* and the slot masks p_b (bits 0-7) and q_b (bits 8-15)
             reinterpret_cast<float2*>(st.xin + (size_t)s * net.XT + L.xo)[xin_pos(L, j)] =
@@ -798,6 +816,116 @@ __global__ void __launch_bounds__(CB_THREADS, 4) k_as_rowB_t(DNet net, DState st
     }
 }
 
+// ---------------------------------------------------------------- slot row sums
+// lambda_b[i] = sum_j W_ij I_b(i, j) Lcheck_ij and kappa_b[i] = lambda_b[i] + sum_j W_ij (1 - I_b(i, j))
+// Ucheck_ij + b_i of active-set slots (g_B of Sec. 4.1, the constants of eq. 4), in float32, from
+// the slots' snapshot bits. Eq. (3) at a slot's snapshot point gives I_b(i, j) = 1 on rows with
+// z_b = 1 (lambda = lz, kappa = lz + b there) and otherwise I_b(i, j) = p_b(j) where W_ij > 0 and
+// q_b(j) where W_ij < 0, with Lcheck = l, Ucheck = u where W > 0 and the reverse where W < 0. A lane
+// team walks the row's sign-partitioned tap list over per-input records {l, u, p bits | q bits << 8}
+// kept in the first Saddle Point input plane (unused while Active Set runs; padding stays zero).
+// The records of every input of the hidden-output layers from the snapshot buffer bo.
+__global__ void k_slot_recs(DNet net, DState st, int bo) {
+    const size_t n = (size_t)net.S * net.NT;
+    for (size_t u = blockIdx.x * (size_t)blockDim.x + threadIdx.x; u < n; u += (size_t)gridDim.x * blockDim.x) {
+        const int s = (int)(u / net.NT), hh = (int)(u - (size_t)s * net.NT);
+        int li = 0;
+        while (li + 2 < net.n && hh >= net.L[li + 1].in_off) ++li;
+        const DLayer& L = net.L[li];
+        const int j = hh - L.in_off;
+        if (j >= L.n_in) continue;   // the last hidden layer feeds only the output row
+        slot_rec_plane(net, st, L, s)[xin_pos(L, j)] =
+            slot_rec(st.lo[u], st.hi[u], st.xsnap[bo][u], st.efix[u], net.ball && li == 0);
+    }
+}
+
+template <int NB>
+__device__ __forceinline__ void slot_sums_unit(const DNet& net, const DState& st, const DLayer& L, bool valid, int s,
+                                               int i, int lane, int T, int b0, int nsl, int bo) {
+    float lam[NB], mu[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) lam[b] = mu[b] = 0.f;
+    if (valid) {
+        int g, base;
+        row_group(L, i, g, base);
+        const float4* rb = slot_rec_plane(net, st, L, s) + base;
+        const int t0 = L.rgrp[2 * g], t1 = L.rgrp[2 * g + 1], t2 = L.rgrp[2 * g + 2];
+        constexpr int B = 4;
+        for (int ph = 0; ph < 2; ++ph) {
+            const int ta = ph ? t1 : t0, tb = ph ? t2 : t1;
+            const int sh = (ph ? 8 : 0) + b0;
+            for (int t = ta + lane; t < tb; t += B * T) {
+                int2 e[B];
+                load_taps<B>(L.rtap, t, tb, T, e);
+                float4 r[B];
+#pragma unroll
+                for (int q = 0; q < B; ++q) r[q] = rb[e[q].x];
+#pragma unroll
+                for (int q = 0; q < B; ++q) {
+                    const float w = __int_as_float(e[q].y);
+                    // Lcheck, Ucheck: (l, u) for W > 0, (u, l) for W < 0
+                    const float wl = w * (ph ? r[q].y : r[q].x), wu = w * (ph ? r[q].x : r[q].y);
+                    const unsigned bits = __float_as_uint(r[q].z) >> sh;
+#pragma unroll
+                    for (int b = 0; b < NB; ++b) {
+                        if ((bits >> b) & 1u) lam[b] += wl;
+                        else mu[b] += wu;
+                    }
+                }
+            }
+        }
+    }
+    if (T > 1) {
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            lam[b] = team_sum(lam[b], T);
+            mu[b] = team_sum(mu[b], T);
+        }
+    }
+    if (!valid || lane != 0) return;
+    const size_t h = (size_t)s * net.NH + L.h_out + i;
+    const unsigned zs = st.zsnap[bo][h];
+    const float bi = L.b[i], lzh = st.lz[h];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        const int bb = b0 + b;
+        if (bb >= nsl) continue;
+        const bool zb = (zs >> bb) & 1u;
+        const size_t hs = ((size_t)s * net.cap + bb) * net.NH + L.h_out + i;
+        st.lam[hs] = zb ? lzh : lam[b];
+        st.kap[hs] = zb ? lzh + bi : lam[b] + mu[b] + bi;
+    }
+}
+
+// Slots b0 .. b0 + NB - 1 of the first nadd additions (snapshot buffer nadd & 1), or with after_add
+// the slot the Active Set iteration that just ended added (BF16 form: that iteration took lambda,
+// kappa from its bf16 products; the col pass wrote the records); returns at once after other
+// iterations. Lane teams as in the float32 row pass, a grid-stride loop over its nvb blocks.
+template <int NB>
+__global__ void __launch_bounds__(CB_THREADS, 4) k_slot_sums_t(DNet net, DState st, DSched sc, TSegs sg, int nvb,
+                                                                int b0, int nadd, int after_add) {
+    if (after_add) {
+        const int it = st.ctr[0] - 1;
+        if (it < sc.TM) return;
+        const int b = cb_slot_at(it - sc.TM, sc);
+        if (b < 0) return;
+        nadd = cb_additions_before(it - sc.TM + 1, sc);
+        b0 = b;
+    }
+    const int bo = nadd & 1;
+    for (int vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
+        const int q = tseg_of(sg, vb);
+        const DLayer& L = net.L[sg.layer[q]];
+        const int T = sg.T[q];
+        const int t = (vb - sg.start[q]) * CB_THREADS + threadIdx.x;
+        const int unit = t / T, lane = t - unit * T;
+        const bool valid = unit < net.S * L.n_out;
+        const int s = valid ? unit / L.n_out : 0, i = valid ? unit - s * L.n_out : 0;
+        const int nsl = valid ? min(nadd, st.caps[s]) : 0;
+        slot_sums_unit<NB>(net, st, L, valid, s, i, lane, T, b0, nsl, bo);
+    }
+}
+
 // rp and bz from the current duals and snapshots (after a state import): the float32 output
 // records, or with tc the BF16 form's bf16 operand planes.
 __global__ void k_rowprep(DNet net, DState st, DSched sc, int tc) {
@@ -937,8 +1065,9 @@ __global__ void k_sp_prep(DNet net, DState st) {
 
 // Phase A epilogue for input j of layer L (k = li + 1, m = k - 1): f_m from acc = (W_k^T alpha_k)[j]
 // (Sec. 5.1), the primal conditional gradient (eqs. 7-8 with B = E), the bound terms, and the
-// records of input j for the row pass: the float32 thresholds of the oracle eq. (3) at the primal
-// iterate x (buffer cur). init != 0 also starts the primal iterate at the conditional gradient.
+// records of input j for the row pass: the thresholds of the oracle eq. (3) at the primal iterate
+// x (buffer cur), rounded up to float32 (cb_tau_up) so that the row pass's compares are exact.
+// init != 0 also starts the primal iterate at the conditional gradient.
 __device__ __forceinline__ void sp_phaseA_epilogue(const DNet& net, const DState& st, const DLayer& L, int k,
                                                    int s, int j, float acc, int cur, int init) {
     const int m = k - 1;
@@ -966,9 +1095,8 @@ __device__ __forceinline__ void sp_phaseA_epilogue(const DNet& net, const DState
     if (k <= net.n - 1) {
         float tp = -INFINITY, tn = -INFINITY;
         if (lo != hi) {
-            const float den = __fsub_rn(hi, lo);
-            tp = __fdiv_rn(__fsub_rn(x, lo), den);
-            tn = __fdiv_rn(__fsub_rn(hi, x), den);
+            tp = cb_tau_up(x, lo, lo, hi);
+            tn = cb_tau_up(hi, x, lo, hi);
         }
         float4* r = sp_iplane(net, st, L, s) + xin_pos(L, j);
         r[0] = make_float4(x, tp, lo, hi);
@@ -1274,9 +1402,8 @@ __global__ void __launch_bounds__(CB_BALL_THREADS) k_ball_sp(DNet net, DState st
             st.spx[cur][xo] = xb;
             float tp = -INFINITY, tn = -INFINITY;
             if (lo != hi) {
-                const float den = __fsub_rn(hi, lo);
-                tp = __fdiv_rn(__fsub_rn(xb, lo), den);
-                tn = __fdiv_rn(__fsub_rn(hi, xb), den);
+                tp = cb_tau_up(xb, lo, lo, hi);
+                tn = cb_tau_up(hi, xb, lo, hi);
             }
             float4* r = sp_iplane(net, st, L, s) + xin_pos(L, j);
             r[0] = make_float4(xb, tp, lo, hi);

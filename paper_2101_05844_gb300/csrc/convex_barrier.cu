@@ -66,6 +66,10 @@ struct as_ctx {
     TSegs tA1{}, tB1{};                           // one lane per unit
     int blocksTA1 = 0, blocksTB1 = 0;
     long long team_row = 40000, team_col = 40000; // team-size targets of the float32 passes
+    uint32_t tc_stage_limit = tc::TC_WAIT_LIMIT;  // try_wait rounds of the GEMMs' stage waits
+    // host-side fault injection for tests (environment CB_FAIL_ALLOC_AT = n): the n-th device
+    // allocation of the context is refused as if the device were out of memory
+    long long fail_alloc_at = 0, alloc_calls = 0;
 };
 
 static int fail(as_ctx* c, int code, const char* fmt, ...) {
@@ -93,6 +97,9 @@ static int dalloc(as_ctx* c, T** p, size_t count) {
     void* q = nullptr;
     size_t bytes = count * sizeof(T);
     if (bytes == 0) bytes = 16;
+    if (++c->alloc_calls == c->fail_alloc_at)
+        return fail(c, AS_ERR_OOM, "device allocation %lld (%zu bytes) refused by CB_FAIL_ALLOC_AT", c->alloc_calls,
+                    bytes);
     cudaError_t e = cudaMalloc(&q, bytes);
     if (e != cudaSuccess)
         return fail(c, e == cudaErrorMemoryAllocation ? AS_ERR_OOM : AS_ERR_CUDA,
@@ -808,6 +815,8 @@ extern "C" int as_init(as_ctx** out, const as_net* net, int S, const float* x_lo
     as_ctx* c = new (std::nothrow) as_ctx();
     if (!c) return AS_ERR_OOM;
     c->stream = (cudaStream_t)stream;
+    if (const char* f = getenv("CB_FAIL_ALLOC_AT")) c->fail_alloc_at = atoll(f);
+    if (const char* f = getenv("CB_TC_STAGE_WAIT_LIMIT")) c->tc_stage_limit = (uint32_t)strtoul(f, nullptr, 10);
     cudaError_t e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         delete c;

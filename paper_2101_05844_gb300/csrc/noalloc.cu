@@ -3,7 +3,6 @@
 // post-activation bounds passed from one layer to the next in a fixed, file-scope device array
 // instead of context buffers, so the call itself allocates nothing.
 #include <cstdio>
-#include <mutex>
 
 #include "../../include/convex_barrier.h"
 #include "cb_walk.cuh"
@@ -16,35 +15,31 @@ namespace {
 constexpr size_t kScratchFloats = AS_NOALLOC_SCRATCH_FLOATS;
 static __device__ __align__(256) float g_ibp_scratch[kScratchFloats];
 
-// Device address of g_ibp_scratch for each device, looked up once per device. In host code the
-// array's name only stands for the symbol; a kernel must be given this address instead.
-constexpr int kMaxDevices = 64;
-float* g_scratch_addr[kMaxDevices] = {};
-std::mutex g_scratch_mutex;
-
+// Device address of g_ibp_scratch on the current device. In host code the array's name only stands
+// for the symbol; a kernel must be given this address instead. It is looked up on every call (a
+// lookup, not an allocation, once the module is loaded on the device), so that a device reset or a
+// new primary context, after which the module is loaded again at a possibly different address,
+// never leaves a stale address behind.
 int scratch_address(float** out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return AS_ERR_CUDA;
-    std::lock_guard<std::mutex> lock(g_scratch_mutex);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_ibp_scratch) != cudaSuccess || !p) {
-            cudaGetLastError();
-            return AS_ERR_CUDA;
-        }
-        g_scratch_addr[dev] = (float*)p;
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_ibp_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return AS_ERR_CUDA;
     }
-    *out = g_scratch_addr[dev];
+    *out = (float*)p;
     return AS_OK;
 }
 
-bool on_device(const void* p) {
+// Device memory of the current device (or managed memory): the only memory the kernels may read and
+// write without peer access.
+bool on_device(const void* p, int dev) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 // One hidden layer of interval propagation (App. E): FP64 accumulation of W+ l + W- u + b and
@@ -88,6 +83,8 @@ __global__ void k_ibp_noalloc(DLayer L, int S, int bias_per, const float* in_lo,
 extern "C" int as_ibp_noalloc(const as_net* net, int S, const float* x_lo, const float* x_hi,
                               const signed char* splits, float* lhat, float* uhat, void* stream) {
     if (!net || !net->layers || S < 1 || !x_lo || !x_hi || !lhat || !uhat) return AS_ERR_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return AS_ERR_CUDA;
     const int n = net->n_layers;
     if (n < 2 || n > AS_MAX_LAYERS) return AS_ERR_SHAPE;
     DLayer Ls[AS_MAX_LAYERS];
@@ -97,7 +94,7 @@ extern "C" int as_ibp_noalloc(const as_net* net, int S, const float* x_lo, const
         const as_layer& A = net->layers[k];
         DLayer& L = Ls[k];
         L = DLayer{};
-        if (!A.W || !A.b || !on_device(A.W) || !on_device(A.b)) return AS_ERR_ARG;
+        if (!A.W || !A.b || !on_device(A.W, dev) || !on_device(A.b, dev)) return AS_ERR_ARG;
         L.kind = A.kind;
         if (A.kind == AS_LAYER_LINEAR) {
             if (A.in_c < 1 || A.out_c < 1) return AS_ERR_SHAPE;
@@ -126,8 +123,8 @@ extern "C" int as_ibp_noalloc(const as_net* net, int S, const float* x_lo, const
         NH += L.n_out;
         if (L.n_out > widest) widest = L.n_out;
     }
-    if (!on_device(x_lo) || !on_device(x_hi) || !on_device(lhat) || !on_device(uhat) ||
-        (splits && !on_device(splits)))
+    if (!on_device(x_lo, dev) || !on_device(x_hi, dev) || !on_device(lhat, dev) || !on_device(uhat, dev) ||
+        (splits && !on_device(splits, dev)))
         return AS_ERR_ARG;
     // four scratch regions of S x widest floats
     if ((size_t)S * (size_t)widest * 4 > kScratchFloats) return AS_ERR_SCRATCH;

@@ -87,14 +87,20 @@ extern "C" int as_import_state(as_ctx* c, const void* src) {
     std::vector<long long> sizes;
     int r = layout(c, sp, sizes);
     if (r != AS_OK) return r;
-    const int* ids = sp ? kSaddle : kActiveSet;
-    for (size_t q = 0; q < sizes.size(); ++q) {
+    // every section's size first, so that a blob of another net, batch size or max_cuts leaves the
+    // context untouched
+    const unsigned char* q = p;
+    for (size_t k = 0; k < sizes.size(); ++k) {
         long long b = 0;
-        std::memcpy(&b, p, sizeof b);
-        p += sizeof b;
-        if (b != sizes[q]) return AS_ERR_SHAPE;   // another net, batch size or max_cuts
-        if ((r = as_set_state(c, ids[q], p)) != AS_OK) return r;
-        p += b;
+        std::memcpy(&b, q, sizeof b);
+        if (b != sizes[k]) return AS_ERR_SHAPE;
+        q += sizeof b + b;
+    }
+    const int* ids = sp ? kSaddle : kActiveSet;
+    for (size_t k = 0; k < sizes.size(); ++k) {
+        p += sizeof(long long);
+        if ((r = as_set_state(c, ids[k], p)) != AS_OK) return r;
+        p += sizes[k];
     }
     return AS_OK;
 }

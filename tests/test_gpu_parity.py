@@ -3,9 +3,10 @@
 Tolerances (float32 GPU arithmetic against FP64):
   * interval bounds: the float32 interval contains the FP64 one and is within 4e-6 (1 + |v|) of it
     (FP64 accumulation per layer, outward rounding to float32 at every layer);
-  * one-iteration lockstep of the duals: 1e-5 relative, 1e-7 absolute floor, on every
-    entry whose update direction is decided: entries where the oracle's gradient is within
-    1e-4 of zero are checked for validity only (both signs give a valid Adam step);
+  * one-iteration lockstep of the duals: 1e-5 relative, 1e-7 absolute floor, plus the spread of
+    the oracle's Adam step over gradients within a float32 summation bound of its own
+    (tests/lockstep.py); rows that read an x* or z* decided within that bound are left out and
+    counted (none in the drawn states, a small fraction allowed at full size);
   * bounds: 1e-4 absolute, 1e-5 relative where values are large;
   * masks and snapshot bits: bit-exact.
 """
@@ -16,9 +17,11 @@ from oracle import active_set as AS
 from oracle import dual as du
 from oracle import envelope as ev
 from oracle import network as nw
+from oracle import relaxation as rx
 from oracle import saddle as SPm
 from paper_2101_05844_gb300 import binding, synth
 from tests.helpers import sample_min_output
+from tests.lockstep import check_active_set_step
 from tests.state_helpers import draw_state, hidden_concat, oracle_bounds_f32, split_hidden
 
 pytestmark = pytest.mark.gpu
@@ -101,19 +104,10 @@ def test_one_iteration_lockstep(name, S, kw, it, nslots):
     for s, sv in enumerate(solvers):
         P = sv.P
         _, f, g, x, z = du.evaluate(P, sv.st)
-        grads = du.supergradient(P, sv.st, x, z)
         slots_before = len(sv.st.slots[1])
-        # gradient of the slot this iteration adds: eq. (9) at the oracle's mask at (x*, z*)
-        gnew = [None]
-        for k in range(1, P.n):
-            from oracle import relaxation as rx
-            I = rx.mask(P.W[k], P.lo[k - 1], P.hi[k - 1], x[k - 1], z[k])
-            lam_n, mu_n = rx.row_sums(P.W[k], P.lo[k - 1], P.hi[k - 1], I)
-            gnew.append(x[k] - (P.W[k] * I) @ x[k - 1] + lam_n * (1 - z[k]) - z[k] * (P.b[k] + mu_n))
-        sv.step(1)
-        # primal minimiser: exact
-        np.testing.assert_array_equal(xstar[s], np.concatenate([x[k] for k in range(P.n)]).astype(np.float32))
         np.testing.assert_array_equal(zstar[s], hidden_concat(z).astype(np.uint8))
+        res = check_active_set_step(sv, dict(alpha=al[s], beta0=b0[s], beta1=b1[s], slots=sb[s], xstar=xstar[s]))
+        assert res["exempt_rows"] == 0 and res["undecided_x"] == 0
         # the new slot's snapshot: the oracle's mask at (x*, z*) (bit-exact)
         nnew = len(sv.st.slots[1])
         if nnew > slots_before:
@@ -122,28 +116,11 @@ def test_one_iteration_lockstep(name, S, kw, it, nslots):
             for k in range(1, P.n):
                 xb = ((xs[s, offs[k - 1]:offs[k]] >> b) & 1).astype(bool)
                 zb = ((zs[s, offs[k] - P.widths[0]:offs[k + 1] - P.widths[0]] >> b) & 1).astype(float)
-                from oracle import relaxation as rx
                 Igpu = rx.mask(P.W[k], P.lo[k - 1], P.hi[k - 1], np.where(xb, P.hi[k - 1], P.lo[k - 1]), zb)
                 np.testing.assert_array_equal(Igpu, sv.st.slots[k][b].I)
             np.testing.assert_allclose(
                 lam[s, b], hidden_concat([None] + [sv.st.slots[k][b].lam for k in range(1, P.n)]),
                 rtol=1e-5, atol=1e-5)
-
-        def check(gpu, ref, gref):
-            decided = (np.abs(gref) > 1e-4) | (gref == 0)
-            np.testing.assert_allclose(gpu[decided], ref[decided], rtol=1e-5, atol=1e-7)
-            assert (gpu >= 0).all()
-            assert decided.mean() > 0.9
-        check(al[s], hidden_concat(sv.st.alpha), hidden_concat(grads["galpha"]))
-        check(b0[s], hidden_concat(sv.st.beta0), hidden_concat(grads["gbeta0"]))
-        check(b1[s], hidden_concat(sv.st.beta1), hidden_concat(grads["gbeta1"]))
-        for b in range(len(sv.st.slots[1])):
-            ref = hidden_concat([None] + [sv.st.slots[k][b].beta for k in range(1, P.n)])
-            if b < slots_before:
-                gref = hidden_concat([None] + [grads["gslots"][k][b] for k in range(1, P.n)])
-            else:
-                gref = hidden_concat(gnew)
-            check(sb[s, b], ref, gref)
 
 
 def _as_margin(sv):
@@ -156,8 +133,30 @@ def _as_margin(sv):
     return m
 
 
+def test_small_mlp_active_set_matches_oracle_at_every_iteration():
+    """The small MLP workload as specified (8-16-16-1, one subproblem, 100 iterations: 20 Big-M,
+    then 80 Active Set with masks added at t = 0, 1, 24, 25, 48, cap 5, omega = 24): the float32
+    GPU run and the FP64 oracle agree to 1e-4 at every iteration, with no divergence allowed, and
+    the final and best bounds agree to 1e-4."""
+    prob, Ps = _problems("mlp_tiny", 1)
+    kw = dict(bigm_iters=20, as_iters=80, omega=24, max_cuts=5)
+    ctx = binding.context_for(prob, binding.default_options(graph_chunk=0, track_best=1, **kw))
+    sv = AS.ActiveSet(Ps[0], AS.Options(**kw))
+    worst = 0.0
+    for it in range(100):
+        ctx.as_step(1)
+        sv.step(1)
+        d = abs(ctx.bound()[0] - du.evaluate(sv.P, sv.st)[0])
+        worst = max(worst, d)
+        assert d <= 1e-4, f"iteration {it}: GPU and oracle bounds differ by {d}"
+    b, best = ctx.bound(best=True)
+    assert b[0] == pytest.approx(sv.bound(), abs=1e-4)
+    assert best[0] == pytest.approx(sv.best, abs=1e-4)
+    assert [len(sv.st.slots[k]) for k in range(1, sv.P.n)] == [5, 5]
+    assert best[0] <= sample_min_output(sv.P, 100_000) + 1e-6
+
+
 @pytest.mark.parametrize("name,S,kw,iters", [
-    ("mlp_tiny", 1, dict(bigm_iters=20, as_iters=80, omega=24, max_cuts=5), 100),
     ("mlp_5_7_6_3", 4, dict(bigm_iters=30, as_iters=60, omega=20, max_cuts=4), 90),
     ("small_conv", 3, dict(bigm_iters=20, as_iters=40, omega=12, max_cuts=5), 60),
 ])
@@ -489,29 +488,16 @@ def test_full_size_wide_conv_lockstep_on_sampled_subproblems(it, nslots):
         assert gb[s] == pytest.approx(du.evaluate(sv.P, sv.st)[0], abs=1e-4, rel=1e-5)
     ctx.as_step(1)
     S = 9
-    al = ctx.get_state(binding.ST_ALPHA).reshape(S, -1)
-    b1 = ctx.get_state(binding.ST_BETA1).reshape(S, -1)
+    st = {key: ctx.get_state(code).reshape(S, -1) for key, code in
+          (("alpha", binding.ST_ALPHA), ("beta0", binding.ST_BETA0), ("beta1", binding.ST_BETA1),
+           ("xstar", binding.ST_XSTAR))}
     sb = ctx.get_state(binding.ST_SLOT_BETA).reshape(S, ctx.cap, -1)
-    xstar = ctx.get_state(binding.ST_XSTAR).reshape(S, -1)
     for s, sv in solvers.items():
-        P = sv.P
-        _, f, g, x, z = du.evaluate(P, sv.st)
-        grads = du.supergradient(P, sv.st, x, z)
-        fmin = min(np.abs(fk).min() for fk in f)
-        sv.step(1)
-        decided_f = np.concatenate([np.abs(fk) > 1e-5 for fk in f])
-        np.testing.assert_array_equal(xstar[s][decided_f], np.concatenate(x).astype(np.float32)[decided_f])
-        if fmin <= 1e-5:
-            continue   # a near-zero f: the minimiser, and so the step, is decided by rounding
-        for gpu, ref, gref in ((al[s], sv.st.alpha, grads["galpha"]), (b1[s], sv.st.beta1, grads["gbeta1"])):
-            ref, gref = hidden_concat(ref), hidden_concat(gref)
-            ok = (np.abs(gref) > 1e-4) | (gref == 0)
-            np.testing.assert_allclose(gpu[ok], ref[ok], rtol=1e-5, atol=1e-7)
-        for b in range(nslots):
-            ref = hidden_concat([None] + [sv.st.slots[k][b].beta for k in range(1, P.n)])
-            gref = hidden_concat([None] + [grads["gslots"][k][b] for k in range(1, P.n)])
-            ok = (np.abs(gref) > 1e-4) | (gref == 0)
-            np.testing.assert_allclose(sb[s, b][ok], ref[ok], rtol=1e-5, atol=1e-7)
+        # wide rows (fan-in up to 2048) widen the float32 bound: at least 80% of the entries are
+        # checked at the rounding tolerance itself, the rest within the spread it allows
+        res = check_active_set_step(sv, dict(alpha=st["alpha"][s], beta0=st["beta0"][s], beta1=st["beta1"][s],
+                                             slots=sb[s], xstar=st["xstar"][s]), min_tight=0.8)
+        assert res["checked"] >= 0.9 * 3 * res["rows"]
 
 
 def test_batched_subdomains_lockstep_with_splits_and_caps():
@@ -564,25 +550,18 @@ def test_batched_subdomains_lockstep_with_splits_and_caps():
         for k in range(1, sv.P.n):
             del sv.st.slots[k][int(caps[s]):]
     ctx.as_step(1)
-    al = ctx.get_state(binding.ST_ALPHA).reshape(4096, -1)
+    st = {key: ctx.get_state(code).reshape(4096, -1) for key, code in
+          (("alpha", binding.ST_ALPHA), ("beta0", binding.ST_BETA0), ("beta1", binding.ST_BETA1),
+           ("xstar", binding.ST_XSTAR))}
     sb = ctx.get_state(binding.ST_SLOT_BETA).reshape(4096, ctx.cap, -1)
     for s, sv in solvers.items():
-        P = sv.P
-        _, f, g, x, z = du.evaluate(P, sv.st)
-        grads = du.supergradient(P, sv.st, x, z)
-        if min(np.abs(fk).min() for fk in f) <= 1e-5:
-            continue
-        sv.step(1)
-        ref, gref = hidden_concat(sv.st.alpha), hidden_concat(grads["galpha"])
-        ok = (np.abs(gref) > 1e-4) | (gref == 0)
-        np.testing.assert_allclose(al[s][ok], ref[ok], rtol=1e-5, atol=1e-7)
+        # wide rows (fan-in up to 2048) widen the float32 bound: at least 80% of the entries are
+        # checked at the rounding tolerance itself, the rest within the spread it allows
+        res = check_active_set_step(sv, dict(alpha=st["alpha"][s], beta0=st["beta0"][s], beta1=st["beta1"][s],
+                                             slots=sb[s], xstar=st["xstar"][s]), min_tight=0.8)
+        assert res["checked"] >= 0.9 * 3 * res["rows"]
         nslots = len(sv.st.slots[1])
         assert nslots == min(int(caps[s]), 5)
-        for b in range(min(nslots, 4)):
-            ref = hidden_concat([None] + [sv.st.slots[k][b].beta for k in range(1, P.n)])
-            gref = hidden_concat([None] + [grads["gslots"][k][b] for k in range(1, P.n)])
-            ok = (np.abs(gref) > 1e-4) | (gref == 0)
-            np.testing.assert_allclose(sb[s, b][ok], ref[ok], rtol=1e-5, atol=1e-7)
         for b in range(nslots, ctx.cap):
             assert (sb[s, b] == 0).all()      # capped: the slot stays empty
 

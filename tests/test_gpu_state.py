@@ -49,3 +49,25 @@ def test_mismatched_imports_are_refused():
         other.import_state(blob)
     with pytest.raises(binding.CBError):
         a.import_state(np.zeros_like(blob))
+
+
+def test_a_refused_import_leaves_the_context_unchanged():
+    """A blob of another batch size passes the iteration counter's section but not the duals': the
+    import is refused before any buffer is written, so the context goes on as if never touched."""
+    prob = synth.problem("small_conv", S=3, seed=2)
+    opt = binding.default_options(graph_chunk=0, bigm_iters=10, as_iters=60, omega=8, max_cuts=4)
+    a = binding.context_for(prob, opt)
+    a.as_step(23)
+    ref = binding.context_for(prob, opt)
+    ref.as_step(23)
+    small = synth.problem("small_conv", S=2, seed=2)
+    other = binding.context_for(small, opt)
+    other.as_step(5)
+    blob = other.export_state()
+    with pytest.raises(binding.CBError) as e:
+        a.import_state(blob)
+    assert e.value.code == binding.AS_ERR_SHAPE
+    a.as_step(9)
+    ref.as_step(9)
+    np.testing.assert_array_equal(a.bound(), ref.bound())
+    np.testing.assert_array_equal(a.get_state(binding.ST_ITER, np.int32), ref.get_state(binding.ST_ITER, np.int32))

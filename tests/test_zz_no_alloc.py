@@ -4,8 +4,9 @@ It serves callers that cannot call cudaMalloc: a verifier embedded in a process 
 memory belongs to another allocator (a framework's caching allocator, a serving engine's fixed
 pool), or a latency-critical caller that cannot take the implicit synchronisation of
 cudaMalloc / cudaFree. These tests call it through the C ABI and check its bounds against the
-ones the context path (as_init) computes, on two calls in a row, with the interval-bound
-tolerance of the other GPU tests; and that it refuses a problem larger than its fixed scratch.
+ones the context path (as_init) computes, bit for bit, on consecutive calls; that it refuses a
+problem larger than its fixed scratch, host pointers, and (where a second GPU exists) memory of
+another device, by its host-side checks alone.
 """
 import numpy as np
 import pytest
@@ -57,8 +58,14 @@ def test_noalloc_bounds_equal_context_bounds_on_consecutive_calls():
         lh_ref, uh_ref = _context_bounds(prob, S)
         lh, uh = _noalloc_bounds(prob, S, torch)
         assert np.isfinite(lh).all() and np.isfinite(uh).all()
-        np.testing.assert_array_less(np.abs(lh - lh_ref), 4e-6 * (1 + np.abs(lh_ref)) + 1e-30)
-        np.testing.assert_array_less(np.abs(uh - uh_ref), 4e-6 * (1 + np.abs(uh_ref)) + 1e-30)
+        # the same float64 accumulation in the same lane order and the same outward rounding as the
+        # context's interval bounds: bit for bit
+        np.testing.assert_array_equal(lh, lh_ref)
+        np.testing.assert_array_equal(uh, uh_ref)
+        if prob.get("splits") is not None:
+            # the split branch runs: some split neurons were clamped to zero at one end
+            sp = prob["splits"]
+            assert ((lh == 0) & (sp > 0)).sum() + ((uh == 0) & (sp < 0)).sum() > 0
 
 
 def test_noalloc_refuses_problems_beyond_its_scratch():
@@ -77,3 +84,22 @@ def test_noalloc_refuses_problems_beyond_its_scratch():
     assert binding.ibp_noalloc(dnet, lo, hi, lh, uh) == binding.AS_ERR_SCRATCH
     # host pointers are refused too: the call cannot copy them without allocating
     assert binding.ibp_noalloc(dnet[:1] + dnet[1:], lo.cpu(), hi.cpu(), lh, uh) == binding.AS_ERR_ARG
+
+
+def test_noalloc_refuses_memory_of_another_device():
+    """Buffers on a device other than the current one are refused before any launch (the kernels
+    could reach them only through peer access). Needs a second GPU; the check is host-side."""
+    torch = pytest.importorskip("torch")
+    assert torch.cuda.is_available()
+    if torch.cuda.device_count() < 2:
+        pytest.skip("one GPU: no memory of another device to pass")
+    prob = synth.problem("small_conv", S=2, seed=1)
+    torch.cuda.set_device(0)
+    net = _device_net(prob["net"], torch)
+    NH = sum(L["n_out"] for L in prob["net"][:-1])
+    other = torch.device("cuda", 1)
+    lo = torch.from_numpy(prob["lo"]).to(other)
+    hi = torch.from_numpy(prob["hi"]).to(other)
+    lh = torch.empty((2, NH), device=other)
+    uh = torch.empty((2, NH), device=other)
+    assert binding.ibp_noalloc(net, lo, hi, lh, uh) == binding.AS_ERR_ARG
