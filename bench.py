@@ -1,18 +1,22 @@
 """Benchmark of the batched Active Set / Saddle Point hot path on one or more GB300 GPUs.
 
-One step bounds one batch of the workload end to end through the C ABI:
-  Active Set: reset (interval bounds) + 200 Big-M + 800 Active Set iterations + bound;
-  Saddle Point: reset + 200 Big-M + 1000 Saddle Point iterations (conversion and 100 primal
-  initialisation steps included) + bound.
-Default workload: the paper's "Wide" conv net (3x32x32 -> conv16 4x4/2 -> conv32 4x4/2 -> FC100
--> FC10), one L-infinity box of radius 2/255 around a U[0,1] image, the 9 logit-difference
-properties as 9 subproblems; synthetic He-initialised weights.
-
-Output: one JSON line (rank 0). value = subproblem-iterations per second over the whole step,
-inputs resident on the device; e2e = the same with the batch in pinned host memory and the
-bounds read back to the host, copies inside the timed region; roofline = the dominant kernel's
-achieved FP32 rate against the FP32 ALU peak; cpu_baseline = the CPU oracle on a bounded sample.
---impl reference times the CPU oracle as the reference arm.
+Default workload (the precision configuration, the largest that fits one GPU): the conv net
+3x32x32 -> 4 conv 3x3 (32, 32, 64, 64 channels; strides 1, 2, 1, 2; padding 1) -> FC512 -> FC10 on
+1024 L-infinity boxes of half-width 8/255 around U[0,1] images, one property per box (the top logit
+at the centre against the runner-up); synthetic He-initialised weights. One step bounds the whole
+batch end to end through the C ABI and covers every step of the hot path:
+  the BF16 form of Big-M then Active Set (100 Big-M + 400 Active Set iterations; masks added at
+  Active Set iterations 0, 1, 120, 121, 240, cap 5: S1-S6 of the path), the bound re-evaluated in
+  float32 with float64 summation (S8); then Saddle Point continuing from those duals (AS-SP, S7:
+  conversion, 10 primal-initialisation steps, 20 iterations) and its bound.
+value = subproblem-iterations per second of the step (520 per box), inputs resident in HBM; e2e =
+the same with the batch in pinned host memory and both bounds read back, copies inside the timed
+region. forms = the same Active Set schedule in the plain float32 form and the BF16 form on the same
+batch and GPU: subproblem-iterations/s and the time each takes to reach the float32 form's final
+bound (minus 1e-4, absolute and relative). roofline = the dominant kernel of a profiled step against
+its bound (HBM bytes, tensor or FP32 ALU flops); cpu_baseline = the CPU oracle on a bounded sample.
+wide_conv = the Wide conv net's 9 properties (Active Set and Saddle Point solves on two streams), the
+earlier headline, as an extra key. --impl reference times the CPU oracle as the reference arm.
 """
 from __future__ import annotations
 
@@ -33,10 +37,61 @@ sys.path.insert(0, ROOT)
 METRIC = "Active-Set subproblem-iters/s & time-to-bound vs plain FP32; % HBM roofline"
 UNIT = "subproblem-iters/s"
 L2_BYTES = 129 * 1024 * 1024
-SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
+# the default workload's schedule (conv4, 1024 boxes)
+C4_S, C4_BIGM, C4_AS, C4_OMEGA, C4_CAP = 1024, 100, 400, 120, 5
+C4_SP_INIT, C4_SP_ITERS = 10, 20
+# the Wide conv net's (the extra key)
 AS_BIGM, AS_ITERS, SP_BIGM, SP_ITERS = 200, 800, 200, 1000
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def fp32_peak_tflops(torch, dev):
+    """FP32 ALU peak: SMs (queried at run time) x 128 FP32 lanes x 2 flop x the maximum SM clock
+    (MEASURED_PEAKS.json, else nvidia-smi, else 2.07 GHz)."""
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = measured_peaks().get("sm_max_mhz")
+    src = "MEASURED_PEAKS.json sm_max_mhz"
+    if not mhz:
+        try:
+            out = subprocess.run(["nvidia-smi", "-i", str(dev.index or 0), "--query-gpu=clocks.max.sm",
+                                  "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=10)
+            mhz, src = float(out.stdout.strip().splitlines()[0]), "nvidia-smi clocks.max.sm"
+        except (OSError, ValueError, IndexError, subprocess.SubprocessError):
+            mhz, src = 2070.0, "nominal 2.07 GHz"
+    return sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12, f"{sms} SMs x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz ({src})"
+
+
+def conv4_options(binding, precision, profile=0, graph_chunk=25, bigm=C4_BIGM, as_iters=C4_AS, omega=C4_OMEGA):
+    return binding.default_options(bigm_iters=bigm, as_iters=as_iters, omega=omega, max_cuts=C4_CAP,
+                                   graph_chunk=graph_chunk, profile=profile, precision=precision,
+                                   sp_init_steps=C4_SP_INIT)
+
+
+def conv4_step(ctx, batch, out_as, out_sp, events=None):
+    """One step of the default workload on one context: reset, Big-M + Active Set, bound, Saddle
+    Point continuation, bound. events: three CUDA events recorded before, between and after the
+    two solves (on the current stream, which the context's stream is)."""
+    lo, hi, C = batch
+    if events:
+        events[0].record()
+    ctx.reset(lo, hi, C)
+    ctx.as_step(C4_BIGM + C4_AS)
+    ctx.bound_into(64, out_as)
+    if events:
+        events[1].record()
+    ctx.sp_step(C4_SP_ITERS)
+    ctx.bound_into(64, out_sp)
+    if events:
+        events[2].record()
 
 
 def workload_options(binding, profile=0):
@@ -48,14 +103,9 @@ def workload_options(binding, profile=0):
     return as_opt, sp_opt
 
 
-def iterations_per_step():
-    return AS_BIGM + AS_ITERS + SP_BIGM + SP_ITERS
-
-
-def run_step(ctx_as, ctx_sp, batch, out_as, out_sp):
-    """One step: the Active Set solve and the Saddle Point solve of the batch. The two contexts are
-    independent; when they sit on different streams their launches overlap on the GPU (all work
-    is enqueued before the first bound evaluation, which waits for its own stream)."""
+def wide_step(ctx_as, ctx_sp, batch, out_as, out_sp):
+    """The Wide conv net's step: the Active Set solve and the Saddle Point solve of the batch, on
+    contexts on different streams, so their launches overlap on the GPU."""
     lo, hi, C = batch
     ctx_as.reset(lo, hi, C)
     ctx_as.as_step(AS_BIGM + AS_ITERS)
@@ -218,7 +268,7 @@ def batched_run(binding, torch, dev, stream, rank):
     caps = prob["caps"].astype(float)
     mean_slots = [float(np.minimum(k, caps).mean()) for k in sched]
     flops = algorithmic_flops(prob["net"], S, top, mean_slots, kt[top][1])
-    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2.07e9 / 1e12
+    peak, _ = fp32_peak_tflops(torch, dev)
     achieved = flops / (kt[top][0] / 1e3) / 1e12
     teams = ctx.team_targets()
     ctx.close()
@@ -241,115 +291,6 @@ def batched_run(binding, torch, dev, stream, rank):
             "unit": UNIT, "ms": ms, "roofline": {"bound": "alu", "kernel": top, "achieved": achieved, "peak": peak,
                                                  "unit": "TFLOP/s", "frac": achieved / peak},
             "kernel_ms": {k: v[0] for k, v in kt.items() if v[1]}}
-
-
-def precision_run(binding, torch, dev, stream, rank, S=1024, chunk=25):
-    """The precision workload: the conv net 3x32x32 -> 4 conv 3x3 -> FC512 -> FC10 on S boxes of
-    half-width 8/255, 100 Big-M + 400 Active Set iterations, once in float32 and once in the BF16
-    form (tensor-core products, precision 16), same schedule, same GPU. Reports each form's
-    subproblem-iterations/s (one timed run after a warm-up) and the time to bound: iteration time
-    (CUDA events around each chunk of iterations; the bound evaluations between chunks are not
-    counted) until a subproblem's bound, re-evaluated in float32, first reaches the float32
-    form's final bound minus 1e-4 (absolute, and relative to 1 + |bound|); the BF16 form also on
-    an 800-iteration schedule of its own."""
-    from paper_2101_05844_gb300 import synth
-    prob = synth.problem("conv4", S=S, seed=rank)
-    iters = 500
-    t = {k: torch.from_numpy(prob[k]).to(dev) for k in ("lo", "hi", "C")}
-    out = {}
-    finals = {}
-    ctxs = {}
-    for prec in (32, 16):
-        opt = binding.default_options(bigm_iters=100, as_iters=400, omega=120, max_cuts=5, graph_chunk=25,
-                                      precision=prec)
-        ctxs[prec] = binding.Context(prob["net"], prob["lo"], prob["hi"], prob["C"], options=opt, stream=stream)
-    bound = torch.zeros(S, dtype=torch.float64, device=dev)
-    for prec, ctx in ctxs.items():
-        ctx.reset(t["lo"], t["hi"], t["C"])
-        ctx.as_step(iters)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ctx.reset(t["lo"], t["hi"], t["C"])
-        e0.record()
-        ctx.as_step(iters)
-        e1.record()
-        e1.synchronize()
-        ms = e0.elapsed_time(e1)
-        ctx.bound_into(64, bound)
-        finals[prec] = bound.cpu().numpy().copy()
-        out[f"fp{prec}" if prec == 32 else "bf16"] = {"value": S * iters / (ms / 1e3), "unit": UNIT, "ms": ms,
-                                                       "mean_final_bound": float(finals[prec].mean())}
-    # the bound a form must reach: the float32 form's final bound less 1e-4, absolute, and less
-    # 1e-4 (1 + |bound|) (bounds here reach 1e4-1e5, where 1e-4 is below a float32 ulp)
-    targets = {"abs_1e-4": finals[32] - 1e-4, "rel_1e-4": finals[32] - 1e-4 * (1 + np.abs(finals[32]))}
-    for prec, ctx in ctxs.items():
-        ctx.reset(t["lo"], t["hi"], t["C"])
-        reach = {k: np.full(S, np.nan) for k in targets}
-        elapsed = 0.0
-        for c0 in range(0, iters, chunk):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            ctx.as_step(min(chunk, iters - c0))
-            e1.record()
-            e1.synchronize()
-            elapsed += e0.elapsed_time(e1)
-            ctx.bound_into(64, bound)
-            b = bound.cpu().numpy()
-            for k, tg in targets.items():
-                new = np.isnan(reach[k]) & (b >= tg)
-                reach[k][new] = elapsed
-        key = "fp32" if prec == 32 else "bf16"
-        out[key]["time_to_bound_ms"] = {}
-        for k, r in reach.items():
-            done = ~np.isnan(r)
-            out[key]["time_to_bound_ms"][k] = {"reached": int(done.sum()), "of": S,
-                                               "median": float(np.median(r[done])) if done.any() else None,
-                                               "max": float(np.max(r[done])) if done.any() else None}
-    gap = finals[16] - finals[32]
-    out["bf16_minus_fp32_final_bound"] = {"mean": float(gap.mean()), "min": float(gap.min()), "max": float(gap.max())}
-    # the BF16 form on a schedule of its own: 800 iterations (160 Big-M + 640 Active Set, the
-    # learning rates stretched over them), about the float32 form's 500 iterations in wall time
-    long_opt = binding.default_options(bigm_iters=160, as_iters=640, omega=192, max_cuts=5, graph_chunk=25,
-                                       precision=16)
-    lc = binding.Context(prob["net"], prob["lo"], prob["hi"], prob["C"], options=long_opt, stream=stream)
-    lc.reset(t["lo"], t["hi"], t["C"])
-    reach = {k: np.full(S, np.nan) for k in targets}
-    elapsed = 0.0
-    for c0 in range(0, 800, chunk):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        lc.as_step(chunk)
-        e1.record()
-        e1.synchronize()
-        elapsed += e0.elapsed_time(e1)
-        lc.bound_into(64, bound)
-        b = bound.cpu().numpy()
-        for k, tg in targets.items():
-            new = np.isnan(reach[k]) & (b >= tg)
-            reach[k][new] = elapsed
-    fin = bound.cpu().numpy().copy()
-    out["bf16_800"] = {"ms": elapsed, "mean_final_bound": float(fin.mean()),
-                       "minus_fp32_final_bound_mean": float((fin - finals[32]).mean()), "time_to_bound_ms": {}}
-    for k, r in reach.items():
-        done = ~np.isnan(r)
-        out["bf16_800"]["time_to_bound_ms"][k] = {"reached": int(done.sum()), "of": S,
-                                                  "median": float(np.median(r[done])) if done.any() else None,
-                                                  "max": float(np.max(r[done])) if done.any() else None}
-    lc.close()
-    # per-kernel device time of 60 iterations (20 Big-M + 40 Active Set, 5 slots), each form
-    out["kernel_ms_60_iterations"] = {}
-    for prec in (32, 16):
-        popt = binding.default_options(bigm_iters=20, as_iters=40, omega=12, max_cuts=5, graph_chunk=0, profile=1,
-                                       precision=prec)
-        pc = binding.Context(prob["net"], prob["lo"], prob["hi"], prob["C"], options=popt, stream=stream)
-        pc.as_step(60)
-        out["kernel_ms_60_iterations"]["fp32" if prec == 32 else "bf16"] = {
-            k: v[0] for k, v in pc.kernel_times().items() if v[1]}
-        pc.close()
-    out["workload"] = {"net": "conv4", "subproblems": S, "iterations": iters, "eps": "8/255"}
-    for ctx in ctxs.values():
-        ctx.close()
-    return out
 
 
 def differentiation_run(binding, torch, dev, stream, rank):
@@ -522,41 +463,200 @@ def l2_run(binding, torch, dev, stream, rank):
             "unit": UNIT, "cpu_baseline": oracle_rate("wide_conv", "l2") if rank == 0 else None, **out}
 
 
-def hbm_rooflines(workload, kt):
-    """The HBM side of the roofline for every kernel with a committed DRAM capture: measured DRAM
-    bytes per launch (ncu, the captured build) over this run's mean launch duration (CUDA events),
-    against the measured copy bandwidth of MEASURED_PEAKS.json."""
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            peak, src = float(json.load(f)["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (of measured)"
-    except (OSError, KeyError, ValueError):
-        peak, src = 6800.0, "fallback 6.8 TB/s"
-    out = {}
-    for k, (tms, n) in kt.items():
-        t = captured_traffic(workload, k)
-        if t is None or not n or tms <= 0:
+def dense_nnz(L):
+    """Nonzeros of a layer's dense operator (taps inside the zero padding left out)."""
+    if L["kind"] == "linear":
+        return L["n_in"] * L["n_out"]
+    c, h, w = L["in_shape"]
+    oc, oh, ow = L["out_shape"]
+    cy = sum(1 for oy in range(oh) for ky in range(L["kh"]) if 0 <= oy * L["stride"] - L["pad"] + ky < h)
+    cx = sum(1 for ox in range(ow) for kx in range(L["kw"]) if 0 <= ox * L["stride"] - L["pad"] + kx < w)
+    return oc * c * cy * cx
+
+
+def conv4_slots(opt):
+    """Slots each Active Set iteration's col pass (before its addition) and row pass (after it)
+    consume, per global iteration (Alg. 1's addition schedule, one mask per iteration)."""
+    col, row = [], []
+    for it in range(opt.bigm_iters + opt.as_iters):
+        if it < opt.bigm_iters:
+            col.append(0)
+            row.append(0)
             continue
-        us = tms / n * 1e3
-        gbs = t / (us * 1e-6) / 1e9
-        out[k] = {"dram_bytes_per_launch": t, "launch_us": us, "achieved": gbs, "peak": peak, "unit": "GB/s",
-                  "frac": gbs / peak, "peak_source": src}
+        t = it - opt.bigm_iters
+        q, r = divmod(t, opt.omega)
+        before = min(q * opt.vars_per_add + min(r, opt.vars_per_add), opt.max_cuts)
+        add = 1 if (r < opt.vars_per_add and q * opt.vars_per_add + r < opt.max_cuts) else 0
+        col.append(before)
+        row.append(before + add)
+    return col, row
+
+
+def colA_bf16_bytes(net, ns, cap):
+    """Algorithmic DRAM bytes per subproblem of one BF16-form col-pass launch with ns slots: per input
+    j of every layer k (neuron layer k - 1): its box (8), snapshot and fixed bytes (2), x*, f written
+    (8); where layer k is hidden, the (1 + ns) W+ / W- products read (8 (1 + ns)) and the operand
+    planes written (2 signs x (1 + cap) slots x 2); where j is hidden, alpha, beta_0, beta_1, uhat,
+    lhat (20), the slots' beta and kappa (8 ns), z snapshot and z* (2); the output row's weight (4)."""
+    total = 0
+    n = len(net)
+    for k, L in enumerate(net, start=1):
+        per = 18
+        if k <= n - 1:
+            per += 8 * (1 + ns) + 4 * (1 + cap)
+        else:
+            per += 4
+        if k - 1 >= 1:
+            per += 22 + 8 * ns
+        total += per * L["n_in"]
+    return total
+
+
+def rowB_bf16_bytes(net, ns, cap):
+    """Algorithmic DRAM bytes per subproblem of one BF16-form row-pass launch with ns slots: per
+    hidden neuron, the (1 + ns) products (4 each), x* (4), z*, z snapshot (2), uhat, lhat (8), alpha,
+    beta_0, beta_1 and their six Adam moments read and written (72), the slots' beta, moments,
+    lambda, kappa read (20 ns) and beta, moments written (12 ns), the col pass's operand planes
+    written (2 (1 + cap))."""
+    nh = sum(L["n_out"] for L in net[:-1])
+    return nh * (4 * (1 + ns) + 4 + 2 + 8 + 72 + 32 * ns + 2 * (1 + cap))
+
+
+def tc_flops(net, ns):
+    """Algorithmic flops per subproblem of one launch group of the BF16 form's tensor-core products
+    (all hidden layers): W x* and the ns masked products, 2 (1 + ns) nnz (the sign split and the
+    channel padding the GEMMs also multiply are not counted)."""
+    return 2.0 * (1 + ns) * sum(dense_nnz(L) for L in net[:-1])
+
+
+def conv4_roofline(binding, torch, dev, net, S, kt, opt):
+    """The dominant kernel of a profiled step (per-kernel CUDA events) against its roofline."""
+    col, row = conv4_slots(opt)
+    peaks = measured_peaks()
+    total_ms = sum(v[0] for v in kt.values())
+    top = max(kt, key=lambda k: kt[k][0])
+    tms, n = kt[top]
+    out = {"kernel": top, "launches": n, "kernel_ms": tms,
+           "share_of_kernel_time": tms / total_ms if total_ms else None}
+    if top in ("as_colA", "as_rowB"):
+        if top == "as_colA":
+            ns_list = col + [col[-1]] * max(0, n - len(col))   # the bound's launch: the last slots
+            per = [colA_bf16_bytes(net, k, C4_CAP) for k in ns_list[:n]]
+        else:
+            per = [rowB_bf16_bytes(net, k, C4_CAP) for k in row[:n]]
+        algo = S * float(sum(per))
+        gbs = algo / (tms / 1e3) / 1e9
+        peak = float(peaks.get("hbm_gbs", 6800.0))
+        out.update({"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                    "bytes_per_launch": algo / n,
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks
+                    else "fallback 6.8 TB/s (of fallback)",
+                    "traffic": captured_traffic("conv4", top, S)})
+    elif top in ("tc_col", "tc_row"):
+        nsl = col if top == "tc_col" else row
+        layers = len(net) - 1
+        per_launch = [tc_flops(net, k) / layers for k in nsl for _ in range(layers)]
+        algo = S * float(sum(per_launch[:n]))
+        tf = algo / (tms / 1e3) / 1e12
+        peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1700.0)))
+        out.update({"bound": "tensor", "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
+                    "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured; timed inside a long step)",
+                    "traffic": captured_traffic("conv4", top, S)})
+    else:
+        flops = algorithmic_flops(net, S, top, row, n)
+        peak, src = fp32_peak_tflops(torch, dev)
+        tf = flops / (tms / 1e3) / 1e12 if tms > 0 else None
+        out.update({"bound": "alu", "achieved": tf, "peak": peak, "unit": "TFLOP/s",
+                    "frac": tf / peak if tf else None, "peak_source": src + " (derived)",
+                    "traffic": captured_traffic("conv4", top, S)})
     return out
 
 
-def captured_traffic(workload, kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu capture of this workload, or None
+def run_chunks(torch, ctx, batch, iters, chunk, bound):
+    """Iterations of a reset context in chunks, CUDA events around each chunk, the bound evaluated
+    after each (not timed): (elapsed ms, [(ms so far, bounds)] after every chunk)."""
+    lo, hi, C = batch
+    ctx.reset(lo, hi, C)
+    hist, elapsed = [], 0.0
+    for c0 in range(0, iters, chunk):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.as_step(min(chunk, iters - c0))
+        e1.record()
+        e1.synchronize()
+        elapsed += e0.elapsed_time(e1)
+        ctx.bound_into(64, bound)
+        hist.append((elapsed, bound.cpu().numpy().copy()))
+    return elapsed, hist
+
+
+def reach_summary(hist, targets):
+    """Per target: how many subproblems' bounds reached it, and the median and largest time at which
+    they first did."""
+    out = {}
+    for k, tg in targets.items():
+        r = np.full(tg.size, np.nan)
+        for ms, b in hist:
+            r[np.isnan(r) & (b >= tg)] = ms
+        done = ~np.isnan(r)
+        out[k] = {"reached": int(done.sum()), "of": int(r.size),
+                  "median_ms": float(np.median(r[done])) if done.any() else None,
+                  "max_ms": float(np.max(r[done])) if done.any() else None}
+    return out
+
+
+def forms_compare(binding, torch, prob, batch, S, stream):
+    """The plain float32 form and the BF16 form of the same Active Set schedule on the same batch:
+    subproblem-iterations/s (sums of chunk times) and the time to reach the float32 form's final
+    bound minus 1e-4 (absolute, and relative to 1 + |bound|: bounds here are 1e4-1e5, where 1e-4
+    is below a float32 ulp); the BF16 form also on an 800-iteration schedule of its own (160 Big-M
+    + 640 Active Set, omega 192), which it runs in less time than the float32 form's 500."""
+    iters, chunk = C4_BIGM + C4_AS, 25
+    bound = torch.zeros(S, dtype=torch.float64, device="cuda")
+    runs = {}
+    for key, opt, n in (("fp32", conv4_options(binding, 32), iters), ("bf16", conv4_options(binding, 16), iters),
+                        ("bf16_800", conv4_options(binding, 16, bigm=160, as_iters=640, omega=192), 800)):
+        ctx = binding.Context(prob["net"], prob["lo"], prob["hi"], prob["C"], options=opt, stream=stream)
+        runs[key] = (n,) + run_chunks(torch, ctx, batch, n, chunk, bound)
+        ctx.close()
+    fin32 = runs["fp32"][2][-1][1]
+    targets = {"abs_1e-4": fin32 - 1e-4, "rel_1e-4": fin32 - 1e-4 * (1 + np.abs(fin32))}
+    out = {}
+    for key, (n, ms, hist) in runs.items():
+        fin = hist[-1][1]
+        gap = fin - fin32
+        out[key] = {"value": S * n / (ms / 1e3), "unit": UNIT, "ms": ms, "iterations": n,
+                    "mean_final_bound": float(fin.mean()), "time_to_bound": reach_summary(hist, targets),
+                    "minus_fp32_final_bound": {"mean": float(gap.mean()), "min": float(gap.min()),
+                                               "max": float(gap.max())}}
+    t32 = out["fp32"]["time_to_bound"]["rel_1e-4"]["max_ms"]
+    t16 = out["bf16_800"]["time_to_bound"]["rel_1e-4"]
+    out["time_to_bound"] = {
+        "target": "every box's float32-form final bound minus 1e-4 (1 + |bound|), bound re-evaluated in float32",
+        "fp32_ms": t32, "bf16_ms": t16["max_ms"] if t16["reached"] == S else None,
+        "bf16_reached": t16["reached"], "of": S,
+        "speedup": (t32 / t16["max_ms"]) if (t32 and t16["reached"] == S) else None}
+    return out
+
+
+def captured_traffic(workload, kernel, S=None):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture of this workload (scaled from
+    the captured batch to S subproblems: the traffic of these passes grows with the batch), or None
     when there is none or the kernel source has changed since it was taken."""
     import hashlib
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles", f"dram_traffic_{workload}.json")
+    path = os.path.join(ROOT, "profiles", f"dram_traffic_{workload}.json")
     try:
         with open(path) as f:
             rec = json.load(f)
-        src = os.path.join(os.path.dirname(os.path.abspath(__file__)), rec["source"])
-        with open(src, "rb") as f:
-            if hashlib.sha256(f.read()).hexdigest() != rec["source_sha256"]:
-                return None
-        return rec["dram_bytes_per_launch"].get(kernel)
-    except (OSError, KeyError, ValueError):
+        for src in rec["sources"]:
+            with open(os.path.join(ROOT, src["path"]), "rb") as f:
+                if hashlib.sha256(f.read()).hexdigest() != src["sha256"]:
+                    return None
+        v = rec["dram_bytes_per_launch"].get(kernel)
+        if v is None:
+            return None
+        return v * (S / rec["subproblems"]) if S else v
+    except (OSError, KeyError, ValueError, TypeError):
         return None
 
 
@@ -571,23 +671,31 @@ def slowest_rank(values, dist, device):
     return t.tolist()
 
 
-def job_throughput(S_per_rank, world, ms_per_step):
-    """Whole-job subproblem-iterations per second: every rank bounds its own batch of S_per_rank
-    subproblems for iterations_per_step() iterations in ms_per_step (the slowest rank's)."""
-    return S_per_rank * iterations_per_step() * world / (ms_per_step / 1e3)
+def job_throughput(units_per_rank_step, world, ms_per_step):
+    """Whole-job subproblem-iterations per second: every rank does units_per_rank_step
+    subproblem-iterations per step in ms_per_step (the slowest rank's)."""
+    return units_per_rank_step * world / (ms_per_step / 1e3)
+
+
+SAMPLE_SCHEDULES = {
+    # (Big-M iterations, Active Set schedule length, omega, iterations at most) of the oracle sample
+    "wide_conv": (4, 200, 15, 40),
+    "conv4": (2, 200, 15, 3),
+}
 
 
 def _oracle_sample_code(prob_name, s, seconds_budget, variant=""):
     """A bounded oracle run on subproblem s: variant "" the workload itself, "l2" over the l2 ball
     inscribed in its box, "layer2" the intermediate-bounds subproblem of layer 2's first neuron
     (the sub-network up to the second layer, property row +e_0)."""
+    bigm, asi, omega, cap_it = SAMPLE_SCHEDULES.get(prob_name, SAMPLE_SCHEDULES["wide_conv"])
     return f"""
 import os, sys, time, json
 import numpy as np
 sys.path.insert(0, {ROOT!r})
 from oracle import active_set as AS, network as nw
 from paper_2101_05844_gb300 import synth
-prob = synth.problem({prob_name!r}, seed=0)
+prob = synth.problem({prob_name!r}, S={s} + 1, seed=0)
 t0 = time.time()
 net = prob["net"]
 if {variant!r} == "layer2":
@@ -598,10 +706,10 @@ else:
 dense = nw.dense_layers(net)
 P = nw.Problem(net, prob["lo"][{s}], prob["hi"][{s}], crow, dense=dense, ball={variant!r} == "l2")
 setup = time.time() - t0
-opt = AS.Options(bigm_iters=4, as_iters=200, omega=15, max_cuts=5)
+opt = AS.Options(bigm_iters={bigm}, as_iters={asi}, omega={omega}, max_cuts=5)
 st = AS.ActiveSet(P, opt)
 t0 = time.time(); n = 0
-while n < 40 and (time.time() - t0) < {seconds_budget}:
+while n < {cap_it} and (time.time() - t0) < {seconds_budget}:
     st.step(1); n += 1
 dt = time.time() - t0
 print(json.dumps({{"iters": n, "seconds": dt, "setup_s": setup}}))
@@ -621,38 +729,53 @@ def oracle_rate(prob_name, variant, seconds_budget=10.0):
             "sample": f"one subproblem, {d['iters']} iterations, FP64 numpy, single thread; {d['seconds']:.1f} s"}
 
 
-def cpu_baseline(prob_name, seconds_budget=20.0):
+def _mem_available_gb():
+    try:
+        with open("/proc/meminfo") as f:
+            for ln in f:
+                if ln.startswith("MemAvailable:"):
+                    return int(ln.split()[1]) / 2 ** 20
+    except (OSError, ValueError):
+        pass
+    return 0.0
+
+
+def cpu_baseline(prob_name, seconds_budget=20.0, all_cores=True):
     """Times the CPU oracle, single-threaded, on a bounded sample of the workload: one subproblem,
-    a few Big-M then Active Set iterations (with the two first mask additions). As context, the
-    same sample on every subproblem at once, one single-threaded process each on the host's cores
-    (fresh interpreters, started after the GPU work: nothing is forked from a CUDA process)."""
+    a few Big-M then Active Set iterations (the first with a mask addition; the dense operators are
+    built before the timer starts). As context, the same sample on several subproblems at once, one
+    single-threaded process each, on as many host cores as memory allows (fresh interpreters, started
+    after the GPU work: nothing is forked from a CUDA process)."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
     r = subprocess.run([sys.executable, "-c", _oracle_sample_code(prob_name, 0, seconds_budget)],
-                       capture_output=True, text=True, env=env, timeout=600)
+                       capture_output=True, text=True, env=env, timeout=900)
     if r.returncode != 0:
         return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": r.stderr[-300:]}
     d = json.loads(r.stdout.strip().splitlines()[-1])
+    bigm = SAMPLE_SCHEDULES.get(prob_name, SAMPLE_SCHEDULES["wide_conv"])[0]
     out = {"value": d["iters"] / d["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
-           "sample": f"1 of the 9 subproblems, {d['iters']} iterations (4 Big-M, then Active Set, masks "
-                     f"added at Active Set iterations 0, 1, 15, 16, 30), FP64 numpy, dense conv "
-                     f"operators, single thread; {d['seconds']:.1f} s"}
-    from paper_2101_05844_gb300 import synth
-    S = synth.problem(prob_name, seed=0)["lo"].shape[0]
-    k = max(1, min(os.cpu_count() or 1, S))
-    procs = [subprocess.Popen([sys.executable, "-c", _oracle_sample_code(prob_name, q, seconds_budget / 2)],
+           "sample": f"subproblem 0 of the {prob_name} batch, {d['iters']} iterations ({bigm} Big-M, then Active "
+                     f"Set with a mask added at its first iteration), FP64 numpy, dense operators (built in "
+                     f"{d['setup_s']:.1f} s, not timed), single thread; {d['seconds']:.1f} s"}
+    if not all_cores:
+        return out
+    per_gb = 10.0 if prob_name == "conv4" else 1.0
+    k = max(1, min(os.cpu_count() or 1, int(_mem_available_gb() // per_gb), 16))
+    procs = [subprocess.Popen([sys.executable, "-c", _oracle_sample_code(prob_name, q, seconds_budget)],
                               stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env)
              for q in range(k)]
     rates = []
     for p in procs:
-        so, _ = p.communicate(timeout=600)
+        so, _ = p.communicate(timeout=900)
         if p.returncode == 0:
             e = json.loads(so.strip().splitlines()[-1])
             rates.append(e["iters"] / e["seconds"])
     if len(rates) == k:
         out["all_cores"] = {"value": sum(rates), "unit": UNIT, "cores": k, "host_cores": os.cpu_count(),
                             "sample": f"the same sample on {k} subproblems at once, one single-threaded "
-                                      f"process each; the sum of their rates"}
+                                      f"process each (as many as the host's memory allows, at most its "
+                                      f"cores); the sum of their rates"}
     return out
 
 
@@ -660,14 +783,59 @@ def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    cb = cpu_baseline(args.workload, seconds_budget=max(10.0, 20.0 / max(1, args.steps)))
+    cb = cpu_baseline(args.workload, seconds_budget=max(10.0, 25.0 / max(1, args.steps)), all_cores=False)
+    S = args.subproblems if args.workload == "conv4" else 9
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "subproblems": 9, "note": "CPU oracle, bounded sample"},
+            "config": {"workload": args.workload, "subproblems": S, "note": "CPU oracle, bounded sample"},
             "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
                                           "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+def wide_conv_run(binding, torch, dev, rank, steps, warmup, flush):
+    """The Wide conv net's 9 properties (one box, the earlier headline): an Active Set solve
+    (200 Big-M + 800 Active Set) and a Saddle Point solve (200 Big-M + 1000 Saddle Point) per step
+    on two streams, timed like the default workload."""
+    from paper_2101_05844_gb300 import synth
+    prob = synth.problem("wide_conv", seed=rank)
+    S = prob["lo"].shape[0]
+    batch = tuple(torch.from_numpy(prob[k]).to(dev) for k in ("lo", "hi", "C"))
+    outs = [torch.zeros(S, dtype=torch.float64, device=dev) for _ in range(2)]
+    as_opt, sp_opt = workload_options(binding)
+    s_as, s_sp = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    ctx_as = binding.Context(prob["net"], prob["lo"], prob["hi"], prob["C"], options=as_opt, stream=s_as.cuda_stream)
+    ctx_sp = binding.Context(prob["net"], prob["lo"], prob["hi"], prob["C"], options=sp_opt, stream=s_sp.cuda_stream)
+    main = torch.cuda.current_stream(dev)
+    for _ in range(warmup):
+        wide_step(ctx_as, ctx_sp, batch, outs[0], outs[1])
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(main)
+        s_as.wait_event(e0)
+        s_sp.wait_event(e0)
+        wide_step(ctx_as, ctx_sp, batch, outs[0], outs[1])
+        main.wait_stream(s_as)
+        main.wait_stream(s_sp)
+        e1.record(main)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = sum(times) / len(times)
+    iters = AS_BIGM + AS_ITERS + SP_BIGM + SP_ITERS
+    out = {"workload": "wide_conv: 3x32x32 -> conv16 4x4/2 -> conv32 4x4/2 -> FC100 -> FC10, one box of "
+                       "half-width 2/255, its 9 logit-difference properties",
+           "value": S * iters / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "subproblems": S,
+           "iterations_per_step": {"active_set": AS_BIGM + AS_ITERS, "big_m_before_sp": SP_BIGM,
+                                   "saddle_point": SP_ITERS},
+           "bounds": {"active_set": [float(v) for v in outs[0].cpu()], "saddle_point": [float(v) for v in outs[1].cpu()]}}
+    ctx_as.close()
+    ctx_sp.close()
+    return out
 
 
 def main():
@@ -676,13 +844,16 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="wide_conv")
+    ap.add_argument("--workload", default="conv4", choices=["conv4", "wide_conv"],
+                    help="conv4: the default step (1024 boxes); wide_conv: the reference arm's oracle sample "
+                         "on the Wide conv net")
+    ap.add_argument("--subproblems", type=int, default=C4_S,
+                    help="boxes of the conv4 batch (1024; fewer only for a profiler capture)")
+    ap.add_argument("--profile-only", action="store_true",
+                    help="only warm-up and timed steps of the conv4 workload, nothing else (profiler captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precision", action="store_true",
-                    help="also time the precision workload: conv4 on 1024 boxes, float32 against the "
-                         "BF16 form, subproblem-iterations/s and time to the float32 bound")
-    ap.add_argument("--precision-subproblems", type=int, default=1024,
-                    help="boxes of the precision form (1024 by default; fewer for a profiler capture)")
+    ap.add_argument("--no-forms", action="store_true", help="skip the float32 / BF16 comparison")
+    ap.add_argument("--no-wide", action="store_true", help="skip the Wide conv extra key")
     ap.add_argument("--differentiation", action="store_true",
                     help="also time the differentiation workload: MLP 784-1024x3-10, 256 boxes, 300 "
                          "Active Set iterations, then the bound and its envelope gradient")
@@ -695,16 +866,16 @@ def main():
                     help="also run branch and bound with stratified bounding on the wide conv net's 9 properties")
     ap.add_argument("--bab-time", type=float, default=10.0, help="time limit per property of --bab (seconds)")
     ap.add_argument("--l2", action="store_true",
-                    help="also time the headline Active Set schedule over the l2 ball inscribed in each box")
+                    help="also time the Wide conv Active Set schedule over the l2 ball inscribed in each box")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)
         return
 
-    import numpy as np
     import torch
 
     from paper_2101_05844_gb300 import binding, synth
+    from paper_2101_05844_gb300.shard import gather_bounds, shard_batch
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -715,26 +886,20 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     binding.lib()
-
-    prob = synth.problem(args.workload, seed=rank)   # each rank bounds its own batch (weak scaling)
-    S = prob["lo"].shape[0]
     dev = torch.device("cuda", local)
-    lo_d = torch.from_numpy(prob["lo"]).to(dev)
-    hi_d = torch.from_numpy(prob["hi"]).to(dev)
-    C_d = torch.from_numpy(prob["C"]).to(dev)
-    lo_h = torch.from_numpy(prob["lo"]).pin_memory()
-    hi_h = torch.from_numpy(prob["hi"]).pin_memory()
-    C_h = torch.from_numpy(prob["C"]).pin_memory()
+
+    # one batch of world x subproblems boxes; each rank bounds its contiguous slice (weak scaling:
+    # the slice stays the same size as ranks are added) and the bounds are gathered once per step
+    a, b = shard_batch(args.subproblems * world, world, rank)
+    S = b - a
+    prob = synth.problem("conv4", S=args.subproblems * world, seed=0, part=(a, b))
+    batch_d = tuple(torch.from_numpy(prob[k]).to(dev) for k in ("lo", "hi", "C"))
+    batch_h = tuple(torch.from_numpy(prob[k]).pin_memory() for k in ("lo", "hi", "C"))
     out_d = [torch.zeros(S, dtype=torch.float64, device=dev) for _ in range(2)]
     out_h = [torch.zeros(S, dtype=torch.float64).pin_memory() for _ in range(2)]
-    as_opt, sp_opt = workload_options(binding)
-    stream = torch.cuda.current_stream().cuda_stream
-    # the step's two solves on streams of their own (joined to the timing stream by events)
-    s_as, s_sp = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
-    ctx_as = binding.Context(prob["net"], prob["lo"], prob["hi"], prob["C"], options=as_opt,
-                             stream=s_as.cuda_stream)
-    ctx_sp = binding.Context(prob["net"], prob["lo"], prob["hi"], prob["C"], options=sp_opt,
-                             stream=s_sp.cuda_stream)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    ctx = binding.Context(prob["net"], prob["lo"], prob["hi"], prob["C"], options=conv4_options(binding, 16),
+                          stream=stream)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
 
     def barrier():
@@ -743,88 +908,85 @@ def main():
         torch.cuda.synchronize()
 
     def timed(batch, outs, k):
-        times = []
-        main = torch.cuda.current_stream(dev)
+        times, parts = [], []
         for _ in range(k):
             flush.fill_(1.0)                      # evict L2 between steps
             torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(main)
-            s_as.wait_event(e0)
-            s_sp.wait_event(e0)
-            run_step(ctx_as, ctx_sp, batch, outs[0], outs[1])
-            main.wait_stream(s_as)
-            main.wait_stream(s_sp)
-            e1.record(main)
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1))
-        return times
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            conv4_step(ctx, batch, outs[0], outs[1], ev)
+            if dist:     # the job's best bound per box, in batch order, on every rank (its only collective)
+                gather_bounds(torch.maximum(outs[0], outs[1]).to(dev), args.subproblems * world, dist)
+                ev[2].record()
+            ev[2].synchronize()
+            times.append(ev[0].elapsed_time(ev[2]))
+            parts.append((ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])))
+        return times, parts
 
-    torch.cuda.synchronize()
     for _ in range(args.warmup):
-        run_step(ctx_as, ctx_sp, (lo_d, hi_d, C_d), out_d[0], out_d[1])
+        conv4_step(ctx, batch_d, out_d[0], out_d[1])
     barrier()
-    l0 = ctx_as.launch_count() + ctx_sp.launch_count()
+    l0 = ctx.launch_count()
     with ClockSampler(local) as clk:
         barrier()
-        times = timed((lo_d, hi_d, C_d), out_d, args.steps)
+        times, parts = timed(batch_d, out_d, args.steps)
         barrier()
-    launches = ctx_as.launch_count() + ctx_sp.launch_count() - l0
-    # end to end through the API with host buffers
+    launches = ctx.launch_count() - l0
+    if args.profile_only:
+        if rank == 0:
+            print(json.dumps({"profile_only": True, "ms_per_step": sum(times) / len(times), "subproblems": S}))
+        return
+    # end to end through the API with the batch in pinned host memory and the bounds read back
     for _ in range(max(1, args.warmup // 2)):
-        run_step(ctx_as, ctx_sp, (lo_h, hi_h, C_h), out_h[0], out_h[1])
+        conv4_step(ctx, batch_h, out_h[0], out_h[1])
     barrier()
-    e2e_times = timed((lo_h, hi_h, C_h), out_h, args.steps)
+    e2e_times, _ = timed(batch_h, out_h, args.steps)
     barrier()
-    bounds_as = out_h[0].numpy().copy()
-    bounds_sp = out_h[1].numpy().copy()
+    bounds_as, bounds_sp = out_h[0].numpy().copy(), out_h[1].numpy().copy()
 
+    per_step = S * (C4_BIGM + C4_AS + C4_SP_ITERS)
     ms, ms_e2e = slowest_rank([sum(times) / len(times), sum(e2e_times) / len(e2e_times)], dist, dev)
-    value = job_throughput(S, world, ms)
-    e2e_value = job_throughput(S, world, ms_e2e)
+    value = job_throughput(per_step, world, ms)
+    ms_as = sum(p[0] for p in parts) / len(parts)
+    ms_sp = sum(p[1] for p in parts) / len(parts)
 
-    # per-kernel device time for the roofline: one profiled step (CUDA events around each launch)
-    as_p, sp_p = workload_options(binding, profile=1)
-    pa = binding.Context(prob["net"], prob["lo"], prob["hi"], prob["C"], options=as_p, stream=stream)
-    ps = binding.Context(prob["net"], prob["lo"], prob["hi"], prob["C"], options=sp_p, stream=stream)
-    run_step(pa, ps, (lo_d, hi_d, C_d), out_d[0], out_d[1])
-    kt = {}
-    for ctx in (pa, ps):
-        for name, (tms, n) in ctx.kernel_times().items():
-            a, b = kt.get(name, (0.0, 0))
-            kt[name] = (a + tms, b + n)
-    top = max(kt, key=lambda k: kt[k][0])
-    sched = slots_schedule(as_opt)
-    tms, n = kt[top]
-    flops = algorithmic_flops(prob["net"], S, top, sched, n)
-    peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * 2.07e9 / 1e12
-    achieved = flops / (tms / 1e3) / 1e12 if tms > 0 else None
-    step_kernel_ms = sum(v[0] for v in kt.values())
+    # per-kernel device time of one profiled step (CUDA events around each launch) for the roofline
+    popt = conv4_options(binding, 16, profile=1, graph_chunk=0)
+    pc = binding.Context(prob["net"], prob["lo"], prob["hi"], prob["C"], options=popt, stream=stream)
+    conv4_step(pc, batch_d, out_d[0], out_d[1])
+    kt = {k: v for k, v in pc.kernel_times().items() if v[1]}
+    pc.close()
+    roof = conv4_roofline(binding, torch, dev, prob["net"], S, kt, popt)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": args.workload, "subproblems_per_gpu": S,
-                   "iterations_per_step": {"active_set": AS_BIGM + AS_ITERS, "big_m_before_sp": SP_BIGM,
-                                           "saddle_point": SP_ITERS},
-                   "l2": "flushed between timed steps (write of 2x L2)", "parallelism": f"replicas x{world}",
-                   "team_targets": {"active_set": list(ctx_as.team_targets()),
-                                    "saddle_point": list(ctx_sp.team_targets())}},
-        "e2e": {"value": e2e_value, "unit": UNIT, "ms_per_step": ms_e2e,
-                "h2d_bytes_per_step": 2 * (lo_h.numel() * 4 + hi_h.numel() * 4 + C_h.numel() * 4),
+        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": "conv4", "net": "3x32x32 -> 4 conv 3x3 (32, 32, 64, 64; s1, s2, s1, s2) -> FC512 -> FC10",
+                   "subproblems_per_gpu": S, "eps": "8/255",
+                   "iterations_per_step": {"big_m": C4_BIGM, "active_set": C4_AS, "saddle_point": C4_SP_ITERS,
+                                           "saddle_point_primal_init_steps": C4_SP_INIT},
+                   "form": "BF16 products on the tensor cores, float32 duals and Adam, bound in float32 with "
+                           "float64 summation; Saddle Point in float32",
+                   "l2": "flushed between timed steps (write of 2x L2); the batch's state is several GB",
+                   "parallelism": f"batch sharded over {world} GPU(s): contiguous slices, network replicated, "
+                                  f"one gather of the bounds per step"},
+        "parts": {"active_set_bf16": {"ms": ms_as, "value": S * (C4_BIGM + C4_AS) / (ms_as / 1e3), "unit": UNIT},
+                  "saddle_point": {"ms": ms_sp, "value": S * C4_SP_ITERS / (ms_sp / 1e3), "unit": UNIT,
+                                   "note": "conversion, primal initialisation and iterations"}},
+        "e2e": {"value": job_throughput(per_step, world, ms_e2e), "unit": UNIT, "ms_per_step": ms_e2e,
+                "h2d_bytes_per_step": sum(t.numel() * t.element_size() for t in batch_h),
                 "d2h_bytes_per_step": 2 * S * 8},
         "gpu_launches": launches,
-        "roofline": {"bound": "alu", "kernel": top, "achieved": achieved, "peak": peak_tflops,
-                     "unit": "TFLOP/s", "frac": (achieved / peak_tflops) if achieved else None,
-                     "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (derived)",
-                     "traffic": captured_traffic(args.workload, top), "launches": n, "kernel_ms": tms,
-                     "share_of_kernel_time": tms / step_kernel_ms if step_kernel_ms else None},
-        "roofline_hbm": hbm_rooflines(args.workload, kt),
-        "kernel_ms_per_step": {k: v[0] for k, v in kt.items() if v[1]},
+        "roofline": roof,
+        "kernel_ms_per_step": {k: v[0] for k, v in kt.items()},
         "clocks": clk.summary(),
-        "bounds": {"active_set": [float(v) for v in bounds_as], "saddle_point": [float(v) for v in bounds_sp]},
+        "bounds": {"active_set_mean": float(bounds_as.mean()), "saddle_point_mean": float(bounds_sp.mean())},
     }
+    ctx.close()
+    if not args.no_forms:
+        line["forms"] = forms_compare(binding, torch, prob, batch_d, S, stream)
+    if not args.no_wide:
+        line["wide_conv"] = wide_conv_run(binding, torch, dev, rank, args.steps, args.warmup, flush)
     if args.batched:
         line["batched"] = batched_run(binding, torch, dev, stream, rank)
     if args.differentiation:
@@ -835,14 +997,10 @@ def main():
         line["bab"] = bab_run(binding, torch, dev, stream, rank, args.bab_time)
     if args.intermediate:
         line["intermediate"] = intermediate_run(binding, torch, dev, stream, rank)
-    if args.precision:
-        line["precision"] = precision_run(binding, torch, dev, stream, rank, S=args.precision_subproblems)
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.workload)
+        line["cpu_baseline"] = cpu_baseline("conv4", seconds_budget=25.0)
     if rank == 0:
         print(json.dumps(line))
-    for c in (ctx_as, ctx_sp, pa, ps):
-        c.close()
     if dist:
         dist.destroy_process_group()
 

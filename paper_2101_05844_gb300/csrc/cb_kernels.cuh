@@ -99,6 +99,7 @@ __global__ void k_ibp(DNet net, DState st, int li, const signed char* splits) {
     const float* lo = st.lo + (size_t)s * net.NT + L.in_off;
     const float* hi = st.hi + (size_t)s * net.NT + L.in_off;
     double a = 0.0, c = 0.0;
+    int nf = 0;
     const bool ell = net.ball && li == 0;
     row_walk(L, i, lane, [&](int j, float w) {
         const double wd = w;
@@ -108,9 +109,19 @@ __global__ void k_ibp(DNet net, DState st, int li, const signed char* splits) {
             c += wd * wd * e * e;
         } else if (w >= 0.f) { a += wd * lo[j]; c += wd * hi[j]; }
         else { a += wd * hi[j]; c += wd * lo[j]; }
+        nf += (w != 0.f && lo[j] != hi[j]) ? 1 : 0;
     });
     a = warp_sum(a);
     c = warp_sum(c);
+    for (int o = 16; o > 0; o >>= 1) nf += __shfl_xor_sync(0xffffffffu, nf, o);
+    if (lane == 0 && !ell) {
+        // the row constants of the batch, the same sums before the bias (k_lz computes them alone
+        // for caller-given bounds and over an ellipsoid's layer 1)
+        const size_t h = (size_t)s * net.NH + L.h_out + i;
+        st.lz[h] = (float)a;
+        st.uz[h] = (float)c;
+        st.nfree[h] = nf;
+    }
     if (lane == 0) {
         if (ell) {   // the exact range of W_i x + b over {sum ((x - c) / e)^2 <= 1}: W_i c + b -+ |W_i D|
             const double r = sqrt(c);

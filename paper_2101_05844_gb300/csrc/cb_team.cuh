@@ -227,6 +227,34 @@ __device__ __forceinline__ void load_taps(const int2* tap, int t, int tb, int T,
     }
 }
 
+// ---------------------------------------------------------------- BF16 form: staged plane stores
+// A block of the BF16 form's conv passes is one tile of 8 channels (its warps) x 32 positions (its
+// lanes) of one subproblem (tc_tile_unit). The channels-last bf16 planes hold the 8 channels of a
+// position in one 16-byte piece, so the block gathers its values in shared memory, position-major,
+// and stores whole pieces: one 16-byte store per (plane, position) instead of eight 2-byte stores
+// scattered a channel stride apart.
+constexpr int CB_STAGE_PLANES = 2 * (CB_MAXCUT + 1);
+struct TcStage {
+    __align__(16) uint16_t v[CB_STAGE_PLANES][CB_THREADS];
+};
+// this thread's entry of plane e: position (lane) major, channel (warp) minor
+__device__ __forceinline__ uint16_t& stage_at(TcStage& st, int e) {
+    return st.v[e][(threadIdx.x & 31) * 8 + (threadIdx.x >> 5)];
+}
+__device__ __forceinline__ uint16_t bf16_bits_rn(float v) {
+    return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+}
+// Stores planes 0 .. nplanes - 1 of the stage: plane e of the tile goes to dst(e) + the position's
+// offset; pos_off(p) gives the element offset of position p (channel octet cb of the tile added).
+template <class Dst, class PosOff>
+__device__ __forceinline__ void stage_store(const TcStage& st, int nplanes, int P, int pb, Dst dst, PosOff pos_off) {
+    for (int c = threadIdx.x; c < nplanes * 32; c += CB_THREADS) {
+        const int e = c >> 5, pos = c & 31, p = pb * 32 + pos;
+        if (p >= P) continue;
+        *reinterpret_cast<uint4*>(dst(e) + pos_off(p)) = *reinterpret_cast<const uint4*>(&st.v[e][pos * 8]);
+    }
+}
+
 // ---------------------------------------------------------------- Active Set col pass (phase A)
 // The masked backward product of eq. (6) for input j, regrouped by the sign of W: at binary
 // iterates eq. (3) gives I_b(i, j) = 1 on rows with z_b[i] = 1 (their beta is in the record's
@@ -237,7 +265,8 @@ __device__ __forceinline__ void load_taps(const int2* tap, int t, int tb, int T,
 // with no per-pair mask work; the input's own bits pick p_b Pp_b + q_b Pn_b at the end.
 template <int NS>
 __device__ __forceinline__ void as_colA_body(const DNet& net, const DState& st, const DSched& sc, const DLayer& L,
-                                             int k, bool valid, int s, int j, int lane, int T, int mode, bool tc) {
+                                             int k, bool valid, int s, int j, int lane, int T, int mode, bool tc,
+                                             TcStage* stg) {
     const int m = k - 1;
     const Step sp = cb_step(st.ctr[0], sc, st.lr_tab);
     const size_t NT = net.NT, NH = net.NH, cap = net.cap;
@@ -394,8 +423,13 @@ __device__ __forceinline__ void as_colA_body(const DNet& net, const DState& st, 
             for (int t = 0; t <= net.cap; ++t) {
                 const long long pl = ((long long)t * net.S + s) * 2;
                 const bool p = t == 0 || ((mpos >> (t - 1)) & 1u), qq = t == 0 || ((mneg >> (t - 1)) & 1u);
-                X[pl * B.PX + off] = p ? xb : zero;
-                X[(pl + 1) * B.PX + off] = qq ? xb : zero;
+                if (stg) {   // conv tile: the block stores whole 16-byte pieces after the body
+                    stage_at(*stg, 2 * t) = __bfloat16_as_ushort(p ? xb : zero);
+                    stage_at(*stg, 2 * t + 1) = __bfloat16_as_ushort(qq ? xb : zero);
+                } else {
+                    X[pl * B.PX + off] = p ? xb : zero;
+                    X[(pl + 1) * B.PX + off] = qq ? xb : zero;
+                }
             }
             // the new slot's float32 lambda, kappa (k_slot_sums_t after the row pass) walk these records
             if (add_iter)
@@ -515,9 +549,11 @@ __device__ __forceinline__ int tseg_of(const TSegs& sg, int blk) {
 
 // Col pass over layers k = 1..n (phase A of an iteration, or the bound evaluation with mode 1):
 // f_m for every neuron j of layer m = k-1 (Sec. 4.1), x*, z* (eqs. 7-8), per-neuron bound terms
-// (eq. 6) and, on addition iterations, the new slot's snapshot bits (Alg. 1, Prop. 1).
-__global__ void __launch_bounds__(CB_THREADS, 4) k_as_colA_t(DNet net, DState st, DSched sc, TSegs sg, int mode,
-                                                              int tc) {
+// (eq. 6) and, on addition iterations, the new slot's snapshot bits (Alg. 1, Prop. 1). TC: the
+// BF16 form (sums from the tensor-core products, one lane per unit, conv layers in tiles).
+template <bool TC>
+__global__ void __launch_bounds__(CB_THREADS, 4) k_as_colA_t(DNet net, DState st, DSched sc, TSegs sg,
+                                                                       int mode) {
     const int q = tseg_of(sg, blockIdx.x);
     const int li = sg.layer[q];
     const DLayer& L = net.L[li];
@@ -526,24 +562,45 @@ __global__ void __launch_bounds__(CB_THREADS, 4) k_as_colA_t(DNet net, DState st
     const int unit = t / T, lane = t - unit * T;
     bool valid = unit < net.S * L.n_in;
     int s = valid ? unit / L.n_in : 0, o = valid ? unit - s * L.n_in : 0;
-    if (tc && L.kind == 1) {   // one lane per unit, tiled
+    const bool staged = TC && L.kind == 1 && li + 1 <= net.n - 1;
+    __shared__ TcStage stage;
+    if (TC && L.kind == 1) {   // one lane per unit, tiled
         o = tc_tile_unit(t, L.ci, L.hi * L.wi, net.S, s);
         valid = o >= 0;
         o = valid ? o : 0;
     }
+    if (staged)   // zeros stay where the tile has no unit (channel padding)
+        for (int e = 0; e < 2 * (net.cap + 1); ++e) stage_at(stage, e) = 0;
+    TcStage* stg = staged ? &stage : nullptr;
     const int j = (valid && sg.perm[q]) ? sg.perm[q][o] : o;
     const Step sp = cb_step(st.ctr[0], sc, st.lr_tab);
     const int ns = min(sp.nadd_before, sc.maxcut);
     switch (ns) {
-        case 0: as_colA_body<0>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, tc != 0); break;
-        case 1: as_colA_body<1>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, tc != 0); break;
-        case 2: as_colA_body<2>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, tc != 0); break;
-        case 3: as_colA_body<3>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, tc != 0); break;
-        case 4: as_colA_body<4>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, tc != 0); break;
-        case 5: as_colA_body<5>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, tc != 0); break;
-        case 6: as_colA_body<6>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, tc != 0); break;
-        case 7: as_colA_body<7>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, tc != 0); break;
-        default: as_colA_body<8>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, tc != 0); break;
+        case 0: as_colA_body<0>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, TC, stg); break;
+        case 1: as_colA_body<1>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, TC, stg); break;
+        case 2: as_colA_body<2>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, TC, stg); break;
+        case 3: as_colA_body<3>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, TC, stg); break;
+        case 4: as_colA_body<4>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, TC, stg); break;
+        case 5: as_colA_body<5>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, TC, stg); break;
+        case 6: as_colA_body<6>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, TC, stg); break;
+        case 7: as_colA_body<7>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, TC, stg); break;
+        default: as_colA_body<8>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, TC, stg); break;
+    }
+    if (staged) {
+        __syncthreads();
+        const BfLayer& B = net.bf[li];
+        const int ncb = (L.ci + 7) >> 3, npb = (L.hi * L.wi + 31) >> 5;
+        const int tile = (blockIdx.x - sg.start[q]), ts = tile / (ncb * npb);
+        const int rem = tile - ts * (ncb * npb), cb = rem / npb, pb = rem - cb * npb;
+        if (ts < net.S) {
+            uint16_t* X = B.X;
+            stage_store(stage, 2 * (net.cap + 1), L.hi * L.wi, pb,
+                        [&](int e) { return X + (((long long)(e >> 1) * net.S + ts) * 2 + (e & 1)) * B.PX; },
+                        [&](int p) {
+                            const int y = p / L.wi, x = p - y * L.wi;
+                            return ((long long)(y + L.pd) * L.Wp + (x + L.pd)) * B.Cip + cb * 8;
+                        });
+        }
     }
 }
 
@@ -562,7 +619,7 @@ __global__ void __launch_bounds__(CB_THREADS, 4) k_as_colA_t(DNet net, DState st
 template <int NS, bool ADD>
 __device__ __forceinline__ void as_rowB_body(const DNet& net, const DState& st, const DSched& sc, const DLayer& L,
                                              int li, bool valid, int s, int i, int lane, int T, const Step& sp, int it,
-                                             bool tc) {
+                                             bool tc, TcStage* stg) {
     const size_t NT = net.NT, NH = net.NH, cap = net.cap;
     const int cap_s = valid ? st.caps[s] : 0;
     const int newb = (ADD && sp.b_new < cap_s) ? sp.b_new : -1;
@@ -638,7 +695,9 @@ __device__ __forceinline__ void as_rowB_body(const DNet& net, const DState& st, 
             roff = ((long long)(oy + L.hl) * L.Wpo + (ox + L.wl)) * net.bf[li].Cop + co;
         }
         auto put = [&](int e, float v) {
-            if (tc)
+            if (tc && stg)   // conv tile: the block stores whole 16-byte pieces after the body
+                stage_at(*stg, e) = bf16_bits_rn(v);
+            else if (tc)
                 reinterpret_cast<__nv_bfloat16*>(net.bf[li].R)[((long long)e * net.S + s) * net.bf[li].PR + roff] =
                     __float2bfloat16_rn(v);
             else
@@ -759,7 +818,9 @@ __device__ __forceinline__ void as_rowB_body(const DNet& net, const DState& st, 
     }
     if (T > 1) contrib = team_sum(contrib, T);
     if (valid && lane == 0) {
-        if (tc) {
+        if (tc && stg) {
+            stage_at(*stg, 0) = bf16_bits_rn(contrib);
+        } else if (tc) {
             const BfLayer& B = net.bf[li];
             const int oy = p / L.wo, ox = p - (p / L.wo) * L.wo;
             const long long roff = ((long long)(oy + L.hl) * L.Wpo + (ox + L.wl)) * B.Cop + co;
@@ -770,7 +831,8 @@ __device__ __forceinline__ void as_rowB_body(const DNet& net, const DState& st, 
     }
 }
 
-__global__ void __launch_bounds__(CB_THREADS, 4) k_as_rowB_t(DNet net, DState st, DSched sc, TSegs sg, int tc) {
+template <bool TC>
+__global__ void __launch_bounds__(CB_THREADS, 4) k_as_rowB_t(DNet net, DState st, DSched sc, TSegs sg) {
     const int q = tseg_of(sg, blockIdx.x);
     const DLayer& L = net.L[sg.layer[q]];
     const int T = sg.T[q];
@@ -778,7 +840,9 @@ __global__ void __launch_bounds__(CB_THREADS, 4) k_as_rowB_t(DNet net, DState st
     const int unit = t / T, lane = t - unit * T;
     bool valid = unit < net.S * L.n_out;
     int s = valid ? unit / L.n_out : 0, i = valid ? unit - s * L.n_out : 0;
-    if (tc && L.kind == 1) {   // one lane per unit, tiled
+    const bool staged = TC && L.kind == 1;
+    __shared__ TcStage stage;
+    if (TC && L.kind == 1) {   // one lane per unit, tiled
         i = tc_tile_unit(t, L.co, L.ho * L.wo, net.S, s);
         valid = i >= 0;
         i = valid ? i : 0;
@@ -786,28 +850,48 @@ __global__ void __launch_bounds__(CB_THREADS, 4) k_as_rowB_t(DNet net, DState st
     const int it = st.ctr[0];
     const Step sp = cb_step(it, sc, st.lr_tab);
     const int ns = min(sp.nadd_before + (sp.b_new >= 0 ? 1 : 0), sc.maxcut);
+    if (staged)   // zeros stay where the tile has no unit (channel padding)
+        for (int e = 0; e <= ns; ++e) stage_at(stage, e) = 0;
+    TcStage* stg = staged ? &stage : nullptr;
+    const int li = sg.layer[q];
     if (sp.b_new >= 0) {
         switch (ns) {
-            case 1: as_rowB_body<1, true>(net, st, sc, L, sg.layer[q], valid, s, i, lane, T, sp, it, tc != 0); break;
-            case 2: as_rowB_body<2, true>(net, st, sc, L, sg.layer[q], valid, s, i, lane, T, sp, it, tc != 0); break;
-            case 3: as_rowB_body<3, true>(net, st, sc, L, sg.layer[q], valid, s, i, lane, T, sp, it, tc != 0); break;
-            case 4: as_rowB_body<4, true>(net, st, sc, L, sg.layer[q], valid, s, i, lane, T, sp, it, tc != 0); break;
-            case 5: as_rowB_body<5, true>(net, st, sc, L, sg.layer[q], valid, s, i, lane, T, sp, it, tc != 0); break;
-            case 6: as_rowB_body<6, true>(net, st, sc, L, sg.layer[q], valid, s, i, lane, T, sp, it, tc != 0); break;
-            case 7: as_rowB_body<7, true>(net, st, sc, L, sg.layer[q], valid, s, i, lane, T, sp, it, tc != 0); break;
-            default: as_rowB_body<8, true>(net, st, sc, L, sg.layer[q], valid, s, i, lane, T, sp, it, tc != 0); break;
+            case 1: as_rowB_body<1, true>(net, st, sc, L, li, valid, s, i, lane, T, sp, it, TC, stg); break;
+            case 2: as_rowB_body<2, true>(net, st, sc, L, li, valid, s, i, lane, T, sp, it, TC, stg); break;
+            case 3: as_rowB_body<3, true>(net, st, sc, L, li, valid, s, i, lane, T, sp, it, TC, stg); break;
+            case 4: as_rowB_body<4, true>(net, st, sc, L, li, valid, s, i, lane, T, sp, it, TC, stg); break;
+            case 5: as_rowB_body<5, true>(net, st, sc, L, li, valid, s, i, lane, T, sp, it, TC, stg); break;
+            case 6: as_rowB_body<6, true>(net, st, sc, L, li, valid, s, i, lane, T, sp, it, TC, stg); break;
+            case 7: as_rowB_body<7, true>(net, st, sc, L, li, valid, s, i, lane, T, sp, it, TC, stg); break;
+            default: as_rowB_body<8, true>(net, st, sc, L, li, valid, s, i, lane, T, sp, it, TC, stg); break;
         }
     } else {
         switch (ns) {
-            case 0: as_rowB_body<0, false>(net, st, sc, L, sg.layer[q], valid, s, i, lane, T, sp, it, tc != 0); break;
-            case 1: as_rowB_body<1, false>(net, st, sc, L, sg.layer[q], valid, s, i, lane, T, sp, it, tc != 0); break;
-            case 2: as_rowB_body<2, false>(net, st, sc, L, sg.layer[q], valid, s, i, lane, T, sp, it, tc != 0); break;
-            case 3: as_rowB_body<3, false>(net, st, sc, L, sg.layer[q], valid, s, i, lane, T, sp, it, tc != 0); break;
-            case 4: as_rowB_body<4, false>(net, st, sc, L, sg.layer[q], valid, s, i, lane, T, sp, it, tc != 0); break;
-            case 5: as_rowB_body<5, false>(net, st, sc, L, sg.layer[q], valid, s, i, lane, T, sp, it, tc != 0); break;
-            case 6: as_rowB_body<6, false>(net, st, sc, L, sg.layer[q], valid, s, i, lane, T, sp, it, tc != 0); break;
-            case 7: as_rowB_body<7, false>(net, st, sc, L, sg.layer[q], valid, s, i, lane, T, sp, it, tc != 0); break;
-            default: as_rowB_body<8, false>(net, st, sc, L, sg.layer[q], valid, s, i, lane, T, sp, it, tc != 0); break;
+            case 0: as_rowB_body<0, false>(net, st, sc, L, li, valid, s, i, lane, T, sp, it, TC, stg); break;
+            case 1: as_rowB_body<1, false>(net, st, sc, L, li, valid, s, i, lane, T, sp, it, TC, stg); break;
+            case 2: as_rowB_body<2, false>(net, st, sc, L, li, valid, s, i, lane, T, sp, it, TC, stg); break;
+            case 3: as_rowB_body<3, false>(net, st, sc, L, li, valid, s, i, lane, T, sp, it, TC, stg); break;
+            case 4: as_rowB_body<4, false>(net, st, sc, L, li, valid, s, i, lane, T, sp, it, TC, stg); break;
+            case 5: as_rowB_body<5, false>(net, st, sc, L, li, valid, s, i, lane, T, sp, it, TC, stg); break;
+            case 6: as_rowB_body<6, false>(net, st, sc, L, li, valid, s, i, lane, T, sp, it, TC, stg); break;
+            case 7: as_rowB_body<7, false>(net, st, sc, L, li, valid, s, i, lane, T, sp, it, TC, stg); break;
+            default: as_rowB_body<8, false>(net, st, sc, L, li, valid, s, i, lane, T, sp, it, TC, stg); break;
+        }
+    }
+    if (staged) {
+        __syncthreads();
+        const BfLayer& B = net.bf[li];
+        const int ncb = (L.co + 7) >> 3, npb = (L.ho * L.wo + 31) >> 5;
+        const int tile = (blockIdx.x - sg.start[q]), ts = tile / (ncb * npb);
+        const int rem = tile - ts * (ncb * npb), cb = rem / npb, pb = rem - cb * npb;
+        if (ts < net.S) {
+            uint16_t* R = B.R;
+            stage_store(stage, ns + 1, L.ho * L.wo, pb,
+                        [&](int e) { return R + ((long long)e * net.S + ts) * B.PR; },
+                        [&](int p) {
+                            const int oy = p / L.wo, ox = p - oy * L.wo;
+                            return ((long long)(oy + L.hl) * L.Wpo + (ox + L.wl)) * B.Cop + cb * 8;
+                        });
         }
     }
     if (last_block(&st.done[0]) && threadIdx.x == 0) {

@@ -613,7 +613,10 @@ static int load_batch(as_ctx* c, const float* x_lo, const float* x_hi, const flo
     k_efix<<<grid_for((size_t)S * NT), CB_THREADS, 0, s>>>(D, st);
     c->launches++;
     TRY(check_launch(c, "k_efix"));
+    // interval propagation computed lz, uz and the free counts with its own sums; caller-given bounds,
+    // and layer 1 over an ellipsoid (whose interval comes from other sums), need k_lz
     for (int k = 0; k < n - 1; ++k) {
+        if (!lhat && !(D.ball && k == 0)) continue;
         const long long warps = (long long)S * D.L[k].n_out;
         k_lz<<<(int)((warps + CB_WARPS - 1) / CB_WARPS), CB_THREADS, 0, s>>>(D, st, k);
         c->launches++;
@@ -874,11 +877,11 @@ static cudaEvent_t prof_event(as_ctx* c) {
 static int launch_as_iter(as_ctx* c, cudaStream_t s) {
     // the per-neuron bound terms are only summed when the best bound is tracked
     const int mode = c->opt.track_best ? 0 : 2;
-    LAUNCH(c, s, CB_K_AS_COLA, (k_as_colA_t<<<c->blocksTA, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->tA, mode, 0)));
+    LAUNCH(c, s, CB_K_AS_COLA, (k_as_colA_t<false><<<c->blocksTA, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->tA, mode)));
     if (c->net.ball) LAUNCH(c, s, CB_K_BALL_X0, (k_ball_x0<<<c->net.S, CB_BALL_THREADS, 0, s>>>(c->net, c->st)));
     if (c->opt.track_best)
         LAUNCH(c, s, CB_K_REDUCE, (k_reduce<<<c->net.S, CB_THREADS, 0, s>>>(c->net, c->st, 64, nullptr, 1)));
-    LAUNCH(c, s, CB_K_AS_ROWB, (k_as_rowB_t<<<c->blocksTB, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->tB, 0)));
+    LAUNCH(c, s, CB_K_AS_ROWB, (k_as_rowB_t<false><<<c->blocksTB, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->tB)));
     return check_launch(c, "Active Set iteration");
 }
 
@@ -1002,7 +1005,7 @@ extern "C" int as_bound(as_ctx* c, int precision, double* out, double* best) {
     } else {
         // the BF16 form's iterates give a bound through float32 lambda, kappa and records
         if (c->opt.precision == 16) TRY(recompute_slot_sums(c));
-        LAUNCH(c, s, CB_K_AS_COLA, (k_as_colA_t<<<c->blocksTA, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->tA, 1, 0)));
+        LAUNCH(c, s, CB_K_AS_COLA, (k_as_colA_t<false><<<c->blocksTA, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->tA, 1)));
         if (c->net.ball) LAUNCH(c, s, CB_K_BALL_X0, (k_ball_x0<<<S, CB_BALL_THREADS, 0, s>>>(c->net, c->st)));
     }
     double* dout = c->bound_out;

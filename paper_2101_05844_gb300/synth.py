@@ -187,22 +187,59 @@ def properties_runner_up(logits: np.ndarray) -> np.ndarray:
     return C
 
 
-def make_splits(layers: list[dict], S: int, max_splits: int, seed: int) -> np.ndarray:
-    """Branch-and-bound style ReLU splits: int8 [S, sum of hidden widths].
+def hidden_preactivations(net: list[dict], x: np.ndarray) -> np.ndarray:
+    """Pre-activations of every hidden neuron (hidden layers concatenated) for a batch of inputs
+    x [B, n_0], float64: the network's own forward pass."""
+    import torch
+    import torch.nn.functional as F
 
-    Each subdomain fixes k ~ U{0..max_splits} distinct hidden neurons, each active (+1) or
-    inactive (-1) with probability 1/2; 0 means free. A split takes effect only on a neuron whose
-    bounds straddle zero (the bounding code decides that), as branch and bound splits only those.
+    h = torch.from_numpy(np.asarray(x, dtype=np.float64))
+    out = []
+    for L in net[:-1]:
+        W = torch.from_numpy(L["W"].astype(np.float64))
+        b = torch.from_numpy(L["b"].astype(np.float64))
+        if L["kind"] == "linear":
+            z = h.reshape(h.shape[0], -1) @ W.T + b
+        else:
+            z = F.conv2d(h.reshape(h.shape[0], *L["in_shape"]), W, b, stride=L["stride"],
+                         padding=L["pad"]).reshape(h.shape[0], -1)
+        out.append(z)
+        h = torch.relu(z)
+    return torch.cat(out, 1).numpy()
+
+
+def sign_changing_neurons(net: list[dict], lo: np.ndarray, hi: np.ndarray, n_samples: int, seed: int) -> np.ndarray:
+    """Indices of the hidden neurons whose pre-activation takes both signs over sampled points of the
+    box [lo, hi] (half of them uniform, half random vertices). The network reaches both signs inside
+    the box, so every sound pair of bounds of such a neuron straddles zero: these are neurons that
+    branch and bound may split."""
+    rng = SplitMix64(seed)
+    n0 = lo.size
+    lo64, hi64 = lo.astype(np.float64), hi.astype(np.float64)
+    half = n_samples // 2
+    X = lo64 + rng.uniform(half * n0).reshape(half, n0) * (hi64 - lo64)
+    V = np.where(rng.uniform((n_samples - half) * n0).reshape(-1, n0) < 0.5, lo64, hi64)
+    Z = hidden_preactivations(net, np.vstack([X, V]))
+    return np.flatnonzero((Z.min(axis=0) < 0) & (Z.max(axis=0) > 0))
+
+
+def make_splits(candidates: np.ndarray, n_hidden: int, S: int, max_splits: int, seed: int) -> np.ndarray:
+    """Branch-and-bound style ReLU splits: int8 [S, n_hidden].
+
+    Each subdomain fixes k ~ U{0..max_splits} distinct neurons drawn from `candidates` (neurons that
+    change sign inside the root box), each active (+1) or inactive (-1) with probability 1/2; 0
+    means free. A split takes effect only where the neuron's bounds, with the splits of the layers
+    before it applied, still straddle zero (the bounding code decides that).
     """
     rng = SplitMix64(seed)
-    n_hidden = sum(L["n_out"] for L in layers[:-1])
+    cand = np.asarray(candidates, np.int64)
     out = np.zeros((S, n_hidden), np.int8)
     for s in range(S):
-        k = int(rng.integers(1, 0, max_splits)[0])
-        # distinct indices by a partial Fisher-Yates shuffle driven by the stream
-        idx = np.arange(n_hidden)
+        k = min(int(rng.integers(1, 0, max_splits)[0]), cand.size)
+        # distinct candidates by a partial Fisher-Yates shuffle driven by the stream
+        idx = cand.copy()
         for a in range(k):
-            r = a + int(rng.integers(1, 0, n_hidden - 1 - a)[0])
+            r = a + int(rng.integers(1, 0, cand.size - 1 - a)[0])
             idx[a], idx[r] = idx[r], idx[a]
         signs = np.where(rng.uniform(k) < 0.5, -1, 1).astype(np.int8)
         out[s, idx[:k]] = signs
@@ -217,11 +254,12 @@ def make_caps(S: int, lo: int, hi: int, seed: int) -> np.ndarray:
 # The workloads, by name and size.
 # --------------------------------------------------------------------------------------------
 
-def problem(name: str, S: int | None = None, seed: int = 0) -> dict:
+def problem(name: str, S: int | None = None, seed: int = 0, part: tuple[int, int] | None = None) -> dict:
     """A complete synthetic bounding problem.
 
     Returns {"net", "lo", "hi", "C", "splits", "caps", "eps"}: C is the property matrix
-    [S, n_out] (each subproblem lower-bounds C[s] . network(x) over its box).
+    [S, n_out] (each subproblem lower-bounds C[s] . network(x) over its box). part = (a, b): only
+    subproblems a .. b - 1 of the batch of S (the same values as in the whole batch; conv4 only).
     """
     base = 1000 * seed
     if name == "mlp_tiny":  # MLP 8-16-16-1, one box of half-width 0.1 around a U[0,1]^8 centre
@@ -248,7 +286,8 @@ def problem(name: str, S: int | None = None, seed: int = 0) -> dict:
         lo = np.repeat(lo1, S, axis=0)
         hi = np.repeat(hi1, S, axis=0)
         C = np.repeat(C1, S, axis=0)
-        splits = make_splits(layers, S, 20, base + 3)
+        cand = sign_changing_neurons(net, lo1[0], hi1[0], 512, base + 5)
+        splits = make_splits(cand, sum(L["n_out"] for L in layers[:-1]), S, 20, base + 3)
         caps = make_caps(S, 1, 5, base + 4)
         return dict(net=net, lo=lo, hi=hi, C=C, splits=splits, caps=caps, eps=eps)
     if name == "conv4":
@@ -257,6 +296,8 @@ def problem(name: str, S: int | None = None, seed: int = 0) -> dict:
         S = S or 1024
         eps = 8.0 / 255.0
         c, lo, hi = make_boxes(3072, S, eps, base + 2)
+        if part is not None:
+            c, lo, hi = c[part[0]:part[1]], lo[part[0]:part[1]], hi[part[0]:part[1]]
         C = properties_runner_up(forward(net, c))
         return dict(net=net, lo=lo, hi=hi, C=C, splits=None, caps=None, eps=eps)
     if name == "mlp_wide":
