@@ -225,7 +225,10 @@ long long as_launch_count(as_ctx* ctx);
 #define AS_K_TC_ROW 9  /* BF16 form: tensor-core products of the row pass              */
 #define AS_K_SLOT_SUMS 10 /* BF16 form: float32 lambda, kappa after an addition        */
 #define AS_K_BALL_X0 11   /* ellipsoid input set: x_0*, its bound terms and records       */
-#define AS_K_COUNT 12
+#define AS_K_BATCH 12     /* a batch's set-up (as_init, as_reset): box checks, property rows,
+                             interval bounds, row constants, fixed inputs                   */
+#define AS_K_SP_START 13  /* Saddle Point's start: statistics (eq. 10), caps (eq. 16), records */
+#define AS_K_COUNT 14
 
 /* With as_options.profile set: total device time (CUDA events on the context's stream) and
  * launch count of one kernel over the context's life so far. Synchronises the stream. */

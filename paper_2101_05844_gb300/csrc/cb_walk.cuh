@@ -6,26 +6,47 @@
 namespace cb {
 
 // ------------------------------------------------------------------------------------ walks
-// Lane-strided walk over the fan-in of output neuron i of layer L: fn(j, w) for each input j.
+// Lane-strided walk over the fan-in of output neuron i of layer L: fn(j, w) for each input j, by a
+// team of T lanes (lane = 0 .. T - 1). Conv layers: the lanes stride over (input channel, kernel
+// row) pairs and each walks its row's kernel columns, the receptive field clipped to the image once
+// per neuron, with no integer division inside the loop.
 template <class Fn>
-__device__ __forceinline__ void row_walk(const DLayer& L, int i, int lane, Fn fn) {
+__device__ __forceinline__ void row_walk_team(const DLayer& L, int i, int lane, int T, Fn fn) {
     if (L.kind == 0) {
         const float* Wr = L.W + (size_t)i * L.n_in;
-        for (int j = lane; j < L.n_in; j += 32) fn(j, __ldg(Wr + j));
-    } else {
-        const int hw = L.ho * L.wo;
-        const int co = i / hw, rem = i - co * hw;
-        const int oy = rem / L.wo, ox = rem - oy * L.wo;
-        const int kk = L.kh * L.kw, fan = L.ci * kk;
-        const float* Wr = L.W + (size_t)co * fan;
-        const int y0 = oy * L.st - L.pd, x0 = ox * L.st - L.pd;
-        for (int r = lane; r < fan; r += 32) {
-            const int c = r / kk, q = r - c * kk;
-            const int ky = q / L.kw, kx = q - ky * L.kw;
-            const int y = y0 + ky, x = x0 + kx;
-            if (y >= 0 && y < L.hi && x >= 0 && x < L.wi) fn((c * L.hi + y) * L.wi + x, __ldg(Wr + r));
+#pragma unroll 4
+        for (int j = lane; j < L.n_in; j += T) fn(j, __ldg(Wr + j));
+        return;
+    }
+    const int hw = L.ho * L.wo;
+    const int co = i / hw, rem = i - co * hw;
+    const int oy = rem / L.wo, ox = rem - oy * L.wo;
+    const int y0 = oy * L.st - L.pd, x0 = ox * L.st - L.pd;
+    const int ky0 = max(0, -y0), ky1 = min(L.kh, L.hi - y0);
+    const int kx0 = max(0, -x0), kx1 = min(L.kw, L.wi - x0);
+    const float* Wc = L.W + (size_t)co * L.ci * L.kh * L.kw;
+    int c = lane / L.kh, ky = lane - c * L.kh;
+    const int cstep = T / L.kh, kstep = T - cstep * L.kh;
+    while (c < L.ci) {
+        if (ky >= ky0 && ky < ky1) {
+            const float* Wk = Wc + (c * L.kh + ky) * L.kw;
+            const int jrow = (c * L.hi + y0 + ky) * L.wi + x0;
+#pragma unroll 4
+            for (int kx = kx0; kx < kx1; ++kx) fn(jrow + kx, __ldg(Wk + kx));
+        }
+        c += cstep;
+        ky += kstep;
+        if (ky >= L.kh) {
+            ky -= L.kh;
+            ++c;
         }
     }
+}
+
+// The same walk by a whole warp.
+template <class Fn>
+__device__ __forceinline__ void row_walk(const DLayer& L, int i, int lane, Fn fn) {
+    row_walk_team(L, i, lane, 32, fn);
 }
 
 // Serial walk over the fan-out of input neuron j of layer L: fn(i, w) for each output i.

@@ -529,6 +529,33 @@ static int alloc_state(as_ctx* c) {
     return AS_OK;
 }
 
+// Per-kernel timing: with as_options.profile set, each launch is bracketed by CUDA events on its
+// stream; as_kernel_times reads and accumulates them.
+static cudaEvent_t prof_event(as_ctx* c) {
+    if (!c->pool.empty()) {
+        cudaEvent_t e = c->pool.back();
+        c->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+#define LAUNCH(c, s, id, ...)                                      \
+    do {                                                           \
+        if ((c)->opt.profile) {                                    \
+            as_ctx::Rec r_{id, prof_event(c), prof_event(c)};      \
+            cudaEventRecord(r_.a, s);                              \
+            __VA_ARGS__;                                           \
+            cudaEventRecord(r_.b, s);                              \
+            (c)->pending.push_back(r_);                            \
+        } else {                                                   \
+            __VA_ARGS__;                                           \
+        }                                                          \
+        (c)->launches++;                                           \
+    } while (0)
+
 // Box, property rows, intermediate bounds, splits and caps of a batch; zeroes the duals.
 static int load_batch(as_ctx* c, const float* x_lo, const float* x_hi, const float* C, const float* lhat,
                       const float* uhat, const signed char* splits, const int* caps, bool host_checks) {
@@ -544,8 +571,7 @@ static int load_batch(as_ctx* c, const float* x_lo, const float* x_hi, const flo
     TRY(clear_planes(c));
     c->bounds_ibp = lhat == nullptr;
     c->have_splits = splits != nullptr && lhat == nullptr;
-    k_fill<<<grid_for(S), CB_THREADS, 0, s>>>(st.best, (size_t)S, -INFINITY);
-    c->launches++;
+    LAUNCH(c, s, CB_K_BATCH, (k_fill<<<grid_for(S), CB_THREADS, 0, s>>>(st.best, (size_t)S, -INFINITY)));
     c->sp_started = false;
     if (host_checks) {
         std::vector<float> hl((size_t)S * n0), hh((size_t)S * n0);
@@ -570,18 +596,15 @@ static int load_batch(as_ctx* c, const float* x_lo, const float* x_hi, const flo
     CUDA_TRY(c, cudaMemcpy2DAsync(st.hi, NT * sizeof(float), x_hi, n0 * sizeof(float), n0 * sizeof(float), S,
                                   cudaMemcpyDefault, s));
     if (!host_checks) {
-        k_check_box<<<grid_for((size_t)S * n0), CB_THREADS, 0, s>>>(D, st);
-        c->launches++;
+        LAUNCH(c, s, CB_K_BATCH, (k_check_box<<<grid_for((size_t)S * n0), CB_THREADS, 0, s>>>(D, st)));
     }
     if (caps) CUDA_TRY(c, cudaMemcpyAsync(c->caps_dev, caps, S * sizeof(int), cudaMemcpyDefault, s));
     else {
-        k_fill_int<<<grid_for(S), CB_THREADS, 0, s>>>(c->caps_dev, (size_t)S, c->opt.max_cuts);
-        c->launches++;
+        LAUNCH(c, s, CB_K_BATCH, (k_fill_int<<<grid_for(S), CB_THREADS, 0, s>>>(c->caps_dev, (size_t)S, c->opt.max_cuts)));
     }
     if (C) CUDA_TRY(c, cudaMemcpyAsync(c->C, C, (size_t)S * c->n_out * sizeof(float), cudaMemcpyDefault, s));
-    k_fold<<<S, CB_THREADS, 0, s>>>(D, c->Wlast, c->blast, C ? c->C : nullptr, c->n_out, (float*)D.Wout,
-                                    (float*)D.bout);
-    c->launches++;
+    LAUNCH(c, s, CB_K_BATCH, (k_fold<<<S, CB_THREADS, 0, s>>>(D, c->Wlast, c->blast, C ? c->C : nullptr, c->n_out,
+                                                             (float*)D.Wout, (float*)D.bout)));
     TRY(check_launch(c, "k_fold"));
     if (lhat) {
         CUDA_TRY(c, cudaMemcpyAsync(st.lhat, lhat, NHS * sizeof(float), cudaMemcpyDefault, s));
@@ -594,8 +617,7 @@ static int load_batch(as_ctx* c, const float* x_lo, const float* x_hi, const flo
             for (size_t q = 0; q < NHS; ++q)
                 if (!(a[q] <= b[q])) return fail(c, AS_ERR_ARG, "lhat > uhat at hidden entry %zu", q);
         }
-        k_post_from_pre<<<grid_for(NHS), CB_THREADS, 0, s>>>(D, st);
-        c->launches++;
+        LAUNCH(c, s, CB_K_BATCH, (k_post_from_pre<<<grid_for(NHS), CB_THREADS, 0, s>>>(D, st)));
         TRY(check_launch(c, "k_post_from_pre"));
     } else {
         const signed char* dsp = nullptr;
@@ -605,21 +627,18 @@ static int load_batch(as_ctx* c, const float* x_lo, const float* x_hi, const flo
         }
         for (int k = 0; k < n - 1; ++k) {
             const long long warps = (long long)S * D.L[k].n_out;
-            k_ibp<<<(int)((warps + CB_WARPS - 1) / CB_WARPS), CB_THREADS, 0, s>>>(D, st, k, dsp);
-            c->launches++;
+            LAUNCH(c, s, CB_K_BATCH, (k_ibp<<<(int)((warps + CB_WARPS - 1) / CB_WARPS), CB_THREADS, 0, s>>>(D, st, k, dsp)));
             TRY(check_launch(c, "k_ibp"));
         }
     }
-    k_efix<<<grid_for((size_t)S * NT), CB_THREADS, 0, s>>>(D, st);
-    c->launches++;
+    LAUNCH(c, s, CB_K_BATCH, (k_efix<<<grid_for((size_t)S * NT), CB_THREADS, 0, s>>>(D, st)));
     TRY(check_launch(c, "k_efix"));
     // interval propagation computed lz, uz and the free counts with its own sums; caller-given bounds,
     // and layer 1 over an ellipsoid (whose interval comes from other sums), need k_lz
     for (int k = 0; k < n - 1; ++k) {
         if (!lhat && !(D.ball && k == 0)) continue;
         const long long warps = (long long)S * D.L[k].n_out;
-        k_lz<<<(int)((warps + CB_WARPS - 1) / CB_WARPS), CB_THREADS, 0, s>>>(D, st, k);
-        c->launches++;
+        LAUNCH(c, s, CB_K_BATCH, (k_lz<<<(int)((warps + CB_WARPS - 1) / CB_WARPS), CB_THREADS, 0, s>>>(D, st, k)));
         TRY(check_launch(c, "k_lz"));
     }
     return AS_OK;
@@ -847,33 +866,6 @@ extern "C" void as_destroy(as_ctx* c) {
 }
 
 // ------------------------------------------------------------------------------- iterations
-// Per-kernel timing: with as_options.profile set, each launch is bracketed by CUDA events on its
-// stream; as_kernel_times reads and accumulates them.
-static cudaEvent_t prof_event(as_ctx* c) {
-    if (!c->pool.empty()) {
-        cudaEvent_t e = c->pool.back();
-        c->pool.pop_back();
-        return e;
-    }
-    cudaEvent_t e;
-    cudaEventCreate(&e);
-    return e;
-}
-
-#define LAUNCH(c, s, id, ...)                                      \
-    do {                                                           \
-        if ((c)->opt.profile) {                                    \
-            as_ctx::Rec r_{id, prof_event(c), prof_event(c)};      \
-            cudaEventRecord(r_.a, s);                              \
-            __VA_ARGS__;                                           \
-            cudaEventRecord(r_.b, s);                              \
-            (c)->pending.push_back(r_);                            \
-        } else {                                                   \
-            __VA_ARGS__;                                           \
-        }                                                          \
-        (c)->launches++;                                           \
-    } while (0)
-
 static int launch_as_iter(as_ctx* c, cudaStream_t s) {
     // the per-neuron bound terms are only summed when the best bound is tracked
     const int mode = c->opt.track_best ? 0 : 2;
@@ -959,12 +951,12 @@ static int sp_start(as_ctx* c) {
     cudaStream_t s = c->stream;
     if (c->opt.precision == 16) TRY(recompute_slot_sums(c));   // float32 lambda, kappa for the conversion
     const size_t NHS = (size_t)c->net.S * c->net.NH;
-    k_sp_convert_elem<<<grid_for(NHS), CB_THREADS, 0, s>>>(c->net, c->st, c->sc, (float)c->opt.sp_c_alpha,
-                                                           (float)c->opt.sp_c_beta);
-    k_sp_convert_P<<<c->blocksP, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->segP);
-    k_sp_prep<<<grid_for(NHS), CB_THREADS, 0, s>>>(c->net, c->st);
-    k_sp_colA_t<<<c->blocksTA, CB_THREADS, 0, s>>>(c->net, c->st, c->tA, 1);
-    c->launches += 4;
+    LAUNCH(c, s, CB_K_SP_START, (k_sp_convert_elem<<<grid_for(NHS), CB_THREADS, 0, s>>>(c->net, c->st, c->sc,
+                                                                                      (float)c->opt.sp_c_alpha,
+                                                                                      (float)c->opt.sp_c_beta)));
+    LAUNCH(c, s, CB_K_SP_START, (k_sp_convert_P<<<c->blocksP, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->segP)));
+    LAUNCH(c, s, CB_K_SP_START, (k_sp_prep<<<grid_for(NHS), CB_THREADS, 0, s>>>(c->net, c->st)));
+    LAUNCH(c, s, CB_K_SP_START, (k_sp_colA_t<<<c->blocksTA, CB_THREADS, 0, s>>>(c->net, c->st, c->tA, 1)));
     if (c->net.ball) LAUNCH(c, s, CB_K_BALL_X0, (k_ball_sp<<<c->net.S, CB_BALL_THREADS, 0, s>>>(c->net, c->st, 1)));
     TRY(check_launch(c, "Saddle Point conversion"));
     for (int t = 0; t < c->opt.sp_init_steps; ++t) {
