@@ -36,40 +36,6 @@ struct TSegs {
 };
 
 template <class Fn>
-__device__ __forceinline__ void row_walk_team(const DLayer& L, int i, int lane, int T, Fn fn) {
-    if (L.kind == 0) {
-        const float* Wr = L.W + (size_t)i * L.n_in;
-#pragma unroll 4
-        for (int j = lane; j < L.n_in; j += T) fn(j, __ldg(Wr + j));
-        return;
-    }
-    const int hw = L.ho * L.wo;
-    const int co = i / hw, rem = i - co * hw;
-    const int oy = rem / L.wo, ox = rem - oy * L.wo;
-    const int y0 = oy * L.st - L.pd, x0 = ox * L.st - L.pd;
-    const int ky0 = max(0, -y0), ky1 = min(L.kh, L.hi - y0);
-    const int kx0 = max(0, -x0), kx1 = min(L.kw, L.wi - x0);
-    const float* Wc = L.W + (size_t)co * L.ci * L.kh * L.kw;
-    // lanes stride over (channel, kernel row) pairs
-    int c = lane / L.kh, ky = lane - c * L.kh;
-    const int cstep = T / L.kh, kstep = T - cstep * L.kh;
-    while (c < L.ci) {
-        if (ky >= ky0 && ky < ky1) {
-            const float* Wk = Wc + (c * L.kh + ky) * L.kw;
-            const int jrow = (c * L.hi + y0 + ky) * L.wi + x0;
-#pragma unroll 4
-            for (int kx = kx0; kx < kx1; ++kx) fn(jrow + kx, __ldg(Wk + kx));
-        }
-        c += cstep;
-        ky += kstep;
-        if (ky >= L.kh) {
-            ky -= L.kh;
-            ++c;
-        }
-    }
-}
-
-template <class Fn>
 __device__ __forceinline__ void col_walk_team(const DLayer& L, int j, int lane, int T, Fn fn) {
     if (L.kind == 0) {
         const float* Wc = L.W + j;
