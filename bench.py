@@ -851,6 +851,9 @@ def main():
                     help="boxes of the conv4 batch (1024; fewer only for a profiler capture)")
     ap.add_argument("--profile-only", action="store_true",
                     help="only warm-up and timed steps of the conv4 workload, nothing else (profiler captures)")
+    ap.add_argument("--form", default="bf16", choices=["bf16", "fp32"],
+                    help="form of the conv4 step's Active Set products (bf16: the default line; fp32 only "
+                         "with --profile-only, for captures of the float32 passes)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the float32 / BF16 comparison")
     ap.add_argument("--no-wide", action="store_true", help="skip the Wide conv extra key")
@@ -898,8 +901,10 @@ def main():
     out_d = [torch.zeros(S, dtype=torch.float64, device=dev) for _ in range(2)]
     out_h = [torch.zeros(S, dtype=torch.float64).pin_memory() for _ in range(2)]
     stream = torch.cuda.current_stream(dev).cuda_stream
-    ctx = binding.Context(prob["net"], prob["lo"], prob["hi"], prob["C"], options=conv4_options(binding, 16),
-                          stream=stream)
+    if args.form == "fp32" and not args.profile_only:
+        ap.error("--form fp32 is for profiler captures (--profile-only); the line reports both forms")
+    ctx = binding.Context(prob["net"], prob["lo"], prob["hi"], prob["C"],
+                          options=conv4_options(binding, 16 if args.form == "bf16" else 32), stream=stream)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
 
     def barrier():

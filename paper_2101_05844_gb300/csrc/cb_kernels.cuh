@@ -286,35 +286,4 @@ __global__ void k_sp_convert_elem(DNet net, DState st, DSched sc, float c_alpha,
     }
 }
 
-// P_k[j] = (W_k^T beta1_k)[j] + sum_b ((W_k o I_b)^T beta_b)[j] for hidden layers k (col pass).
-__global__ void __launch_bounds__(CB_THREADS) k_sp_convert_P(DNet net, DState st, DSched sc, Segs sg) {
-    const int q = seg_of(sg, blockIdx.x);
-    const DLayer& L = net.L[sg.layer[q]];
-    const int u = (blockIdx.x - sg.start[q]) * CB_THREADS + threadIdx.x;
-    if (u >= net.S * L.n_in) return;
-    const int s = u / L.n_in, j = u - s * L.n_in;
-    const Step sp = cb_step(st.ctr[0], sc, st.lr_tab);
-    const int nsl = min(sp.nadd_before, st.caps[s]);
-    const int bo = sp.nadd_before & 1;
-    const size_t NT = net.NT, NH = net.NH;
-    const size_t xo = (size_t)s * NT + L.in_off + j;
-    const unsigned xs = st.xsnap[bo][xo];
-    const bool fixed = st.lo[xo] == st.hi[xo];
-    const size_t rb = (size_t)s * NH + L.h_out;
-    const float* b1 = st.beta1 + rb;
-    const float* bsl = st.bs + (size_t)s * net.cap * NH + L.h_out;
-    const uint8_t* zs = st.zsnap[bo] + rb;
-    float acc = 0.f;
-    col_walk(L, j, [&](int i, float w) {
-        float sb = b1[i];
-        if (nsl) {
-            const unsigned I = cb_slot_mask(zs[i], xs, fixed, w, net.ball && L.in_off == 0);
-            for (int b = 0; b < nsl; ++b)
-                if ((I >> b) & 1u) sb += bsl[(size_t)b * NH + i];
-        }
-        acc += w * sb;
-    });
-    st.P[xo] = acc;
-}
-
 }  // namespace cb

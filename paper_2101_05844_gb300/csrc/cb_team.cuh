@@ -221,6 +221,13 @@ __device__ __forceinline__ void stage_store(const TcStage& st, int nplanes, int 
     }
 }
 
+// Channel and position of a conv tile's unit (BF16 form), worked out once by the kernel.
+struct TcPos {
+    int c, y, x;
+};
+// a / st for the small strides of conv layers, without a division for strides 1 and 2
+__device__ __forceinline__ int div_stride(int a, int st) { return st == 1 ? a : (st == 2 ? a >> 1 : a / st); }
+
 // ---------------------------------------------------------------- Active Set col pass (phase A)
 // The masked backward product of eq. (6) for input j, regrouped by the sign of W: at binary
 // iterates eq. (3) gives I_b(i, j) = 1 on rows with z_b[i] = 1 (their beta is in the record's
@@ -232,7 +239,7 @@ __device__ __forceinline__ void stage_store(const TcStage& st, int nplanes, int 
 template <int NS>
 __device__ __forceinline__ void as_colA_body(const DNet& net, const DState& st, const DSched& sc, const DLayer& L,
                                              int k, bool valid, int s, int j, int lane, int T, int mode, bool tc,
-                                             TcStage* stg) {
+                                             TcStage* stg, TcPos tp) {
     const int m = k - 1;
     const Step sp = cb_step(st.ctr[0], sc, st.lr_tab);
     const size_t NT = net.NT, NH = net.NH, cap = net.cap;
@@ -244,11 +251,9 @@ __device__ __forceinline__ void as_colA_body(const DNet& net, const DState& st, 
         const BfLayer& B = net.bf[k - 1];
         int c = j, ph = 0, q = 0;
         if (L.kind == 1) {
-            const int hw = L.hi * L.wi;
-            c = j / hw;
-            const int rem = j - c * hw, y = rem / L.wi, x = rem - y * L.wi;
-            const int ty = y + L.pd, tx = x + L.pd;
-            const int Y0 = ty / L.st, X0 = tx / L.st;
+            c = tp.c;
+            const int ty = tp.y + L.pd, tx = tp.x + L.pd;
+            const int Y0 = div_stride(ty, L.st), X0 = div_stride(tx, L.st);
             ph = (ty - Y0 * L.st) * L.st + (tx - X0 * L.st);
             q = (Y0 - B.Y0a[ph]) * B.nX[ph] + (X0 - B.X0a[ph]);
         }
@@ -375,14 +380,7 @@ __device__ __forceinline__ void as_colA_body(const DNet& net, const DState& st, 
         if (tc) {
             // BF16 form: the row pass's tensor-core operand, x* (slot 0) and x* p_b / x* q_b
             const BfLayer& B = net.bf[k - 1];
-            int c = j, y = 0, x = 0;
-            if (L.kind == 1) {
-                const int hw = L.hi * L.wi;
-                c = j / hw;
-                const int rem = j - c * hw;
-                y = rem / L.wi;
-                x = rem - y * L.wi;
-            }
+            const int c = L.kind == 1 ? tp.c : j, y = L.kind == 1 ? tp.y : 0, x = L.kind == 1 ? tp.x : 0;
             const long long off = ((long long)(y + L.pd) * L.Wp + (x + L.pd)) * B.Cip + c;
             const __nv_bfloat16 xb = __float2bfloat16_rn(xv), zero = __float2bfloat16_rn(0.f);
             __nv_bfloat16* X = reinterpret_cast<__nv_bfloat16*>(B.X);
@@ -530,10 +528,16 @@ __global__ void __launch_bounds__(CB_THREADS, 4) k_as_colA_t(DNet net, DState st
     int s = valid ? unit / L.n_in : 0, o = valid ? unit - s * L.n_in : 0;
     const bool staged = TC && L.kind == 1 && li + 1 <= net.n - 1;
     __shared__ TcStage stage;
+    TcPos tp{0, 0, 0};
     if (TC && L.kind == 1) {   // one lane per unit, tiled
         o = tc_tile_unit(t, L.ci, L.hi * L.wi, net.S, s);
         valid = o >= 0;
         o = valid ? o : 0;
+        const int P = L.hi * L.wi;
+        tp.c = o / P;
+        const int p = o - tp.c * P;
+        tp.y = p / L.wi;
+        tp.x = p - tp.y * L.wi;
     }
     if (staged)   // zeros stay where the tile has no unit (channel padding)
         for (int e = 0; e < 2 * (net.cap + 1); ++e) stage_at(stage, e) = 0;
@@ -542,15 +546,15 @@ __global__ void __launch_bounds__(CB_THREADS, 4) k_as_colA_t(DNet net, DState st
     const Step sp = cb_step(st.ctr[0], sc, st.lr_tab);
     const int ns = min(sp.nadd_before, sc.maxcut);
     switch (ns) {
-        case 0: as_colA_body<0>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, TC, stg); break;
-        case 1: as_colA_body<1>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, TC, stg); break;
-        case 2: as_colA_body<2>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, TC, stg); break;
-        case 3: as_colA_body<3>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, TC, stg); break;
-        case 4: as_colA_body<4>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, TC, stg); break;
-        case 5: as_colA_body<5>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, TC, stg); break;
-        case 6: as_colA_body<6>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, TC, stg); break;
-        case 7: as_colA_body<7>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, TC, stg); break;
-        default: as_colA_body<8>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, TC, stg); break;
+        case 0: as_colA_body<0>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, TC, stg, tp); break;
+        case 1: as_colA_body<1>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, TC, stg, tp); break;
+        case 2: as_colA_body<2>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, TC, stg, tp); break;
+        case 3: as_colA_body<3>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, TC, stg, tp); break;
+        case 4: as_colA_body<4>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, TC, stg, tp); break;
+        case 5: as_colA_body<5>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, TC, stg, tp); break;
+        case 6: as_colA_body<6>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, TC, stg, tp); break;
+        case 7: as_colA_body<7>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, TC, stg, tp); break;
+        default: as_colA_body<8>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, TC, stg, tp); break;
     }
     if (staged) {
         __syncthreads();
@@ -1334,6 +1338,43 @@ __global__ void __launch_bounds__(CB_THREADS) k_sp_colCA_t(DNet net, DState st, 
         st.ctr[1] = t + 1;
         st.done[1] = 0;
     }
+}
+
+// Saddle Point's start (eq. 10): P_k[j] = (W_k^T beta_{k,1})[j] + sum_b ((W_k o I_b)^T beta_{k,b})[j]
+// of the Active Set duals, for the inputs j of every hidden-output layer k, by lane teams over
+// each input's fan-out (the col pass's geometry); the slot masks from the snapshot bits (eq. 3 at
+// the snapshot points).
+__global__ void __launch_bounds__(CB_THREADS) k_sp_convert_P_t(DNet net, DState st, DSched sc, TSegs sg) {
+    const int q = tseg_of(sg, blockIdx.x);
+    const int li = sg.layer[q];
+    if (li >= net.n - 1) return;   // the output layer's inputs carry no P (whole block)
+    const DLayer& L = net.L[li];
+    const Unit u = team_unit(sg, q, L.n_in, net.S);
+    const Step sp = cb_step(st.ctr[0], sc, st.lr_tab);
+    const int nsl = u.valid ? min(sp.nadd_before, st.caps[u.s]) : 0;
+    const int bo = sp.nadd_before & 1;
+    const size_t xo = (size_t)u.s * net.NT + L.in_off + u.idx;
+    float acc = 0.f;
+    if (u.valid) {
+        const unsigned xs = st.xsnap[bo][xo];
+        const bool fixed = st.lo[xo] == st.hi[xo];
+        const size_t rb = (size_t)u.s * net.NH + L.h_out;
+        const float* b1 = st.beta1 + rb;
+        const float* bsl = st.bs + (size_t)u.s * net.cap * net.NH + L.h_out;
+        const uint8_t* zs = st.zsnap[bo] + rb;
+        const bool interior = net.ball && L.in_off == 0;
+        col_walk_team(L, u.idx, u.lane, u.T, [&](int i, float w) {
+            float sb = b1[i];
+            if (nsl) {
+                const unsigned I = cb_slot_mask(zs[i], xs, fixed, w, interior);
+                for (int b = 0; b < nsl; ++b)
+                    if ((I >> b) & 1u) sb += bsl[(size_t)b * net.NH + i];
+            }
+            acc += w * sb;
+        });
+    }
+    if (u.T > 1) acc = team_sum(acc, u.T);
+    if (u.valid && u.lane == 0) st.P[xo] = acc;
 }
 
 // Primal initialisation (App. C.2, Big-M variables), row pass: inner maximisers at (x, z).

@@ -34,8 +34,8 @@ struct as_ctx {
     bool have_splits = false;      // ... with the split clamps of splits_dev
     bool sp_need_phaseA = true;    // the next Saddle Point iteration starts with a separate phase A
     long long launches = 0;
-    Segs segA{}, segB{}, segP{};
-    int blocksA = 0, blocksB = 0, blocksP = 0;
+    Segs segA{}, segB{};
+    int blocksA = 0, blocksB = 0;
     TSegs tA{}, tB{};                // lane-team launch geometry of the Active Set passes
     int blocksTA = 0, blocksTB = 0;
     cudaGraphExec_t g_as = nullptr, g_sp = nullptr;
@@ -808,13 +808,6 @@ static int init_impl(as_ctx* c, const as_net* net, int S, const float* x_lo, con
             units.push_back((long long)S * D.L[k].n_out);
         }
         make_segs(c->segB, c->blocksB, ids, units, CB_WARPS);
-        ids.clear();
-        units.clear();
-        for (int k = 0; k < n - 1; ++k) {
-            ids.push_back(k);
-            units.push_back((long long)S * D.L[k].n_in);
-        }
-        make_segs(c->segP, c->blocksP, ids, units, CB_THREADS);
     }
     TRY(make_team_segs(c));
     TRY(alloc_state(c));
@@ -954,7 +947,7 @@ static int sp_start(as_ctx* c) {
     LAUNCH(c, s, CB_K_SP_START, (k_sp_convert_elem<<<grid_for(NHS), CB_THREADS, 0, s>>>(c->net, c->st, c->sc,
                                                                                       (float)c->opt.sp_c_alpha,
                                                                                       (float)c->opt.sp_c_beta)));
-    LAUNCH(c, s, CB_K_SP_START, (k_sp_convert_P<<<c->blocksP, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->segP)));
+    LAUNCH(c, s, CB_K_SP_START, (k_sp_convert_P_t<<<c->blocksTA, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->tA)));
     LAUNCH(c, s, CB_K_SP_START, (k_sp_prep<<<grid_for(NHS), CB_THREADS, 0, s>>>(c->net, c->st)));
     LAUNCH(c, s, CB_K_SP_START, (k_sp_colA_t<<<c->blocksTA, CB_THREADS, 0, s>>>(c->net, c->st, c->tA, 1)));
     if (c->net.ball) LAUNCH(c, s, CB_K_BALL_X0, (k_ball_sp<<<c->net.S, CB_BALL_THREADS, 0, s>>>(c->net, c->st, 1)));

@@ -50,7 +50,8 @@ def test_layout_probe_one_tile():
 
 
 @pytest.mark.parametrize("M,N,K,bn", [(128, 32, 64, 32), (256, 64, 128, 64), (300, 100, 200, 128),
-                                      (1000, 256, 576, 256), (64, 48, 24, 64), (777, 33, 1032, 32)])
+                                      (1000, 256, 576, 256), (64, 48, 24, 64), (777, 33, 1032, 32),
+                                      (384, 512, 8192, 64), (130, 40, 320, 128), (129, 8, 4104, 256)])
 def test_matches_float64_within_accumulation_bound(M, N, K, bn):
     _run(M, N, K, bn, seed=M + N + K)
 
