@@ -4,8 +4,11 @@
 subproblem (float64, on lo's device) at the context's current duals; its backward calls
 `as_bound_backward`, the gradient at fixed duals, masks, intermediate bounds and signs of W
 (Danskin), with respect to the weights, biases (of the last layer through the property rows) and
-the input box. The context holds its own copies of the weights (made by `as_init`); the tensors
-passed here must hold the same values, and serve as the leaves the gradient is attached to.
+the input box. The context holds its own copies of the weights (made by `as_init`) and of the box
+(`as_init`, `as_reset`); the tensors passed here must hold the same values and serve as the leaves
+the gradient is attached to. Tensors holding other values (a training loop that updated the
+weights, a new box) are refused with an error rather than given the gradient of the context's
+stale copies: build a new context (weights) or reset it and iterate (box) first.
 """
 from __future__ import annotations
 
@@ -16,6 +19,9 @@ import torch
 class ActiveSetBound(torch.autograd.Function):
     @staticmethod
     def forward(ctx, context, lo, hi, *params):
+        why = context.holds(lo, hi, params)
+        if why is not None:
+            raise ValueError(f"ActiveSetBound: {why}; the bound and its gradient would belong to other values")
         ctx.context = context
         ctx.save_for_backward(lo, hi, *params)
         out = torch.zeros(context.S, dtype=torch.float64, device=lo.device)

@@ -170,6 +170,13 @@ def _ptr(a):
     raise TypeError(type(a))
 
 
+def _snapshot(a):
+    """A float32 copy of an array or tensor's current values (host numpy, or a tensor on its device)."""
+    if isinstance(a, np.ndarray):
+        return np.array(a, np.float32, copy=True)
+    return a.detach().to(dtype=a.dtype).clone()
+
+
 def _layer_struct(L: dict, keep: list) -> Layer:
     W = np.ascontiguousarray(L["W"], np.float32) if isinstance(L["W"], np.ndarray) else L["W"]
     b = np.ascontiguousarray(L["b"], np.float32) if isinstance(L["b"], np.ndarray) else L["b"]
@@ -218,6 +225,10 @@ class Context:
             self.h = ct.c_void_p()
             raise CBError(r, msg)
         self.n_layers = len(net)
+        # the values the context was built on (weights) and is bounding (box): the differentiable
+        # bound (autograd.py) refuses tensors that differ from them
+        self._weights = [_snapshot(x[k]) for x in net for k in ("W", "b")]
+        self._box = (_snapshot(lo), _snapshot(hi))
         self.widths = [net[0]["n_in"]] + [x["n_out"] for x in net[:-1]]
         self.NT = sum(self.widths)
         self.NH = self.NT - self.widths[0]
@@ -234,6 +245,27 @@ class Context:
                 conv(uhat, np.float32), conv(splits, np.int8), conv(caps, np.int32)]
         self._reset_keep = args
         self._check(lib().as_reset(self.h, *[_ptr(a) for a in args]))
+        self._box = (_snapshot(args[0]), _snapshot(args[1]))
+
+    def holds(self, lo, hi, params) -> str | None:
+        """None when lo, hi and params = [W_1, b_1, ..., W_n, b_n] hold the values this context
+        bounds (its box since creation or the last reset, its weights since creation); else which
+        of them differs."""
+        import torch
+
+        def same(t, ref):
+            t = t.detach()
+            r = torch.as_tensor(ref).to(device=t.device, dtype=torch.float32)
+            return t.shape == r.shape and bool(torch.equal(t.to(torch.float32), r))
+
+        if len(params) != len(self._weights):
+            return f"{len(params)} weight tensors given, the net has {len(self._weights)}"
+        for q, (t, ref) in enumerate(zip(params, self._weights)):
+            if not same(t, ref):
+                return f"{'W' if q % 2 == 0 else 'b'}_{q // 2 + 1} differs from the weights the context was built on"
+        if not same(lo, self._box[0]) or not same(hi, self._box[1]):
+            return "the box differs from the one the context is bounding"
+        return None
 
     def team_targets(self) -> tuple:
         """(row, col) team-size targets of the float32 passes: defaults or as_options.autotune's."""

@@ -121,3 +121,35 @@ def test_full_size_mlp_gradient_matches_oracle_on_sampled_entries():
     for k in range(len(prob["net"])):
         np.testing.assert_allclose(dW[k].cpu().numpy(), refW[k], rtol=1e-4, atol=2e-4)
         np.testing.assert_allclose(db[k].cpu().numpy(), refb[k], rtol=1e-4, atol=2e-4)
+
+
+def test_values_other_than_the_contexts_are_refused():
+    """A training loop that updated a weight, or a box other than the one the context bounds, gets
+    an error instead of the gradient of the context's stale copies."""
+    torch = pytest.importorskip("torch")
+    from paper_2101_05844_gb300.autograd import bound
+
+    prob = synth.problem("mlp_4_5_5_1", S=2, seed=1)
+    ctx = binding.context_for(prob, binding.default_options(bigm_iters=5, as_iters=5, graph_chunk=0))
+    ctx.as_step(10)
+    dev = torch.device("cuda")
+    params = []
+    for L in prob["net"]:
+        params += [torch.tensor(L["W"], device=dev, requires_grad=True),
+                   torch.tensor(L["b"], device=dev, requires_grad=True)]
+    lo = torch.tensor(prob["lo"], device=dev, requires_grad=True)
+    hi = torch.tensor(prob["hi"], device=dev, requires_grad=True)
+    bound(ctx, lo, hi, params).sum().backward()      # the context's own values: accepted
+    with torch.no_grad():
+        params[2][0, 0] += 1e-3                        # an optimiser step on W_2
+    with pytest.raises(ValueError, match="W_2"):
+        bound(ctx, lo, hi, params)
+    with torch.no_grad():
+        params[2][0, 0] -= 1e-3
+        lo2 = lo.detach().clone()
+        lo2[0, 0] -= 0.01
+    with pytest.raises(ValueError, match="box"):
+        bound(ctx, lo2, hi, params)
+    ctx.reset(lo2, hi, torch.tensor(prob["C"], device=dev))   # reset to the new box: accepted
+    ctx.as_step(10)
+    assert torch.isfinite(bound(ctx, lo2, hi, params)).all()
