@@ -15,6 +15,12 @@
 // to the stage's mbarrier; the stage is refilled once that barrier completes. The epilogue reads the
 // accumulator back with tcgen05.ld (each warp its 32 TMEM lanes) and stores it to global memory.
 //
+// Convolutions whose kernel taps are shifts along one flat grid (stride-1 row passes, every stride
+// phase of a col pass) take window operands instead (Window, win_tile): a CTA loads the input
+// window of its 128 or 256 rows once, all taps included, and each K step's A descriptor starts at
+// the tap's shift inside it, so that an input position is read from memory once per row block
+// instead of once per tap; only B streams through the stages.
+//
 // Every wait is bounded: a stage barrier that does not complete within its limit (stage_limit)
 // sets *status and the CTA stops issuing work, then waits for its last commit with the full limit
 // (all of its MMAs are then complete), frees its TMEM and returns. Should that drain wait run out as
@@ -301,6 +307,175 @@ __device__ __forceinline__ void gemm_tile(const Gather& ga, const uint16_t* __re
     if (warp == 0 && drained) tmem_free(tmem, BN);
 }
 
+// A operand of a convolution whose kernel taps are shifts along one flat grid: rows m of A are the
+// positions of planes of Pg grid positions laid end to end (plane q = m / Pg), and for tap t row m
+// reads source position m + lo + shift[t] (stride 1 over the source grid: a row-pass convolution
+// of stride 1 over the zero-padded input plane, or a stride phase of a col-pass transposed
+// convolution over the output plane with its zero halo). A source position carries 8-channel
+// column blocks (sign, octet): block (g, o) of position p in plane q at element
+//   base + q pstride + g sign_off + (p - q Pg) cstride + 8 o,
+// zeros outside [0, npos). The K order of B is (tap, block, 8 channels), the blocks padded to an
+// even count ncp (zero blocks) so that every K step of 16 lies within one tap. Rows are outputs
+// where the grid position (y, x) = ((m % Pg) / Wg, (m % Pg) % Wg) lies in [y0, y0 + ny) x
+// [x0, x0 + nx), output index q (ny nx) + (y - y0) nx + (x - x0); the other rows are computed and
+// dropped.
+constexpr int CB_WIN_TAPS = 16;
+struct Window {
+    const uint16_t* base;
+    long long pstride, sign_off, npos;
+    int nsign, noct, ncp, cstride;
+    int lo, nw;                     // window start relative to the tile's first row; positions held
+    int ntaps;
+    int shift[CB_WIN_TAPS];         // per tap, relative to the window start (0 .. nw - rows)
+    int Pg, Wg, y0, x0, ny, nx;
+};
+
+// Shared memory of a window tile: TC_STAGES B stages, the window (ncp blocks of nw positions, 16
+// bytes each), barriers and the TMEM address.
+__host__ __device__ constexpr int win_smem_bytes(int bn, int ncp, int nw) {
+    return TC_STAGES * bn * TC_BK * 2 + ncp * nw * 16 + 64;
+}
+
+// One CTA's MT x 128 rows x BN columns of D = A . B^T with A the window operand w: the CTA loads
+// its window once (every tap's rows), then streams B in K tiles of 64 through TC_STAGES stages; the
+// MMA of K step c (tap t = c / (ncp / 2), block pair j) takes its A operand at the window position
+// shift[t] (+ 128 u for row block u) and blocks 2j, 2j + 1: core matrices adjacent in M 128 bytes
+// apart, in K nw * 16 bytes. Accumulators: MT x BN TMEM columns. D plane-transposed over the output
+// positions (Pq = ny nx per plane): row m's column n at D[(q N + n) Pq + output index].
+template <int BN, int MT>
+__device__ __forceinline__ void win_tile(const Window& w, const uint16_t* __restrict__ B, int ldb,
+                                         float* __restrict__ D, int M, int N, int K, int* status,
+                                         uint32_t stage_limit) {
+    static_assert(BN == 16 || BN == 32 || BN == 64 || BN == 128, "BN");
+    static_assert(MT == 1 || MT == 2, "MT");
+    constexpr int B_BYTES = BN * TC_BK * 2;
+    constexpr uint32_t TCOLS = MT * BN < 32 ? 32u : static_cast<uint32_t>(MT * BN);
+    extern __shared__ __align__(128) uint8_t smem[];
+    const int nw = w.nw, ncp = w.ncp;
+    uint8_t* winp = smem + TC_STAGES * B_BYTES;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(winp + ncp * nw * 16);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + TC_STAGES);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * (MT * TC_BM), n0 = blockIdx.y * BN;
+    if (warp == 0) tmem_alloc(tslot, TCOLS);
+    if (tid == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) mbar_init(&bars[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    const uint32_t sbase = smem_u32(smem), wbase = smem_u32(winp);
+    // the window: positions m0 + lo .. m0 + lo + nw - 1, block fastest (a position's blocks are
+    // adjacent in global memory)
+    {
+        const long long p0 = (long long)m0 + w.lo;
+        const int ncols = w.nsign * w.noct;
+        const int q0 = p0 >= 0 ? (int)(p0 / w.Pg) : 0;
+        for (int i = tid; i < nw * ncp; i += TC_THREADS) {
+            const int r = i / ncp, cb = i - r * ncp;
+            const long long pos = p0 + r;
+            const bool in = cb < ncols && pos >= 0 && pos < w.npos;
+            const uint16_t* src = w.base;
+            if (in) {
+                int q = q0;
+                long long pr = pos - (long long)q0 * w.Pg;
+                while (pr >= w.Pg) {   // a window spans at most nw / Pg + 1 planes
+                    pr -= w.Pg;
+                    ++q;
+                }
+                const int g = cb / w.noct, o = cb - g * w.noct;
+                src = w.base + (long long)q * w.pstride + g * w.sign_off + pr * w.cstride + o * 8;
+            }
+            cp_async16(wbase + static_cast<uint32_t>((cb * nw + r) * 16), src, in ? 16u : 0u);
+        }
+    }
+    const int KT = (K + TC_BK - 1) / TC_BK, nchunks = K / 16, cpt = ncp / 2;
+    if (KT > 0) stage_tile(sbase, B, ldb, n0, N, 0, K, BN);
+    cp_async_commit();   // group 0: the window and B tile 0
+#pragma unroll
+    for (int p = 1; p < TC_STAGES - 1; ++p) {
+        if (p < KT) stage_tile(sbase + p * B_BYTES, B, ldb, n0, N, p * TC_BK, K, BN);
+        cp_async_commit();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    constexpr uint32_t idesc = idesc_bf16(TC_BM, BN);
+    bool ok = true;
+    int issued = 0;
+    for (int kt = 0; kt < KT; ++kt) {
+        const int s = kt % TC_STAGES;
+        const int kn = kt + TC_STAGES - 1;
+        bool w_ok = true;
+        if (kn < KT && kt >= 1)
+            w_ok = mbar_wait(&bars[(kt - 1) % TC_STAGES], ((kt - 1) / TC_STAGES) & 1u, stage_limit);
+        if (!__syncthreads_and(w_ok)) {
+            ok = false;
+            break;
+        }
+        if (kn < KT) stage_tile(sbase + (kn % TC_STAGES) * B_BYTES, B, ldb, n0, N, kn * TC_BK, K, BN);
+        cp_async_commit();
+        cp_async_wait<TC_STAGES - 1>();
+        fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t b = sbase + s * B_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < TC_BK / 16; ++kk) {
+                const int c = kt * (TC_BK / 16) + kk;
+                if (c < nchunks) {
+                    const int t = c / cpt, j = c - t * cpt;
+                    const uint32_t a = wbase + static_cast<uint32_t>((2 * j * nw + w.shift[t]) * 16);
+                    const uint64_t bd = smem_desc(b + kk * 256, 128, 1024);
+#pragma unroll
+                    for (int u = 0; u < MT; ++u)
+                        mma_bf16(tmem + u * BN, smem_desc(a + u * TC_BM * 16, nw * 16, 128), bd, idesc,
+                                 c > 0 ? 1u : 0u);
+                }
+            }
+            mma_commit(&bars[s]);
+        }
+        ++issued;
+    }
+    cp_async_wait<0>();
+    bool f_ok = true;
+    if (issued > 0) {
+        const int last = issued - 1;
+        f_ok = mbar_wait(&bars[last % TC_STAGES], (last / TC_STAGES) & 1u);
+    }
+    const bool drained = __syncthreads_and(f_ok);
+    ok = __syncthreads_and(ok && drained);
+    if (!ok && tid == 0 && status) atomicExch(status, TC_ERR_TIMEOUT);
+    tc_fence_after();
+    if (ok) {
+        const long long Pq = (long long)w.ny * w.nx;
+#pragma unroll 1
+        for (int u = 0; u < MT; ++u) {
+            const int m = m0 + u * TC_BM + warp * 32 + lane;
+            long long dofs = -1;
+            if (m < M) {
+                const int q = m / w.Pg, p = m - q * w.Pg;
+                const int y = p / w.Wg - w.y0, x = p % w.Wg - w.x0;
+                if (y >= 0 && y < w.ny && x >= 0 && x < w.nx) dofs = (long long)q * N * Pq + (long long)y * w.nx + x;
+            }
+#pragma unroll 1
+            for (int c0 = 0; c0 < BN; c0 += 16) {
+                float v[16];
+                tmem_ld16(tmem + (static_cast<uint32_t>(warp * 32) << 16) + u * BN + c0, v);
+                if (dofs >= 0) {
+                    float* dr = D + dofs + (long long)(n0 + c0) * Pq;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (n0 + c0 + j < N) dr[(long long)j * Pq] = v[j];
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0 && drained) tmem_free(tmem, TCOLS);
+}
+
 template <int BN>
 __global__ void __launch_bounds__(TC_THREADS) k_gemm_bf16(Gather ga, const uint16_t* __restrict__ B, int ldb,
                                                           float* __restrict__ D, int ldd, int M, int N, int K,
@@ -315,6 +490,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_bf16(Gather ga, const uint1
 // the current iteration; col pass: before it). CTAs past the rows in use return at once.
 struct GemmGroup {
     Gather ga[CB_MAXPH];
+    Window wa[CB_MAXPH];          // window operands (k_gemm_wgroup_bf16)
     const uint16_t* B[CB_MAXPH];
     float* D[CB_MAXPH];
     int M[CB_MAXPH];              // rows for all 1 + cap slots
@@ -330,9 +506,8 @@ struct GemmGroup {
                                   // exercise the timeout path)
 };
 
-template <int BN>
-__global__ void __launch_bounds__(TC_THREADS) k_gemm_group_bf16(GemmGroup gg, int* status) {
-    const int g = blockIdx.z;
+// Rows of GEMM g in use at the current iteration.
+__device__ __forceinline__ int group_rows(const GemmGroup& gg, int g) {
     const int it = *gg.ctr;
     int ns = 0;
     if (it >= gg.sc.TM) {
@@ -342,10 +517,25 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_group_bf16(GemmGroup gg, in
         ns = ns < gg.sc.maxcut ? ns : gg.sc.maxcut;
     }
     const long long want = (long long)(1 + ns) * gg.rows_per_slot[g];
-    const int M = want < gg.M[g] ? (int)want : gg.M[g];
+    return want < gg.M[g] ? (int)want : gg.M[g];
+}
+
+template <int BN>
+__global__ void __launch_bounds__(TC_THREADS) k_gemm_group_bf16(GemmGroup gg, int* status) {
+    const int g = blockIdx.z;
+    const int M = group_rows(gg, g);
     if ((int)blockIdx.x * TC_BM >= M) return;   // the whole CTA leaves together, before any barrier
     gemm_tile<BN>(gg.ga[g], gg.B[g], gg.ldb[g], gg.D[g], gg.ldd, M, gg.N, gg.K[g], status,
                   gg.transposed && gg.ga[g].P > 1 ? gg.ga[g].P : 0, gg.stage_limit);
+}
+
+// The group's GEMMs with window operands (win_tile), MT row blocks of 128 per CTA.
+template <int BN, int MT>
+__global__ void __launch_bounds__(TC_THREADS) k_gemm_wgroup_bf16(GemmGroup gg, int* status) {
+    const int g = blockIdx.z;
+    const int M = group_rows(gg, g);
+    if ((long long)blockIdx.x * (MT * TC_BM) >= M) return;
+    win_tile<BN, MT>(gg.wa[g], gg.B[g], gg.ldb[g], gg.D[g], M, gg.N, gg.K[g], status, gg.stage_limit);
 }
 
 }  // namespace tc

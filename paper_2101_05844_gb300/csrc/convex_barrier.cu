@@ -59,6 +59,7 @@ struct as_ctx {
     struct TcGemm {
         tc::GemmGroup g;
         int ng, maxM, bn;
+        int win = 0, mt = 1, smem = 0;   // window operands (k_gemm_wgroup_bf16): row blocks per CTA, bytes
     };
     std::vector<TcGemm> tc_row, tc_col;           // per hidden-output layer
     std::vector<std::pair<void*, size_t>> planes; // bf16 operand planes, cleared with each batch
@@ -67,6 +68,9 @@ struct as_ctx {
     int blocksTA1 = 0, blocksTB1 = 0;
     long long team_row = 40000, team_col = 40000; // team-size targets of the float32 passes
     uint32_t tc_stage_limit = tc::TC_WAIT_LIMIT;  // try_wait rounds of the GEMMs' stage waits
+    // conv products of the BF16 form by window operands where their taps are shifts of one grid
+    // (environment CB_TC_WINDOWS = 0: the gathered operands everywhere, to compare the two)
+    bool tc_windows = true;
     // host-side fault injection for tests (environment CB_FAIL_ALLOC_AT = n): the n-th device
     // allocation of the context is refused as if the device were out of memory
     long long fail_alloc_at = 0, alloc_calls = 0;
@@ -832,6 +836,7 @@ extern "C" int as_init(as_ctx** out, const as_net* net, int S, const float* x_lo
     c->stream = (cudaStream_t)stream;
     if (const char* f = getenv("CB_FAIL_ALLOC_AT")) c->fail_alloc_at = atoll(f);
     if (const char* f = getenv("CB_TC_STAGE_WAIT_LIMIT")) c->tc_stage_limit = (uint32_t)strtoul(f, nullptr, 10);
+    if (const char* f = getenv("CB_TC_WINDOWS")) c->tc_windows = atoi(f) != 0;
     cudaError_t e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         delete c;

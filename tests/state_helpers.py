@@ -112,3 +112,24 @@ def draw_state(Ps, ctx, opt_kw, it, nslots, seed, scale=0.3, adam=True, subset=N
 
 def hidden_concat(lists):
     return np.concatenate([np.asarray(v) for v in lists[1:]])
+
+
+def conv4_full_batch(precision, opt_kw, sample):
+    """The conv4 workload at full size (1024 boxes) in the bench's launch configuration (CUDA
+    graphs of 25 iterations), and the oracle's problems for the sampled boxes only, over the
+    context's own interval bounds (the oracle's dense conv operators are large; interval bounds
+    have tests of their own). Returns (ctx, Ps): Ps a list over all boxes, None where not sampled."""
+    from oracle import network as nw
+    from paper_2101_05844_gb300 import synth
+    prob = synth.problem("conv4", seed=0)
+    S = prob["lo"].shape[0]
+    ctx = binding.context_for(prob, binding.default_options(graph_chunk=25, precision=precision, **opt_kw))
+    lh = ctx.get_state(binding.ST_LHAT).reshape(S, -1).astype(np.float64)
+    uh = ctx.get_state(binding.ST_UHAT).reshape(S, -1).astype(np.float64)
+    dense = nw.dense_layers(prob["net"])
+    Ps = [None] * S
+    for s in sample:
+        one = dict(prob, lo=prob["lo"][s:s + 1], hi=prob["hi"][s:s + 1], C=prob["C"][s:s + 1])
+        bd = (split_hidden(lh[s], ctx.widths)[1:], split_hidden(uh[s], ctx.widths)[1:])
+        Ps[s] = nw.problems(one, bounds=[bd], dense=dense)[0]
+    return ctx, Ps

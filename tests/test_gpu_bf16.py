@@ -29,7 +29,7 @@ from oracle import network as nw
 from oracle import relaxation as rx
 from paper_2101_05844_gb300 import binding, synth
 from tests.helpers import netlp_for, sample_min_output
-from tests.state_helpers import draw_state, hidden_concat, oracle_bounds_f32, split_hidden
+from tests.state_helpers import conv4_full_batch, draw_state, hidden_concat, oracle_bounds_f32, split_hidden
 
 pytestmark = pytest.mark.gpu
 E_REL = 2.0 ** -7
@@ -47,12 +47,22 @@ def _lib():
 
 def _adam_range(theta, m, v, g, e, lr, step, opt):
     """Range of one oracle Adam step (AS.adam) over gradients in [g - e, g + e]. The step is not
-    monotone in g (the second moment grows with g^2, so m_hat / sqrt(v_hat) can peak inside the
-    interval when v is small): the interval is sampled densely."""
+    monotone in g: with a = b1 m, c = 1 - b1, d = b2 v, h = 1 - b2 the update is proportional to
+    (a + c g) / sqrt(d + h g^2) (up to eps), whose one stationary point is g* = c d / (a h). The
+    interval is sampled densely, and g* (with a fine grid around it, for eps) is added where it
+    lies inside."""
+    g = np.asarray(g, np.float64)
+    e = np.broadcast_to(np.asarray(e, np.float64), g.shape)
+    cands = [g + d * e for d in np.linspace(-1.0, 1.0, 129)]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        gs = (1 - opt.adam_b1) * opt.adam_b2 * v / (opt.adam_b1 * (1 - opt.adam_b2) * m)
+    gs = np.where(np.isfinite(gs), gs, g)
+    for r in np.linspace(-1e-3, 1e-3, 21):
+        cands.append(np.clip(gs * (1 + r), g - e, g + e))
     outs = []
-    for d in np.linspace(-1.0, 1.0, 129):
+    for gg in cands:
         th, mm, vv = theta.copy(), m.copy(), v.copy()
-        AS.adam(th, mm, vv, g + d * e, lr, step, opt)
+        AS.adam(th, mm, vv, gg, lr, step, opt)
         outs.append(th)
     return np.min(outs, 0), np.max(outs, 0)
 
@@ -68,33 +78,24 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("name,S,kw,it,nslots", CASES)
-def test_bf16_one_iteration_within_rounding_bound(name, S, kw, it, nslots):
-    prob = synth.problem(name, S=S, seed=0)
-    dense = nw.dense_layers(prob["net"])   # conv operators built once for all subproblems
-    Ps0 = nw.problems(prob, dense=dense)
-    lh, uh = oracle_bounds_f32(Ps0)
-    widths = Ps0[0].widths
-    Ps = nw.problems(prob, bounds=[(split_hidden(lh[s].astype(np.float64), widths)[1:],
-                                    split_hidden(uh[s].astype(np.float64), widths)[1:]) for s in range(S)],
-                     dense=dense)
-    ctx = binding.context_for(prob, binding.default_options(graph_chunk=0, precision=16, **kw), bounds=(lh, uh))
-    solvers = draw_state(Ps, ctx, kw, it, nslots, seed=100 + it)
-    opt = AS.Options(**{k: v for k, v in kw.items() if hasattr(AS.Options, k)})
-    # the oracle's pre-step values and the step's schedule
-    pre = [dict(alpha=[None if a is None else a.copy() for a in sv.st.alpha],
-                beta0=[None if a is None else a.copy() for a in sv.st.beta0],
-                beta1=[None if a is None else a.copy() for a in sv.st.beta1],
-                m={q: [None if a is None else a.copy() for a in sv.m[q]] for q in sv.m},
-                v={q: [None if a is None else a.copy() for a in sv.v[q]] for q in sv.v},
-                slots=[[(sl.beta.copy(), sl.m.copy(), sl.v.copy(), sl.added_at) for sl in sv.st.slots[k]]
-                       for k in range(sv.P.n)]) for sv in solvers]
-    if it < opt.bigm_iters:
-        lr, t = AS.linear_lr(opt.bigm_lr0, opt.bigm_lr1, it, opt.bigm_iters), -1
-    else:
-        t = it - opt.bigm_iters
-        lr = AS.linear_lr(opt.as_lr0, opt.as_lr1, t, opt.as_iters)
-    ctx.as_step(1)
+def pre_step(solvers):
+    """The oracle solvers' values before the step (the range check needs them after the oracle's own
+    step)."""
+    return {s: dict(alpha=[None if a is None else a.copy() for a in sv.st.alpha],
+                    beta0=[None if a is None else a.copy() for a in sv.st.beta0],
+                    beta1=[None if a is None else a.copy() for a in sv.st.beta1],
+                    m={q: [None if a is None else a.copy() for a in sv.m[q]] for q in sv.m},
+                    v={q: [None if a is None else a.copy() for a in sv.v[q]] for q in sv.v},
+                    slots=[[(sl.beta.copy(), sl.m.copy(), sl.v.copy(), sl.added_at) for sl in sv.st.slots[k]]
+                           for k in range(sv.P.n)]) for s, sv in solvers.items()}
+
+
+def check_bf16_step(ctx, solvers, pre, it, t, lr, opt):
+    """After one GPU iteration of the BF16 form from the drawn state: z* exact, x* equal wherever
+    the oracle's |f| clears the bf16 bound, every dual in the range of the oracle's Adam step over
+    gradients within the bound (solvers, pre: dicts over the checked subproblems; the oracle
+    solvers take their own step here). Returns (rows checked in full, rows)."""
+    S = ctx.S
     xstar = ctx.get_state(binding.ST_XSTAR).reshape(S, -1)
     zstar = ctx.get_state(binding.ST_ZSTAR, np.uint8).reshape(S, -1)
     al = ctx.get_state(binding.ST_ALPHA).reshape(S, -1)
@@ -102,7 +103,7 @@ def test_bf16_one_iteration_within_rounding_bound(name, S, kw, it, nslots):
     b1 = ctx.get_state(binding.ST_BETA1).reshape(S, -1)
     sb = ctx.get_state(binding.ST_SLOT_BETA).reshape(S, ctx.cap, -1)
     rows_checked = rows_total = 0
-    for s, sv in enumerate(solvers):
+    for s, sv in solvers.items():
         P = sv.P
         _, f, g, x, z = du.evaluate(P, sv.st)
         grads = du.supergradient(P, sv.st, x, z)
@@ -166,6 +167,51 @@ def test_bf16_one_iteration_within_rounding_bound(name, S, kw, it, nslots):
                 gnew = x[k] - (P.W[k] * I) @ x[k - 1] + lam_n * (1 - z[k]) - z[k] * (P.b[k] + mu_n)
                 zero = np.zeros_like(gnew)
                 in_range(sb[s, slots_before, h], zero, zero, zero, gnew, 2 * ex[k], 1, own)
+    return rows_checked, rows_total
+
+
+@pytest.mark.parametrize("name,S,kw,it,nslots", CASES)
+def test_bf16_one_iteration_within_rounding_bound(name, S, kw, it, nslots):
+    prob = synth.problem(name, S=S, seed=0)
+    dense = nw.dense_layers(prob["net"])   # conv operators built once for all subproblems
+    Ps0 = nw.problems(prob, dense=dense)
+    lh, uh = oracle_bounds_f32(Ps0)
+    widths = Ps0[0].widths
+    Ps = nw.problems(prob, bounds=[(split_hidden(lh[s].astype(np.float64), widths)[1:],
+                                    split_hidden(uh[s].astype(np.float64), widths)[1:]) for s in range(S)],
+                     dense=dense)
+    ctx = binding.context_for(prob, binding.default_options(graph_chunk=0, precision=16, **kw), bounds=(lh, uh))
+    solvers = draw_state(Ps, ctx, kw, it, nslots, seed=100 + it)
+    opt = AS.Options(**{k: v for k, v in kw.items() if hasattr(AS.Options, k)})
+    # the oracle's pre-step values and the step's schedule
+    solvers = dict(enumerate(solvers))
+    pre = pre_step(solvers)
+    if it < opt.bigm_iters:
+        lr, t = AS.linear_lr(opt.bigm_lr0, opt.bigm_lr1, it, opt.bigm_iters), -1
+    else:
+        t = it - opt.bigm_iters
+        lr = AS.linear_lr(opt.as_lr0, opt.as_lr1, t, opt.as_iters)
+    ctx.as_step(1)
+    rows_checked, rows_total = check_bf16_step(ctx, solvers, pre, it, t, lr, opt)
+    assert rows_checked >= 0.9 * rows_total, (rows_checked, rows_total)
+
+
+@pytest.mark.parametrize("it,nslots", [(300, 4), (340, 4)])
+def test_bf16_conv4_full_size_one_iteration_on_a_sampled_box(it, nslots):
+    """The default bench workload at full size (conv4 net, 1024 boxes, BF16 form) in the bench's
+    launch configuration: one iteration from a drawn state with 4 filled slots (omega 120:
+    iteration 300 is ordinary, 340 adds slot 4), one sampled box against the oracle within the
+    bf16 bound (its stride-1 conv products and every col-pass product take window operands)."""
+    kw = dict(bigm_iters=100, as_iters=400, omega=120, max_cuts=5)
+    sample = {613}
+    ctx, Ps = conv4_full_batch(16, kw, sample)
+    solvers = draw_state(Ps, ctx, kw, it, nslots, seed=700 + it, subset=sample)
+    opt = AS.Options(**kw)
+    pre = pre_step(solvers)
+    t = it - opt.bigm_iters
+    lr = AS.linear_lr(opt.as_lr0, opt.as_lr1, t, opt.as_iters)
+    ctx.as_step(1)
+    rows_checked, rows_total = check_bf16_step(ctx, solvers, pre, it, t, lr, opt)
     assert rows_checked >= 0.9 * rows_total, (rows_checked, rows_total)
 
 
@@ -216,3 +262,24 @@ def test_bf16_graph_replay_equals_plain_launches():
     g.as_step(50)
     np.testing.assert_array_equal(a.get_state(binding.ST_SLOT_BETA), g.get_state(binding.ST_SLOT_BETA))
     np.testing.assert_array_equal(a.bound(), g.bound())
+
+
+def test_window_and_gathered_products_agree(monkeypatch):
+    """The conv products by window operands (each CTA loads its rows' input window once; a kernel
+    tap is a shift of the operand descriptor) and by gathered operands (environment CB_TC_WINDOWS =
+    0) sum the same bf16 terms in another order: one iteration from the same drawn state on 8 boxes
+    of the conv4 batch gives duals equal up to float32 summation order (a decision near a tie may
+    flip: at least 99.9% of the entries agree)."""
+    kw = dict(bigm_iters=100, as_iters=400, omega=120, max_cuts=5)
+    prob = synth.problem("conv4", S=1024, seed=0, part=(0, 8))
+    out = {}
+    for flag in ("1", "0"):
+        monkeypatch.setenv("CB_TC_WINDOWS", flag)
+        ctx = binding.context_for(prob, binding.default_options(graph_chunk=25, precision=16, **kw))
+        draw_state([None] * ctx.S, ctx, kw, 340, 4, seed=9, subset=set())
+        ctx.as_step(1)
+        out[flag] = [ctx.get_state(code).ravel() for code in
+                     (binding.ST_ALPHA, binding.ST_BETA0, binding.ST_BETA1, binding.ST_SLOT_BETA, binding.ST_XSTAR)]
+    for a, b in zip(out["1"], out["0"]):
+        close = np.abs(a - b) <= 1e-5 * (1 + np.abs(b))
+        assert close.mean() >= 0.999, close.mean()

@@ -22,7 +22,7 @@ from oracle import saddle as SPm
 from paper_2101_05844_gb300 import binding, synth
 from tests.helpers import sample_min_output
 from tests.lockstep import check_active_set_step
-from tests.state_helpers import draw_state, hidden_concat, oracle_bounds_f32, split_hidden
+from tests.state_helpers import conv4_full_batch, draw_state, hidden_concat, oracle_bounds_f32, split_hidden
 
 pytestmark = pytest.mark.gpu
 
@@ -495,6 +495,34 @@ def test_full_size_wide_conv_lockstep_on_sampled_subproblems(it, nslots):
     for s, sv in solvers.items():
         # wide rows (fan-in up to 2048) widen the float32 bound: at least 80% of the entries are
         # checked at the rounding tolerance itself, the rest within the spread it allows
+        res = check_active_set_step(sv, dict(alpha=st["alpha"][s], beta0=st["beta0"][s], beta1=st["beta1"][s],
+                                             slots=sb[s], xstar=st["xstar"][s]), min_tight=0.8)
+        assert res["checked"] >= 0.9 * 3 * res["rows"]
+
+
+C4_KW = dict(bigm_iters=100, as_iters=400, omega=120, max_cuts=5)   # the default bench schedule
+
+
+@pytest.mark.parametrize("it,nslots", [(340, 4)])
+def test_full_size_conv4_lockstep_on_sampled_boxes(it, nslots):
+    """The default bench workload at full size (conv4 net, 1024 boxes) in the float32 form and the
+    bench's launch configuration: one Active Set iteration from a drawn state with 4 filled slots
+    (omega 120: iteration 340 adds slot 4), every dual of two sampled boxes against the oracle."""
+    sample = {0, 777}
+    ctx, Ps = conv4_full_batch(32, C4_KW, sample)
+    solvers = draw_state(Ps, ctx, C4_KW, it, nslots, seed=500 + it, subset=sample)
+    gb = ctx.bound()
+    for s, sv in solvers.items():
+        assert gb[s] == pytest.approx(du.evaluate(sv.P, sv.st)[0], abs=1e-4, rel=1e-5)
+    ctx.as_step(1)
+    S = ctx.S
+    st = {key: ctx.get_state(code).reshape(S, -1) for key, code in
+          (("alpha", binding.ST_ALPHA), ("beta0", binding.ST_BETA0), ("beta1", binding.ST_BETA1),
+           ("xstar", binding.ST_XSTAR))}
+    sb = ctx.get_state(binding.ST_SLOT_BETA).reshape(S, ctx.cap, -1)
+    for s, sv in solvers.items():
+        # conv rows have fan-in 27-576 and FC rows 4096: at least 80% of the entries are checked at
+        # the rounding tolerance itself, the rest within the spread it allows
         res = check_active_set_step(sv, dict(alpha=st["alpha"][s], beta0=st["beta0"][s], beta1=st["beta1"][s],
                                              slots=sb[s], xstar=st["xstar"][s]), min_tight=0.8)
         assert res["checked"] >= 0.9 * 3 * res["rows"]
