@@ -89,8 +89,9 @@ __device__ __forceinline__ float adam_step(float th, float& m, float& v, float g
 
 // ------------------------------------------------------------------------- interval bounds
 // Interval propagation for hidden layer L (App. E): lhat = W+ l + W- u + b, uhat = W+ u + W- l + b
-// accumulated in FP64, rounded outward to float32; splits clamp straddling neurons; then the
-// post-activation box max(., 0).
+// accumulated to float64 accuracy (compensated float32 lanes, CompSum), rounded outward to
+// float32; splits clamp straddling neurons; then the post-activation box max(., 0). Over an
+// ellipsoid (layer 1 of an l2-ball input set) the centre product and the radius in float64.
 __global__ void k_ibp(DNet net, DState st, int li, const signed char* splits) {
     const DLayer& L = net.L[li];
     const int warp = (blockIdx.x * CB_THREADS + threadIdx.x) >> 5, lane = threadIdx.x & 31;
@@ -101,18 +102,26 @@ __global__ void k_ibp(DNet net, DState st, int li, const signed char* splits) {
     double a = 0.0, c = 0.0;
     int nf = 0;
     const bool ell = net.ball && li == 0;
-    row_walk(L, i, lane, [&](int j, float w) {
-        const double wd = w;
-        if (ell) {   // centre product and the squared radius of W_i over the ellipsoid
-            const double e = 0.5 * ((double)hi[j] - (double)lo[j]);
+    if (ell) {
+        row_walk(L, i, lane, [&](int j, float w) {   // centre product and squared radius of W_i
+            const double wd = w, e = 0.5 * ((double)hi[j] - (double)lo[j]);
             a += wd * 0.5 * ((double)lo[j] + (double)hi[j]);
             c += wd * wd * e * e;
-        } else if (w >= 0.f) { a += wd * lo[j]; c += wd * hi[j]; }
-        else { a += wd * hi[j]; c += wd * lo[j]; }
-        nf += (w != 0.f && lo[j] != hi[j]) ? 1 : 0;
-    });
-    a = warp_sum(a);
-    c = warp_sum(c);
+            nf += (w != 0.f && lo[j] != hi[j]) ? 1 : 0;
+        });
+        a = warp_sum(a);
+        c = warp_sum(c);
+    } else {
+        CompSum ca, cc;
+        row_walk(L, i, lane, [&](int j, float w) {
+            const float l = lo[j], u = hi[j];
+            ca.add_prod(w, w >= 0.f ? l : u);
+            cc.add_prod(w, w >= 0.f ? u : l);
+            nf += (w != 0.f && l != u) ? 1 : 0;
+        });
+        a = ca.warp_total();
+        c = cc.warp_total();
+    }
     for (int o = 16; o > 0; o >>= 1) nf += __shfl_xor_sync(0xffffffffu, nf, o);
     if (lane == 0 && !ell) {
         // the row constants of the batch, the same sums before the bias (k_lz computes them alone

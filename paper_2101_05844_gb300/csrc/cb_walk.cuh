@@ -90,4 +90,24 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+// Compensated float32 sum of products (a lane's share of a row sum): every product is split
+// exactly into p + pe (TwoProd by one fma) and added by TwoSum (Knuth), the rounding errors
+// gathered in c, so that s + c holds the partial sum to about k 2^-48 of its sum of |terms| after k
+// terms, the accuracy of a float64 accumulation, at float32 rates (float64 is a narrow pipe on this
+// part). The _rn intrinsics keep the compiler from contracting the error-free steps into fmas.
+struct CompSum {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add_prod(float w, float x) {
+        const float p = __fmul_rn(w, x);
+        const float pe = __fmaf_rn(w, x, -p);
+        const float t = __fadd_rn(s, p);
+        const float z = __fsub_rn(t, s);
+        const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+        s = t;
+        c = __fadd_rn(c, __fadd_rn(e, pe));
+    }
+    // the warp's row sum: the lanes' pairs combined in float64
+    __device__ __forceinline__ double warp_total() const { return warp_sum((double)s + (double)c); }
+};
+
 }  // namespace cb

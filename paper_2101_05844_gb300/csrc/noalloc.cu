@@ -42,8 +42,8 @@ bool on_device(const void* p, int dev) {
     return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
-// One hidden layer of interval propagation (App. E): FP64 accumulation of W+ l + W- u + b and
-// W+ u + W- l + b, outward rounding to float32, split clamps of straddling neurons, then the
+// One hidden layer of interval propagation (App. E): W+ l + W- u + b and W+ u + W- l + b to float64
+// accuracy (the context's compensated float32 sums, in the same order), outward rounding to float32, split clamps of straddling neurons, then the
 // post-activation box written to the next region of the scratch.
 __global__ void k_ibp_noalloc(DLayer L, int S, int bias_per, const float* in_lo, const float* in_hi,
                               int in_stride, const signed char* splits, int NH, int h_off, float* lhat,
@@ -53,14 +53,13 @@ __global__ void k_ibp_noalloc(DLayer L, int S, int bias_per, const float* in_lo,
     const int s = warp / L.n_out, i = warp - s * L.n_out;
     const float* lo = in_lo + (size_t)s * in_stride;
     const float* hi = in_hi + (size_t)s * in_stride;
-    double a = 0.0, c = 0.0;
+    cb::CompSum ca, cc;
     cb::row_walk(L, i, lane, [&](int j, float w) {
-        const double wd = w;
-        if (w >= 0.f) { a += wd * lo[j]; c += wd * hi[j]; }
-        else { a += wd * hi[j]; c += wd * lo[j]; }
+        const float l = lo[j], u = hi[j];
+        ca.add_prod(w, w >= 0.f ? l : u);
+        cc.add_prod(w, w >= 0.f ? u : l);
     });
-    a = cb::warp_sum(a);
-    c = cb::warp_sum(c);
+    double a = ca.warp_total(), c = cc.warp_total();
     if (lane == 0) {
         const double bi = (double)L.b[i / bias_per];
         a += bi;
