@@ -364,27 +364,46 @@ __device__ __forceinline__ void win_tile(const Window& w, const uint16_t* __rest
     }
     const uint32_t sbase = smem_u32(smem), wbase = smem_u32(winp);
     // the window: positions m0 + lo .. m0 + lo + nw - 1, block fastest (a position's blocks are
-    // adjacent in global memory)
+    // adjacent in global memory). With ncp a power of two a thread keeps one block and walks the
+    // positions TC_THREADS / ncp apart, its plane and in-plane position carried along.
     {
         const long long p0 = (long long)m0 + w.lo;
         const int ncols = w.nsign * w.noct;
         const int q0 = p0 >= 0 ? (int)(p0 / w.Pg) : 0;
-        for (int i = tid; i < nw * ncp; i += TC_THREADS) {
-            const int r = i / ncp, cb = i - r * ncp;
-            const long long pos = p0 + r;
-            const bool in = cb < ncols && pos >= 0 && pos < w.npos;
-            const uint16_t* src = w.base;
-            if (in) {
-                int q = q0;
-                long long pr = pos - (long long)q0 * w.Pg;
-                while (pr >= w.Pg) {   // a window spans at most nw / Pg + 1 planes
+        if ((ncp & (ncp - 1)) == 0 && ncp <= TC_THREADS) {
+            const int lg = __ffs(ncp) - 1, cb = tid & (ncp - 1), dr = TC_THREADS >> lg;
+            const int g = cb / w.noct, o = cb - g * w.noct;
+            const uint16_t* bsrc = w.base + g * w.sign_off + o * 8;
+            int r = tid >> lg, q = q0;
+            long long pr = p0 + r - (long long)q0 * w.Pg;
+            for (; r < nw; r += dr, pr += dr) {
+                while (pr >= w.Pg) {   // a step of dr < Pg positions crosses at most one plane
                     pr -= w.Pg;
                     ++q;
                 }
-                const int g = cb / w.noct, o = cb - g * w.noct;
-                src = w.base + (long long)q * w.pstride + g * w.sign_off + pr * w.cstride + o * 8;
+                const long long pos = p0 + r;
+                const bool in = cb < ncols && pos >= 0 && pos < w.npos;
+                const uint16_t* src = in ? bsrc + (long long)q * w.pstride + pr * w.cstride : w.base;
+                cp_async16(wbase + static_cast<uint32_t>((cb * nw + r) * 16), src, in ? 16u : 0u);
             }
-            cp_async16(wbase + static_cast<uint32_t>((cb * nw + r) * 16), src, in ? 16u : 0u);
+        } else {
+            for (int i = tid; i < nw * ncp; i += TC_THREADS) {
+                const int r = i / ncp, cb = i - r * ncp;
+                const long long pos = p0 + r;
+                const bool in = cb < ncols && pos >= 0 && pos < w.npos;
+                const uint16_t* src = w.base;
+                if (in) {
+                    int q = q0;
+                    long long pr = pos - (long long)q0 * w.Pg;
+                    while (pr >= w.Pg) {   // a window spans at most nw / Pg + 1 planes
+                        pr -= w.Pg;
+                        ++q;
+                    }
+                    const int g = cb / w.noct, o = cb - g * w.noct;
+                    src = w.base + (long long)q * w.pstride + g * w.sign_off + pr * w.cstride + o * 8;
+                }
+                cp_async16(wbase + static_cast<uint32_t>((cb * nw + r) * 16), src, in ? 16u : 0u);
+            }
         }
     }
     const int KT = (K + TC_BK - 1) / TC_BK, nchunks = K / 16, cpt = ncp / 2;
