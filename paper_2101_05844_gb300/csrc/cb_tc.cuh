@@ -325,15 +325,16 @@ struct Window {
     long long pstride, sign_off, npos;
     int nsign, noct, ncp, cstride;
     int lo, nw;                     // window start relative to the tile's first row; positions held
+    int bwhole;                     // 1: all of B staged at once with the window (one wait), else streamed
     int ntaps;
     int shift[CB_WIN_TAPS];         // per tap, relative to the window start (0 .. nw - rows)
     int Pg, Wg, y0, x0, ny, nx;
 };
 
-// Shared memory of a window tile: TC_STAGES B stages, the window (ncp blocks of nw positions, 16
-// bytes each), barriers and the TMEM address.
-__host__ __device__ constexpr int win_smem_bytes(int bn, int ncp, int nw) {
-    return TC_STAGES * bn * TC_BK * 2 + ncp * nw * 16 + 64;
+// Shared memory of a window tile: bst B stages (TC_STAGES, or every K tile of B when it is staged
+// whole), the window (ncp blocks of nw positions, 16 bytes each), barriers and the TMEM address.
+__host__ __device__ constexpr int win_smem_bytes(int bn, int ncp, int nw, int bst) {
+    return bst * bn * TC_BK * 2 + ncp * nw * 16 + 64;
 }
 
 // One CTA's MT x 128 rows x BN columns of D = A . B^T with A the window operand w: the CTA loads
@@ -352,7 +353,9 @@ __device__ __forceinline__ void win_tile(const Window& w, const uint16_t* __rest
     constexpr uint32_t TCOLS = MT * BN < 32 ? 32u : static_cast<uint32_t>(MT * BN);
     extern __shared__ __align__(128) uint8_t smem[];
     const int nw = w.nw, ncp = w.ncp;
-    uint8_t* winp = smem + TC_STAGES * B_BYTES;
+    const int KT = (K + TC_BK - 1) / TC_BK, nchunks = K / 16, cpt = ncp / 2;
+    const int bst = w.bwhole ? (KT > TC_STAGES ? KT : TC_STAGES) : TC_STAGES;
+    uint8_t* winp = smem + bst * B_BYTES;
     uint64_t* bars = reinterpret_cast<uint64_t*>(winp + ncp * nw * 16);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + TC_STAGES);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -406,12 +409,13 @@ __device__ __forceinline__ void win_tile(const Window& w, const uint16_t* __rest
             }
         }
     }
-    const int KT = (K + TC_BK - 1) / TC_BK, nchunks = K / 16, cpt = ncp / 2;
     if (KT > 0) stage_tile(sbase, B, ldb, n0, N, 0, K, BN);
-    cp_async_commit();   // group 0: the window and B tile 0
+    if (w.bwhole)
+        for (int kt = 1; kt < KT; ++kt) stage_tile(sbase + kt * B_BYTES, B, ldb, n0, N, kt * TC_BK, K, BN);
+    cp_async_commit();   // group 0: the window and B tile 0 (all of B when staged whole)
 #pragma unroll
     for (int p = 1; p < TC_STAGES - 1; ++p) {
-        if (p < KT) stage_tile(sbase + p * B_BYTES, B, ldb, n0, N, p * TC_BK, K, BN);
+        if (p < KT && !w.bwhole) stage_tile(sbase + p * B_BYTES, B, ldb, n0, N, p * TC_BK, K, BN);
         cp_async_commit();
     }
     tc_fence_before();
@@ -421,7 +425,28 @@ __device__ __forceinline__ void win_tile(const Window& w, const uint16_t* __rest
     constexpr uint32_t idesc = idesc_bf16(TC_BM, BN);
     bool ok = true;
     int issued = 0;
-    for (int kt = 0; kt < KT; ++kt) {
+    if (w.bwhole && KT > 0) {
+        // one wait for the window and B, every MMA, one commit; a wait that runs out (stage_limit)
+        // stops the CTA as in the streamed loop, the drain below waiting with the full limit
+        cp_async_wait<0>();
+        fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            for (int c = 0; c < nchunks; ++c) {
+                const int t = c / cpt, j = c - t * cpt;
+                const uint32_t a = wbase + static_cast<uint32_t>((2 * j * nw + w.shift[t]) * 16);
+                const uint64_t bd = smem_desc(sbase + (c >> 2) * B_BYTES + (c & 3) * 256, 128, 1024);
+#pragma unroll
+                for (int u = 0; u < MT; ++u)
+                    mma_bf16(tmem + u * BN, smem_desc(a + u * TC_BM * 16, nw * 16, 128), bd, idesc, c > 0 ? 1u : 0u);
+            }
+            mma_commit(&bars[0]);
+        }
+        issued = 1;
+        ok = __syncthreads_and(mbar_wait(&bars[0], 0u, stage_limit));
+    }
+    for (int kt = 0; kt < KT && !w.bwhole; ++kt) {
         const int s = kt % TC_STAGES;
         const int kn = kt + TC_STAGES - 1;
         bool w_ok = true;

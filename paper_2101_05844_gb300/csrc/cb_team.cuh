@@ -199,6 +199,14 @@ __device__ __forceinline__ void load_taps(const int2* tap, int t, int tb, int T,
 // position in one 16-byte piece, so the block gathers its values in shared memory, position-major,
 // and stores whole pieces: one 16-byte store per (plane, position) instead of eight 2-byte stores
 // scattered a channel stride apart.
+// 4-byte asynchronous copy global -> shared (L1-allocating): a value in flight holds no register.
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 constexpr int CB_STAGE_PLANES = 2 * (CB_MAXCUT + 1);
 struct TcStage {
     __align__(16) uint16_t v[CB_STAGE_PLANES][CB_THREADS];
@@ -238,35 +246,14 @@ __device__ __forceinline__ int div_stride(int a, int st) { return st == 1 ? a : 
 // with no per-pair mask work; the input's own bits pick p_b Pp_b + q_b Pn_b at the end.
 template <int NS>
 __device__ __forceinline__ void as_colA_body(const DNet& net, const DState& st, const DSched& sc, const DLayer& L,
-                                             int k, bool valid, int s, int j, int lane, int T, int mode, bool tc,
-                                             TcStage* stg, TcPos tp) {
+                                             int k, bool valid, int s, int j, int lane, int T, int mode) {
     const int m = k - 1;
     const Step sp = cb_step(st.ctr[0], sc, st.lr_tab);
     const size_t NT = net.NT, NH = net.NH, cap = net.cap;
     float acc = 0.f, Pp[NS > 0 ? NS : 1], Pn[NS > 0 ? NS : 1];
 #pragma unroll
     for (int b = 0; b < NS; ++b) Pp[b] = Pn[b] = 0.f;
-    if (valid && k <= net.n - 1 && tc) {
-        // BF16 form: the sums come from the tensor-core products of this input's stride phase
-        const BfLayer& B = net.bf[k - 1];
-        int c = j, ph = 0, q = 0;
-        if (L.kind == 1) {
-            c = tp.c;
-            const int ty = tp.y + L.pd, tx = tp.x + L.pd;
-            const int Y0 = div_stride(ty, L.st), X0 = div_stride(tx, L.st);
-            ph = (ty - Y0 * L.st) * L.st + (tx - X0 * L.st);
-            q = (Y0 - B.Y0a[ph]) * B.nX[ph] + (X0 - B.X0a[ph]);
-        }
-        const int P = B.nY[ph] * B.nX[ph];
-        const size_t slot = (size_t)net.S * 2 * L.ci * P, neg = (size_t)L.ci * P;
-        const float* d = B.Dcol[ph] + ((size_t)s * 2 * L.ci + c) * P + q;
-        acc = d[0] + d[neg];
-#pragma unroll
-        for (int b = 0; b < NS; ++b) {
-            Pp[b] = d[(b + 1) * slot];
-            Pn[b] = d[(b + 1) * slot + neg];
-        }
-    } else if (valid && k <= net.n - 1) {
+    if (valid && k <= net.n - 1) {
         int g, base;
         col_group(L, j, g, base);
         const float4* ar = arec_planes(net, st, L, s) + base;
@@ -377,33 +364,155 @@ __device__ __forceinline__ void as_colA_body(const DNet& net, const DState& st, 
     }
     if (k <= net.n - 1) {
         const unsigned mpos = ((~xs_new) & 0xFFu) | fxm, mneg = (xs_new & 0xFFu) | fxm;
-        if (tc) {
-            // BF16 form: the row pass's tensor-core operand, x* (slot 0) and x* p_b / x* q_b
+        // row-pass input record: x* and the slot masks p_b (bits 0-7) and q_b (bits 8-15)
+        reinterpret_cast<float2*>(st.xin + (size_t)s * net.XT + L.xo)[xin_pos(L, j)] =
+            make_float2(xv, __uint_as_float(mpos | (mneg << 8)));
+    }
+}
+
+// Floats per thread of the BF16 col pass's prefetch (as_colA_tc): the W+ and W- products of slot 0
+// and of every slot, l and u, five dual and bound values, three per slot.
+__host__ __device__ constexpr int colA_tc_vals(int cap) { return 9 + 5 * cap; }
+
+// The BF16 form's col pass for one unit (one lane per unit): as as_colA_body with tc, but every
+// value it reads from the state is first copied to shared memory with cp.async (this thread's
+// column of buf, colA_tc_vals(cap) floats a CB_THREADS apart), all copies in flight together
+// without holding registers.
+template <int NS>
+__device__ __forceinline__ void as_colA_tc(const DNet& net, const DState& st, const DSched& sc, const DLayer& L,
+                                           int k, bool valid, int s, int j, int mode, TcStage* stg, TcPos tp,
+                                           float* buf) {
+    const int m = k - 1;
+    const Step sp = cb_step(st.ctr[0], sc, st.lr_tab);
+    const size_t NT = net.NT, NH = net.NH, cap = net.cap;
+    float* my = buf + threadIdx.x;
+    auto at = [&](int v) -> float& { return my[v * CB_THREADS]; };
+    enum { V_LO = 2 * NS + 2, V_HI, V_A, V_B0, V_B1, V_UH, V_LH, V_SL };
+    const bool want_terms = mode != 2;
+    const bool prod = k <= net.n - 1;   // the output layer's inputs have no products
+    const int cap_s = valid ? st.caps[s] : 0;
+    const int nsl = min(sp.nadd_before, cap_s);
+    const int bo = sp.nadd_before & 1;
+    const size_t xo = (size_t)s * NT + L.in_off + j;
+    const size_t h = (size_t)s * NH + L.h_in + j, hs = (size_t)s * cap * NH + L.h_in + j;
+    unsigned xs = 0u;
+    bool fixed = false;
+    if (valid) {
+        if (prod) {
             const BfLayer& B = net.bf[k - 1];
-            const int c = L.kind == 1 ? tp.c : j, y = L.kind == 1 ? tp.y : 0, x = L.kind == 1 ? tp.x : 0;
-            const long long off = ((long long)(y + L.pd) * L.Wp + (x + L.pd)) * B.Cip + c;
-            const __nv_bfloat16 xb = __float2bfloat16_rn(xv), zero = __float2bfloat16_rn(0.f);
-            __nv_bfloat16* X = reinterpret_cast<__nv_bfloat16*>(B.X);
-            for (int t = 0; t <= net.cap; ++t) {
-                const long long pl = ((long long)t * net.S + s) * 2;
-                const bool p = t == 0 || ((mpos >> (t - 1)) & 1u), qq = t == 0 || ((mneg >> (t - 1)) & 1u);
-                if (stg) {   // conv tile: the block stores whole 16-byte pieces after the body
-                    stage_at(*stg, 2 * t) = __bfloat16_as_ushort(p ? xb : zero);
-                    stage_at(*stg, 2 * t + 1) = __bfloat16_as_ushort(qq ? xb : zero);
-                } else {
-                    X[pl * B.PX + off] = p ? xb : zero;
-                    X[(pl + 1) * B.PX + off] = qq ? xb : zero;
-                }
+            int c = j, ph = 0, q = 0;
+            if (L.kind == 1) {
+                c = tp.c;
+                const int ty = tp.y + L.pd, tx = tp.x + L.pd;
+                const int Y0 = div_stride(ty, L.st), X0 = div_stride(tx, L.st);
+                ph = (ty - Y0 * L.st) * L.st + (tx - X0 * L.st);
+                q = (Y0 - B.Y0a[ph]) * B.nX[ph] + (X0 - B.X0a[ph]);
             }
-            // the new slot's float32 lambda, kappa (k_slot_sums_t after the row pass) walk these records
-            if (add_iter)
-                slot_rec_plane(net, st, L, s)[xin_pos(L, j)] =
-                    slot_rec(lo, hi, xs_new, fixed, net.ball && L.in_off == 0);
-        } else {
-            // row-pass input record: x* and the slot masks p_b (bits 0-7) and q_b (bits 8-15)
-            reinterpret_cast<float2*>(st.xin + (size_t)s * net.XT + L.xo)[xin_pos(L, j)] =
-                make_float2(xv, __uint_as_float(mpos | (mneg << 8)));
+            const int P = B.nY[ph] * B.nX[ph];
+            const size_t slot = (size_t)net.S * 2 * L.ci * P, neg = (size_t)L.ci * P;
+            const float* d = B.Dcol[ph] + ((size_t)s * 2 * L.ci + c) * P + q;
+#pragma unroll
+            for (int b = 0; b <= NS; ++b) {
+                cp_async4(&at(2 * b), d + b * slot);
+                cp_async4(&at(2 * b + 1), d + b * slot + neg);
+            }
         }
+        cp_async4(&at(V_LO), st.lo + xo);
+        cp_async4(&at(V_HI), st.hi + xo);
+        if (m >= 1) {
+            cp_async4(&at(V_A), st.alpha + h);
+            cp_async4(&at(V_B0), st.beta0 + h);
+            cp_async4(&at(V_B1), st.beta1 + h);
+            cp_async4(&at(V_UH), st.uhat + h);
+            cp_async4(&at(V_LH), st.lhat + h);
+#pragma unroll
+            for (int b = 0; b < NS; ++b) {
+                if (b >= nsl) continue;
+                cp_async4(&at(V_SL + 3 * b), st.bs + hs + (size_t)b * NH);
+                cp_async4(&at(V_SL + 3 * b + 1), st.kap + hs + (size_t)b * NH);
+                if (want_terms) cp_async4(&at(V_SL + 3 * b + 2), st.lam + hs + (size_t)b * NH);
+            }
+        }
+        xs = st.xsnap[bo][xo];
+        fixed = st.efix[xo];
+    }
+    cp_async_wait_all();
+    if (!valid) return;
+    const bool add_iter = (mode != 1) && sp.b_new >= 0;
+    const bool add = add_iter && sp.b_new < cap_s;
+    const float lo = at(V_LO), hi = at(V_HI);
+    const unsigned fxm = fixed ? 0xFFu : 0u;
+    float f;
+    if (prod) {
+        // an interior input (layer 0 over an ellipsoid) is at neither end of its box: eq. (3) gives z
+        const bool interior = net.ball && L.in_off == 0;
+        const unsigned pm = (interior ? 0u : ((~xs) & 0xFFu)) | fxm, qm = (interior ? 0u : xs) | fxm;
+        f = at(0) + at(1);
+#pragma unroll
+        for (int b = 0; b < NS; ++b) {
+            if ((pm >> b) & 1u) f += at(2 + 2 * b);
+            if ((qm >> b) & 1u) f += at(3 + 2 * b);
+        }
+    } else {
+        f = -net.Wout[(size_t)s * L.n_in + j];
+    }
+    double term = 0.0;
+    if (m >= 1) {
+        const float al = at(V_A), b0 = at(V_B0), b1 = at(V_B1), lh = at(V_LH);
+        float sb = 0.f, gk = b0 * at(V_UH) + b1 * lh;
+        double cterm = 0.0;
+#pragma unroll
+        for (int b = 0; b < NS; ++b)
+            if (b < nsl) {
+                const float bb = at(V_SL + 3 * b);
+                sb += bb;
+                gk += bb * at(V_SL + 3 * b + 1);
+                if (want_terms) cterm += (double)bb * at(V_SL + 3 * b + 2);
+            }
+        f += al - b0 - b1 - sb;
+        const bool z = gk >= 0.f;
+        st.zcur[h] = z;
+        if (want_terms) {
+            const float bm = net.L[m - 1].b[j];
+            term = (double)bm * al + (double)b1 * ((double)lh - bm) + cterm - (z ? (double)gk : 0.0);
+        }
+        if (add_iter) {
+            const unsigned zs_old = st.zsnap[bo][h];
+            st.zsnap[bo ^ 1][h] = (uint8_t)(zs_old | ((add && z) ? (1u << sp.b_new) : 0u));
+        }
+    }
+    const bool up = f >= 0.f;
+    const float xv = up ? hi : lo;
+    st.xval[xo] = xv;
+    st.fval[xo] = f;
+    if (want_terms) st.terms[xo] = term - (double)f * xv;
+    unsigned xs_new = xs;
+    if (add_iter) {
+        xs_new = xs | ((add && up) ? (1u << sp.b_new) : 0u);
+        st.xsnap[bo ^ 1][xo] = (uint8_t)xs_new;
+    }
+    if (prod) {
+        // the row pass's tensor-core operand, x* (slot 0) and x* p_b / x* q_b
+        const unsigned mpos = ((~xs_new) & 0xFFu) | fxm, mneg = (xs_new & 0xFFu) | fxm;
+        const BfLayer& B = net.bf[k - 1];
+        const int c = L.kind == 1 ? tp.c : j, y = L.kind == 1 ? tp.y : 0, x = L.kind == 1 ? tp.x : 0;
+        const long long off = ((long long)(y + L.pd) * L.Wp + (x + L.pd)) * B.Cip + c;
+        const __nv_bfloat16 xb = __float2bfloat16_rn(xv), zero = __float2bfloat16_rn(0.f);
+        __nv_bfloat16* X = reinterpret_cast<__nv_bfloat16*>(B.X);
+        for (int t = 0; t <= net.cap; ++t) {
+            const long long pl = ((long long)t * net.S + s) * 2;
+            const bool p = t == 0 || ((mpos >> (t - 1)) & 1u), qq = t == 0 || ((mneg >> (t - 1)) & 1u);
+            if (stg) {   // conv tile: the block stores whole 16-byte pieces after the body
+                stage_at(*stg, 2 * t) = __bfloat16_as_ushort(p ? xb : zero);
+                stage_at(*stg, 2 * t + 1) = __bfloat16_as_ushort(qq ? xb : zero);
+            } else {
+                X[pl * B.PX + off] = p ? xb : zero;
+                X[(pl + 1) * B.PX + off] = qq ? xb : zero;
+            }
+        }
+        // the new slot's float32 lambda, kappa (k_slot_sums_t after the row pass) walk these records
+        if (add_iter)
+            slot_rec_plane(net, st, L, s)[xin_pos(L, j)] = slot_rec(lo, hi, xs_new, fixed, net.ball && L.in_off == 0);
     }
 }
 
@@ -545,16 +654,30 @@ __global__ void __launch_bounds__(CB_THREADS, 4) k_as_colA_t(DNet net, DState st
     const int j = (valid && sg.perm[q]) ? sg.perm[q][o] : o;
     const Step sp = cb_step(st.ctr[0], sc, st.lr_tab);
     const int ns = min(sp.nadd_before, sc.maxcut);
+    if constexpr (TC) {
+        extern __shared__ float colA_buf[];
+        switch (ns) {
+            case 0: as_colA_tc<0>(net, st, sc, L, li + 1, valid, s, j, mode, stg, tp, colA_buf); break;
+            case 1: as_colA_tc<1>(net, st, sc, L, li + 1, valid, s, j, mode, stg, tp, colA_buf); break;
+            case 2: as_colA_tc<2>(net, st, sc, L, li + 1, valid, s, j, mode, stg, tp, colA_buf); break;
+            case 3: as_colA_tc<3>(net, st, sc, L, li + 1, valid, s, j, mode, stg, tp, colA_buf); break;
+            case 4: as_colA_tc<4>(net, st, sc, L, li + 1, valid, s, j, mode, stg, tp, colA_buf); break;
+            case 5: as_colA_tc<5>(net, st, sc, L, li + 1, valid, s, j, mode, stg, tp, colA_buf); break;
+            case 6: as_colA_tc<6>(net, st, sc, L, li + 1, valid, s, j, mode, stg, tp, colA_buf); break;
+            case 7: as_colA_tc<7>(net, st, sc, L, li + 1, valid, s, j, mode, stg, tp, colA_buf); break;
+            default: as_colA_tc<8>(net, st, sc, L, li + 1, valid, s, j, mode, stg, tp, colA_buf); break;
+        }
+    } else
     switch (ns) {
-        case 0: as_colA_body<0>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, TC, stg, tp); break;
-        case 1: as_colA_body<1>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, TC, stg, tp); break;
-        case 2: as_colA_body<2>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, TC, stg, tp); break;
-        case 3: as_colA_body<3>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, TC, stg, tp); break;
-        case 4: as_colA_body<4>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, TC, stg, tp); break;
-        case 5: as_colA_body<5>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, TC, stg, tp); break;
-        case 6: as_colA_body<6>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, TC, stg, tp); break;
-        case 7: as_colA_body<7>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, TC, stg, tp); break;
-        default: as_colA_body<8>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode, TC, stg, tp); break;
+        case 0: as_colA_body<0>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode); break;
+        case 1: as_colA_body<1>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode); break;
+        case 2: as_colA_body<2>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode); break;
+        case 3: as_colA_body<3>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode); break;
+        case 4: as_colA_body<4>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode); break;
+        case 5: as_colA_body<5>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode); break;
+        case 6: as_colA_body<6>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode); break;
+        case 7: as_colA_body<7>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode); break;
+        default: as_colA_body<8>(net, st, sc, L, li + 1, valid, s, j, lane, T, mode); break;
     }
     if (staged) {
         __syncthreads();
@@ -588,8 +711,7 @@ __global__ void __launch_bounds__(CB_THREADS, 4) k_as_colA_t(DNet net, DState st
 // in exact arithmetic.
 template <int NS, bool ADD>
 __device__ __forceinline__ void as_rowB_body(const DNet& net, const DState& st, const DSched& sc, const DLayer& L,
-                                             int li, bool valid, int s, int i, int lane, int T, const Step& sp, int it,
-                                             bool tc, TcStage* stg) {
+                                             int li, bool valid, int s, int i, int lane, int T, const Step& sp, int it) {
     const size_t NT = net.NT, NH = net.NH, cap = net.cap;
     const int cap_s = valid ? st.caps[s] : 0;
     const int newb = (ADD && sp.b_new < cap_s) ? sp.b_new : -1;
@@ -600,21 +722,7 @@ __device__ __forceinline__ void as_rowB_body(const DNet& net, const DState& st, 
     float acc[NS > 0 ? NS : 1];
 #pragma unroll
     for (int b = 0; b < NS; ++b) acc[b] = 0.f;
-    // BF16 form: output channel and position of this row
-    int co = i, p = 0;
-    if (L.kind == 1) {
-        const int hw = L.ho * L.wo;
-        co = i / hw;
-        p = i - co * hw;
-    }
-    if (valid && tc) {
-        const int P = L.ho * L.wo;
-        const size_t slot = (size_t)net.S * P * L.co;
-        const float* d = net.bf[li].Drow + ((size_t)s * L.co + co) * P + p;
-        acc0 = d[0];
-#pragma unroll
-        for (int b = 0; b < NS; ++b) acc[b] = d[(b + 1) * slot];
-    } else if (valid) {
+    if (valid) {
         int g, base;
         row_group(L, i, g, base);
         const float2* xb = reinterpret_cast<const float2*>(st.xin + (size_t)s * net.XT + L.xo) + base;
@@ -658,21 +766,8 @@ __device__ __forceinline__ void as_rowB_body(const DNet& net, const DState& st, 
         const float xhat = acc0 + bi;
         const size_t hs0 = (size_t)s * cap * NH + L.h_out + i;
         const int ap = arec_pos(L, i);
-        // the col pass's record entry e of this row: float32 plane, or (BF16 form) bf16 operand
-        long long roff = 0;
-        if (tc) {
-            const int oy = p / L.wo, ox = p - (p / L.wo) * L.wo;
-            roff = ((long long)(oy + L.hl) * L.Wpo + (ox + L.wl)) * net.bf[li].Cop + co;
-        }
-        auto put = [&](int e, float v) {
-            if (tc && stg)   // conv tile: the block stores whole 16-byte pieces after the body
-                stage_at(*stg, e) = bf16_bits_rn(v);
-            else if (tc)
-                reinterpret_cast<__nv_bfloat16*>(net.bf[li].R)[((long long)e * net.S + s) * net.bf[li].PR + roff] =
-                    __float2bfloat16_rn(v);
-            else
-                *arec_entry(net, st, L, s, ap, e) = v;
-        };
+        // the col pass's record entry e of this row
+        auto put = [&](int e, float v) { *arec_entry(net, st, L, s, ap, e) = v; };
         if (T == 1) {
             // one lane per unit: every load first, so that they are in flight together (the state
             // arrays may alias as far as the compiler knows, so it would not hoist them itself)
@@ -787,16 +882,140 @@ __device__ __forceinline__ void as_rowB_body(const DNet& net, const DState& st, 
         }
     }
     if (T > 1) contrib = team_sum(contrib, T);
-    if (valid && lane == 0) {
-        if (tc && stg) {
+    if (valid && lane == 0) *arec_entry(net, st, L, s, arec_pos(L, i), 0) = contrib;
+}
+
+// Floats per thread of the BF16 row pass's prefetch (as_rowB_tc): the products of slot 0 and of
+// every slot, x, the interval bounds, the nine dual and moment values, five per slot.
+__host__ __device__ constexpr int rowB_tc_vals(int cap) { return 13 + 6 * cap; }
+
+// The BF16 form's row pass for one unit (one lane per unit): as as_rowB_body, but every value it
+// reads from the state is first copied to shared memory with cp.async (this thread's column of
+// buf, rowB_tc_vals(cap) floats a CB_THREADS apart), all copies in flight together without holding
+// registers, so that a block keeps about 170 bytes per thread in flight and the pass streams at the
+// memory's rate rather than its latency.
+template <int NS, bool ADD>
+__device__ __forceinline__ void as_rowB_tc(const DNet& net, const DState& st, const DSched& sc, const DLayer& L,
+                                           int li, bool valid, int s, int i, const Step& sp, int it, TcStage* stg,
+                                           float* buf) {
+    const size_t NT = net.NT, NH = net.NH, cap = net.cap;
+    const int cap_s = valid ? st.caps[s] : 0;
+    const int newb = (ADD && sp.b_new < cap_s) ? sp.b_new : -1;
+    const int bn = (sp.nadd_before + (sp.b_new >= 0 ? 1 : 0)) & 1;
+    const size_t h = (size_t)s * NH + L.h_out + i;
+    const int nsl = min(sp.nadd_before + (sp.b_new >= 0 ? 1 : 0), cap_s);
+    int co = i, p = 0;
+    if (L.kind == 1) {
+        const int hw = L.ho * L.wo;
+        co = i / hw;
+        p = i - co * hw;
+    }
+    float* my = buf + threadIdx.x;
+    auto at = [&](int v) -> float& { return my[v * CB_THREADS]; };
+    enum { V_X = NS + 1, V_UH, V_LH, V_TH, V_M = V_TH + 3, V_V = V_M + 3, V_SL = V_V + 3 };
+    const size_t hs0 = (size_t)s * cap * NH + L.h_out + i;
+    unsigned zs = 0u;
+    float zf = 0.f;
+    if (valid) {
+        const int P = L.ho * L.wo;
+        const size_t slot = (size_t)net.S * P * L.co;
+        const float* d = net.bf[li].Drow + ((size_t)s * L.co + co) * P + p;
+#pragma unroll
+        for (int b = 0; b <= NS; ++b) cp_async4(&at(b), d + b * slot);
+        cp_async4(&at(V_X), st.xval + (size_t)s * NT + L.out_off + i);
+        cp_async4(&at(V_UH), st.uhat + h);
+        cp_async4(&at(V_LH), st.lhat + h);
+        cp_async4(&at(V_TH), st.alpha + h);
+        cp_async4(&at(V_TH + 1), st.beta0 + h);
+        cp_async4(&at(V_TH + 2), st.beta1 + h);
+        cp_async4(&at(V_M), st.ma + h);
+        cp_async4(&at(V_M + 1), st.m0 + h);
+        cp_async4(&at(V_M + 2), st.m1 + h);
+        cp_async4(&at(V_V), st.va + h);
+        cp_async4(&at(V_V + 1), st.v0 + h);
+        cp_async4(&at(V_V + 2), st.v1 + h);
+#pragma unroll
+        for (int b = 0; b < NS; ++b) {
+            if (b >= nsl) continue;
+            const size_t hs = hs0 + (size_t)b * NH;
+            cp_async4(&at(V_SL + 5 * b), st.bs + hs);
+            cp_async4(&at(V_SL + 5 * b + 1), st.ms + hs);
+            cp_async4(&at(V_SL + 5 * b + 2), st.vs + hs);
+            if (!(ADD && b == newb)) {
+                cp_async4(&at(V_SL + 5 * b + 3), st.lam + hs);
+                cp_async4(&at(V_SL + 5 * b + 4), st.kap + hs);
+            }
+        }
+        zs = st.zsnap[bn][h];
+        zf = st.zcur[h] ? 1.f : 0.f;
+    }
+    cp_async_wait_all();
+    float contrib = 0.f;   // rp = -(alpha - beta_1) + sum_b z_b beta_b
+    if (valid) {
+        const float acc0 = at(0);
+        const float bi = L.b[i];
+        const float x = at(V_X), z = zf;
+        const float xhat = acc0 + bi;
+        auto put = [&](int e, float v) {
+            if (stg) {   // conv tile: the block stores whole 16-byte pieces after the body
+                stage_at(*stg, e) = bf16_bits_rn(v);
+            } else {
+                const BfLayer& B = net.bf[li];
+                const int oy = p / L.wo, ox = p - oy * L.wo;
+                const long long roff = ((long long)(oy + L.hl) * L.Wpo + (ox + L.wl)) * B.Cop + co;
+                reinterpret_cast<__nv_bfloat16*>(B.R)[((long long)e * net.S + s) * B.PR + roff] = __float2bfloat16_rn(v);
+            }
+        };
+        const int step = it + 1;
+        const float ib1 = inv_bias_corr(st.bc1_tab, sc.ntab, step, sc.b1);
+        const float ib2 = inv_bias_corr(st.bc2_tab, sc.ntab, step, sc.b2);
+        const float g3[3] = {xhat - x, x - z * at(V_UH), x - xhat + (1.f - z) * at(V_LH)};
+        float th3[3];
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+            float m = at(V_M + v), w2 = at(V_V + v);
+            th3[v] = adam_step(at(V_TH + v), m, w2, g3[v], sp.lr, ib1, ib2, sc);
+            at(V_M + v) = m;
+            at(V_V + v) = w2;
+        }
+        st.alpha[h] = th3[0]; st.beta0[h] = th3[1]; st.beta1[h] = th3[2];
+        st.ma[h] = at(V_M); st.m0[h] = at(V_M + 1); st.m1[h] = at(V_M + 2);
+        st.va[h] = at(V_V); st.v0[h] = at(V_V + 1); st.v1[h] = at(V_V + 2);
+        contrib = th3[2] - th3[0];
+#pragma unroll
+        for (int b = 0; b < NS; ++b) {
+            if (b >= nsl) {
+                put(1 + b, 0.f);
+                continue;
+            }
+            const size_t hs = hs0 + (size_t)b * NH;
+            const bool zb = (zs >> b) & 1u;
+            const float accb = at(1 + b);
+            float lam = at(V_SL + 5 * b + 3), kap = at(V_SL + 5 * b + 4);
+            if (ADD && b == newb) {
+                const float lzh = st.lz[h];
+                lam = zb ? lzh : accb;
+                // kappa = lambda + sum W (1 - I) Ucheck + b: W x* + b at box vertices; over interior
+                // inputs (layer 0, ellipsoid) the z = 0 mask holds fixed inputs only
+                kap = zb ? lzh + bi : (net.ball && L.in_off == 0 ? st.uz[h] + bi : xhat);
+                st.lam[hs] = lam;
+                st.kap[hs] = kap;
+            }
+            const float prod = zb ? acc0 : accb;
+            const float gb = x - prod + lam * (1.f - z) - z * (kap - lam);
+            const int sstep = sp.t - cb_slot_added_at(b, sc) + 1;
+            float m = at(V_SL + 5 * b + 1), w2 = at(V_SL + 5 * b + 2);
+            const float nv = adam_step(at(V_SL + 5 * b), m, w2, gb, sp.lr,
+                                       inv_bias_corr(st.bc1_tab, sc.ntab, sstep, sc.b1),
+                                       inv_bias_corr(st.bc2_tab, sc.ntab, sstep, sc.b2), sc);
+            st.bs[hs] = nv; st.ms[hs] = m; st.vs[hs] = w2;
+            if (zb) contrib += nv;
+            put(1 + b, zb ? 0.f : nv);
+        }
+        if (stg) {
             stage_at(*stg, 0) = bf16_bits_rn(contrib);
-        } else if (tc) {
-            const BfLayer& B = net.bf[li];
-            const int oy = p / L.wo, ox = p - (p / L.wo) * L.wo;
-            const long long roff = ((long long)(oy + L.hl) * L.Wpo + (ox + L.wl)) * B.Cop + co;
-            reinterpret_cast<__nv_bfloat16*>(B.R)[(long long)s * B.PR + roff] = __float2bfloat16_rn(contrib);
         } else {
-            *arec_entry(net, st, L, s, arec_pos(L, i), 0) = contrib;
+            put(0, contrib);
         }
     }
 }
@@ -824,28 +1043,54 @@ __global__ void __launch_bounds__(CB_THREADS, 4) k_as_rowB_t(DNet net, DState st
         for (int e = 0; e <= ns; ++e) stage_at(stage, e) = 0;
     TcStage* stg = staged ? &stage : nullptr;
     const int li = sg.layer[q];
-    if (sp.b_new >= 0) {
+    if constexpr (TC) {
+        extern __shared__ float rowB_buf[];
+        if (sp.b_new >= 0) {
+            switch (ns) {
+                case 1: as_rowB_tc<1, true>(net, st, sc, L, li, valid, s, i, sp, it, stg, rowB_buf); break;
+                case 2: as_rowB_tc<2, true>(net, st, sc, L, li, valid, s, i, sp, it, stg, rowB_buf); break;
+                case 3: as_rowB_tc<3, true>(net, st, sc, L, li, valid, s, i, sp, it, stg, rowB_buf); break;
+                case 4: as_rowB_tc<4, true>(net, st, sc, L, li, valid, s, i, sp, it, stg, rowB_buf); break;
+                case 5: as_rowB_tc<5, true>(net, st, sc, L, li, valid, s, i, sp, it, stg, rowB_buf); break;
+                case 6: as_rowB_tc<6, true>(net, st, sc, L, li, valid, s, i, sp, it, stg, rowB_buf); break;
+                case 7: as_rowB_tc<7, true>(net, st, sc, L, li, valid, s, i, sp, it, stg, rowB_buf); break;
+                default: as_rowB_tc<8, true>(net, st, sc, L, li, valid, s, i, sp, it, stg, rowB_buf); break;
+            }
+        } else {
+            switch (ns) {
+                case 0: as_rowB_tc<0, false>(net, st, sc, L, li, valid, s, i, sp, it, stg, rowB_buf); break;
+                case 1: as_rowB_tc<1, false>(net, st, sc, L, li, valid, s, i, sp, it, stg, rowB_buf); break;
+                case 2: as_rowB_tc<2, false>(net, st, sc, L, li, valid, s, i, sp, it, stg, rowB_buf); break;
+                case 3: as_rowB_tc<3, false>(net, st, sc, L, li, valid, s, i, sp, it, stg, rowB_buf); break;
+                case 4: as_rowB_tc<4, false>(net, st, sc, L, li, valid, s, i, sp, it, stg, rowB_buf); break;
+                case 5: as_rowB_tc<5, false>(net, st, sc, L, li, valid, s, i, sp, it, stg, rowB_buf); break;
+                case 6: as_rowB_tc<6, false>(net, st, sc, L, li, valid, s, i, sp, it, stg, rowB_buf); break;
+                case 7: as_rowB_tc<7, false>(net, st, sc, L, li, valid, s, i, sp, it, stg, rowB_buf); break;
+                default: as_rowB_tc<8, false>(net, st, sc, L, li, valid, s, i, sp, it, stg, rowB_buf); break;
+            }
+        }
+    } else if (sp.b_new >= 0) {
         switch (ns) {
-            case 1: as_rowB_body<1, true>(net, st, sc, L, li, valid, s, i, lane, T, sp, it, TC, stg); break;
-            case 2: as_rowB_body<2, true>(net, st, sc, L, li, valid, s, i, lane, T, sp, it, TC, stg); break;
-            case 3: as_rowB_body<3, true>(net, st, sc, L, li, valid, s, i, lane, T, sp, it, TC, stg); break;
-            case 4: as_rowB_body<4, true>(net, st, sc, L, li, valid, s, i, lane, T, sp, it, TC, stg); break;
-            case 5: as_rowB_body<5, true>(net, st, sc, L, li, valid, s, i, lane, T, sp, it, TC, stg); break;
-            case 6: as_rowB_body<6, true>(net, st, sc, L, li, valid, s, i, lane, T, sp, it, TC, stg); break;
-            case 7: as_rowB_body<7, true>(net, st, sc, L, li, valid, s, i, lane, T, sp, it, TC, stg); break;
-            default: as_rowB_body<8, true>(net, st, sc, L, li, valid, s, i, lane, T, sp, it, TC, stg); break;
+            case 1: as_rowB_body<1, true>(net, st, sc, L, li, valid, s, i, lane, T, sp, it); break;
+            case 2: as_rowB_body<2, true>(net, st, sc, L, li, valid, s, i, lane, T, sp, it); break;
+            case 3: as_rowB_body<3, true>(net, st, sc, L, li, valid, s, i, lane, T, sp, it); break;
+            case 4: as_rowB_body<4, true>(net, st, sc, L, li, valid, s, i, lane, T, sp, it); break;
+            case 5: as_rowB_body<5, true>(net, st, sc, L, li, valid, s, i, lane, T, sp, it); break;
+            case 6: as_rowB_body<6, true>(net, st, sc, L, li, valid, s, i, lane, T, sp, it); break;
+            case 7: as_rowB_body<7, true>(net, st, sc, L, li, valid, s, i, lane, T, sp, it); break;
+            default: as_rowB_body<8, true>(net, st, sc, L, li, valid, s, i, lane, T, sp, it); break;
         }
     } else {
         switch (ns) {
-            case 0: as_rowB_body<0, false>(net, st, sc, L, li, valid, s, i, lane, T, sp, it, TC, stg); break;
-            case 1: as_rowB_body<1, false>(net, st, sc, L, li, valid, s, i, lane, T, sp, it, TC, stg); break;
-            case 2: as_rowB_body<2, false>(net, st, sc, L, li, valid, s, i, lane, T, sp, it, TC, stg); break;
-            case 3: as_rowB_body<3, false>(net, st, sc, L, li, valid, s, i, lane, T, sp, it, TC, stg); break;
-            case 4: as_rowB_body<4, false>(net, st, sc, L, li, valid, s, i, lane, T, sp, it, TC, stg); break;
-            case 5: as_rowB_body<5, false>(net, st, sc, L, li, valid, s, i, lane, T, sp, it, TC, stg); break;
-            case 6: as_rowB_body<6, false>(net, st, sc, L, li, valid, s, i, lane, T, sp, it, TC, stg); break;
-            case 7: as_rowB_body<7, false>(net, st, sc, L, li, valid, s, i, lane, T, sp, it, TC, stg); break;
-            default: as_rowB_body<8, false>(net, st, sc, L, li, valid, s, i, lane, T, sp, it, TC, stg); break;
+            case 0: as_rowB_body<0, false>(net, st, sc, L, li, valid, s, i, lane, T, sp, it); break;
+            case 1: as_rowB_body<1, false>(net, st, sc, L, li, valid, s, i, lane, T, sp, it); break;
+            case 2: as_rowB_body<2, false>(net, st, sc, L, li, valid, s, i, lane, T, sp, it); break;
+            case 3: as_rowB_body<3, false>(net, st, sc, L, li, valid, s, i, lane, T, sp, it); break;
+            case 4: as_rowB_body<4, false>(net, st, sc, L, li, valid, s, i, lane, T, sp, it); break;
+            case 5: as_rowB_body<5, false>(net, st, sc, L, li, valid, s, i, lane, T, sp, it); break;
+            case 6: as_rowB_body<6, false>(net, st, sc, L, li, valid, s, i, lane, T, sp, it); break;
+            case 7: as_rowB_body<7, false>(net, st, sc, L, li, valid, s, i, lane, T, sp, it); break;
+            default: as_rowB_body<8, false>(net, st, sc, L, li, valid, s, i, lane, T, sp, it); break;
         }
     }
     if (staged) {
