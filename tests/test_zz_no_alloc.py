@@ -4,13 +4,15 @@ It serves callers that cannot call cudaMalloc: a verifier embedded in a process 
 memory belongs to another allocator (a framework's caching allocator, a serving engine's fixed
 pool), or a latency-critical caller that cannot take the implicit synchronisation of
 cudaMalloc / cudaFree. These tests call it through the C ABI and check its bounds against the
-ones the context path (as_init) computes, bit for bit, on consecutive calls; that it refuses a
+ones the context path (as_init) computes, bit for bit, on consecutive calls, and against the
+oracle's float64 interval propagation; that it refuses a
 problem larger than its fixed scratch, host pointers, and (where a second GPU exists) memory of
 another device, by its host-side checks alone.
 """
 import numpy as np
 import pytest
 
+from oracle import network as nw
 from paper_2101_05844_gb300 import binding, synth
 
 pytestmark = pytest.mark.gpu
@@ -58,10 +60,18 @@ def test_noalloc_bounds_equal_context_bounds_on_consecutive_calls():
         lh_ref, uh_ref = _context_bounds(prob, S)
         lh, uh = _noalloc_bounds(prob, S, torch)
         assert np.isfinite(lh).all() and np.isfinite(uh).all()
-        # the same float64 accumulation in the same lane order and the same outward rounding as the
-        # context's interval bounds: bit for bit
+        # the same compensated accumulation in the same lane order and the same outward rounding as
+        # the context's interval bounds: bit for bit
         np.testing.assert_array_equal(lh, lh_ref)
         np.testing.assert_array_equal(uh, uh_ref)
+        # and against the oracle's float64 interval propagation (App. E): sound (the float32 interval
+        # contains it) and within a few float32 ulps per layer
+        for s, P in enumerate(nw.problems(prob)):
+            rl = np.concatenate([np.asarray(P.lhat[k]) for k in range(1, P.n)])
+            ru = np.concatenate([np.asarray(P.uhat[k]) for k in range(1, P.n)])
+            assert (lh[s] <= rl + 1e-9 * (1 + np.abs(rl))).all() and (uh[s] >= ru - 1e-9 * (1 + np.abs(ru))).all()
+            assert (np.abs(lh[s] - rl) <= 4e-6 * (1 + np.abs(rl))).all()
+            assert (np.abs(uh[s] - ru) <= 4e-6 * (1 + np.abs(ru))).all()
         if prob.get("splits") is not None:
             # the split branch runs: some split neurons were clamped to zero at one end
             sp = prob["splits"]
