@@ -108,7 +108,6 @@ struct DState {
     double* best;                    // [S]
     const int* caps;                 // [S]
     int* ctr;                        // [0] AS iteration, [1] SP iteration, [2] SP-init step
-    unsigned* done;                  // block-completion counters [4]
     const float* lr_tab;             // [ntab] step size per global iteration
     const float* bc1_tab;            // [ntab] 1 / (1 - b1^step), step = index
     const float* bc2_tab;            // [ntab] 1 / (1 - b2^step)

@@ -57,19 +57,10 @@ __device__ __forceinline__ int seg_of(const Segs& sg, int blk) {
     return q;
 }
 
-// Last block of a launch: every block calls this at exit; returns true in exactly one block,
-// after every other block of the launch has finished its writes.
-__device__ __forceinline__ bool last_block(unsigned* counter) {
-    __shared__ bool is_last;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        unsigned prev = atomicAdd(counter, 1u);
-        is_last = (prev == gridDim.x - 1);
-    }
-    __syncthreads();
-    return is_last;
-}
+// Advances the iteration counter ctr[i] (0: Active Set, 1: Saddle Point, 2: primal
+// initialisation) after the launch that completes an iteration: stream order has every block of
+// that launch done before it, and the next launches read the new value.
+__global__ void k_advance(int* ctr, int i) { ctr[i] += 1; }
 
 // 1 / (1 - beta^step), the Adam bias corrections, from a table built in FP64 on the host.
 __device__ __forceinline__ float inv_bias_corr(const float* tab, int ntab, int step, float beta) {

@@ -1109,10 +1109,6 @@ __global__ void __launch_bounds__(CB_THREADS, 4) k_as_rowB_t(DNet net, DState st
                         });
         }
     }
-    if (last_block(&st.done[0]) && threadIdx.x == 0) {
-        st.ctr[0] = it + 1;
-        st.done[0] = 0;
-    }
 }
 
 // ---------------------------------------------------------------- slot row sums
@@ -1526,7 +1522,7 @@ __global__ void __launch_bounds__(CB_THREADS) k_sp_rowB_t(DNet net, DState st, D
 // P_bar_k = (W_k o I_dagger)^T beta_bar for input j (the masked backward product of the chosen
 // masks) and (W_k^T alpha_k)[j] at the updated alpha. The epilogue takes the convex combination of
 // P_k and of the primal iterate (x_m, z_m) into the other buffer (Alg. 2), then runs phase A at
-// the new iterate. The last block advances the iteration counter.
+// the new iterate. The launch after it (k_advance) advances the iteration counter.
 __global__ void __launch_bounds__(CB_THREADS) k_sp_colCA_t(DNet net, DState st, DSched sc, TSegs sg) {
     const int q = tseg_of(sg, blockIdx.x);
     const int li = sg.layer[q];
@@ -1578,10 +1574,6 @@ __global__ void __launch_bounds__(CB_THREADS) k_sp_colCA_t(DNet net, DState st, 
             st.spz[nxt][hh] = om * st.spz[cur][hh] + gamma * (st.zbar[hh] ? 1.f : 0.f);
         }
         sp_phaseA_epilogue(net, st, L, k, u.s, u.idx, accA, nxt, 0);
-    }
-    if (last_block(&st.done[1]) && threadIdx.x == 0) {
-        st.ctr[1] = t + 1;
-        st.done[1] = 0;
     }
 }
 
@@ -1684,10 +1676,6 @@ __global__ void __launch_bounds__(CB_THREADS) k_spi_col_t(DNet net, DState st, D
             st.spx[cur][xo] = st.spx[cur][xo] + eta * f;
         else
             st.spx[cur][xo] = fminf(fmaxf(st.spx[cur][xo] + eta * f, st.lo[xo]), st.hi[xo]);
-    }
-    if (last_block(&st.done[2]) && threadIdx.x == 0) {
-        st.ctr[2] = step + 1;
-        st.done[2] = 0;
     }
 }
 
