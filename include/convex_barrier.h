@@ -228,7 +228,8 @@ long long as_launch_count(as_ctx* ctx);
 #define AS_K_BATCH 12     /* a batch's set-up (as_init, as_reset): box checks, property rows,
                              interval bounds, row constants, fixed inputs                   */
 #define AS_K_SP_START 13  /* Saddle Point's start: statistics (eq. 10), caps (eq. 16), records */
-#define AS_K_COUNT 14
+#define AS_K_COUNTER 14   /* the one-thread launches that advance the iteration counters  */
+#define AS_K_COUNT 15
 
 /* With as_options.profile set: total device time (CUDA events on the context's stream) and
  * launch count of one kernel over the context's life so far. Synchronises the stream. */

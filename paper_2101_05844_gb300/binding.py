@@ -38,7 +38,7 @@ EXPORTS = ["as_default_options", "as_init", "as_reset", "as_step", "sp_step", "a
            "as_team_targets", "as_intermediate_bounds", "as_bab", "as_bab_default_options", "as_bound_backward_ibp",
            "as_export_size", "as_export_state", "as_import_state"]
 KERNELS = ["as_colA", "as_rowB", "reduce", "sp_colA", "sp_rowB", "sp_colC", "spi_row", "spi_col", "tc_col",
-           "tc_row", "slot_sums", "ball_x0", "batch", "sp_start"]
+           "tc_row", "slot_sums", "ball_x0", "batch", "sp_start", "counter"]
 
 
 class Layer(ct.Structure):

@@ -11,7 +11,7 @@
 // Kernel ids for per-kernel timing (as_kernel_times).
 enum { CB_K_AS_COLA = 0, CB_K_AS_ROWB, CB_K_REDUCE, CB_K_SP_COLA, CB_K_SP_ROWB, CB_K_SP_COLC,
        CB_K_SPI_ROW, CB_K_SPI_COL, CB_K_TC_COL, CB_K_TC_ROW, CB_K_SLOT_SUMS, CB_K_BALL_X0,
-       CB_K_BATCH, CB_K_SP_START, CB_NPROF };
+       CB_K_BATCH, CB_K_SP_START, CB_K_COUNTER, CB_NPROF };
 
 // One affine layer k (1-based in the paper; stored at index k-1).
 struct DLayer {

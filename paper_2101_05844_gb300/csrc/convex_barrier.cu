@@ -871,7 +871,7 @@ static int launch_as_iter(as_ctx* c, cudaStream_t s) {
     if (c->opt.track_best)
         LAUNCH(c, s, CB_K_REDUCE, (k_reduce<<<c->net.S, CB_THREADS, 0, s>>>(c->net, c->st, 64, nullptr, 1)));
     LAUNCH(c, s, CB_K_AS_ROWB, (k_as_rowB_t<false><<<c->blocksTB, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->tB)));
-    LAUNCH(c, s, CB_K_AS_ROWB, (k_advance<<<1, 1, 0, s>>>(c->st.ctr, 0)));
+    LAUNCH(c, s, CB_K_COUNTER, (k_advance<<<1, 1, 0, s>>>(c->st.ctr, 0)));
     return check_launch(c, "Active Set iteration");
 }
 
@@ -880,7 +880,7 @@ static int launch_as_iter(as_ctx* c, cudaStream_t s) {
 static int launch_sp_iter(as_ctx* c, cudaStream_t s) {
     LAUNCH(c, s, CB_K_SP_ROWB, (k_sp_rowB_t<<<c->blocksTB, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->tB)));
     LAUNCH(c, s, CB_K_SP_COLC, (k_sp_colCA_t<<<c->blocksTA, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->tA)));
-    LAUNCH(c, s, CB_K_SP_COLC, (k_advance<<<1, 1, 0, s>>>(c->st.ctr, 1)));
+    LAUNCH(c, s, CB_K_COUNTER, (k_advance<<<1, 1, 0, s>>>(c->st.ctr, 1)));
     if (c->net.ball) LAUNCH(c, s, CB_K_BALL_X0, (k_ball_sp<<<c->net.S, CB_BALL_THREADS, 0, s>>>(c->net, c->st, 0)));
     if (c->opt.track_best)
         LAUNCH(c, s, CB_K_REDUCE, (k_reduce<<<c->net.S, CB_THREADS, 0, s>>>(c->net, c->st, 64, nullptr, 1)));
@@ -961,7 +961,7 @@ static int sp_start(as_ctx* c) {
     for (int t = 0; t < c->opt.sp_init_steps; ++t) {
         LAUNCH(c, s, CB_K_SPI_ROW, (k_spi_row_t<<<c->blocksTB, CB_THREADS, 0, s>>>(c->net, c->st, c->tB)));
         LAUNCH(c, s, CB_K_SPI_COL, (k_spi_col_t<<<c->blocksTA, CB_THREADS, 0, s>>>(c->net, c->st, c->sc, c->tA)));
-        LAUNCH(c, s, CB_K_SPI_COL, (k_advance<<<1, 1, 0, s>>>(c->st.ctr, 2)));
+        LAUNCH(c, s, CB_K_COUNTER, (k_advance<<<1, 1, 0, s>>>(c->st.ctr, 2)));
         if (c->net.ball)
             LAUNCH(c, s, CB_K_BALL_X0, (k_ball_retract<<<c->net.S, CB_BALL_THREADS, 0, s>>>(c->net, c->st)));
     }
