@@ -551,7 +551,13 @@ def conv4_roofline(binding, torch, dev, net, S, kt, opt):
                     "bytes_per_launch": algo / n,
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks
                     else "fallback 6.8 TB/s (of fallback)",
-                    "traffic": captured_traffic("conv4", top, S)})
+                    "traffic": captured_traffic("conv4", top, S),
+                    # the captured launch has all C4_CAP slots in use: its algorithmic bytes, to
+                    # compare the traffic with (bytes_per_launch averages over the slot schedule)
+                    "traffic_launch": f"Active Set iteration with {C4_CAP} slots, captured at 128 boxes, "
+                                      "scaled to the batch",
+                    "traffic_algorithmic": S * float((colA_bf16_bytes if top == "as_colA" else rowB_bf16_bytes)(
+                        net, C4_CAP, C4_CAP))})
     elif top in ("tc_col", "tc_row"):
         nsl = col if top == "tc_col" else row
         layers = len(net) - 1
