@@ -70,10 +70,14 @@ def fp32_peak_tflops(torch, dev):
     return sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12, f"{sms} SMs x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz ({src})"
 
 
+# the BF16 contexts time their products' plans at as_init (as_options.autotune), before any timing
+TC_AUTOTUNE = int(os.environ.get("CB_BENCH_TC_AUTOTUNE", "1"))
+
+
 def conv4_options(binding, precision, profile=0, graph_chunk=25, bigm=C4_BIGM, as_iters=C4_AS, omega=C4_OMEGA):
     return binding.default_options(bigm_iters=bigm, as_iters=as_iters, omega=omega, max_cuts=C4_CAP,
                                    graph_chunk=graph_chunk, profile=profile, precision=precision,
-                                   sp_init_steps=C4_SP_INIT)
+                                   sp_init_steps=C4_SP_INIT, autotune=TC_AUTOTUNE if precision == 16 else 0)
 
 
 def conv4_step(ctx, batch, out_as, out_sp, events=None):

@@ -80,9 +80,11 @@ typedef struct as_options {
     int track_best;      /* 1: evaluate the bound at every iteration and keep the best        */
     int graph_chunk;     /* iterations per captured CUDA graph (0: plain launches)           */
     int profile;         /* 1: time every kernel with CUDA events (disables graphs)           */
-    int autotune;        /* 1: as_init times the float32 passes' team-size targets (threads per
-                          * layer segment) on this context's net and batch, a few iterations
-                          * each, and keeps the fastest (see as_team_targets); 0: defaults  */
+    int autotune;        /* 1: as_init times, on this context's net and batch, the float32
+                          * passes' team-size targets (threads per layer segment, a few
+                          * iterations each; see as_team_targets) or, in the BF16 form, each
+                          * tensor-core product's plan (window or gathered operands, N tile
+                          * width), and keeps the fastest; 0: defaults                       */
     int precision;       /* products of the Big-M / Active Set passes: 32 (float32, default) or
                           * 16 (the BF16 form: W x* and every masked product (W o I_b) x*, W^T and
                           * every masked W^T product run on the tensor cores with bf16 operands

@@ -62,6 +62,7 @@ struct as_ctx {
         int win = 0, mt = 1, smem = 0;   // window operands (k_gemm_wgroup_bf16): row blocks per CTA, bytes
     };
     std::vector<TcGemm> tc_row, tc_col;           // per hidden-output layer
+    std::vector<TcGemm> tc_row_alt, tc_col_alt;   // gathered-operand plans beside window ones (autotune)
     std::vector<std::pair<void*, size_t>> planes; // bf16 operand planes, cleared with each batch
     int* tc_status = nullptr;                     // set by a tensor-core kernel whose wait ran out
     TSegs tA1{}, tB1{};                           // one lane per unit
@@ -122,6 +123,7 @@ static int dalloc(as_ctx* c, T** p, size_t count) {
 // defined further down (cb_bf16.inc, cb_host_extra.inc)
 static int clear_planes(as_ctx* c);
 static int build_bf16(as_ctx* c, const std::vector<std::vector<float>>& Wh);
+static int autotune_tc(as_ctx* c);
 static int recompute_slot_sums(as_ctx* c);
 
 extern "C" void as_default_options(as_options* o) {
@@ -820,6 +822,10 @@ static int init_impl(as_ctx* c, const as_net* net, int S, const float* x_lo, con
     if (c->opt.autotune && c->opt.precision == 32) {
         TRY(autotune_teams(c));
         TRY(load_batch(c, x_lo, x_hi, C, lhat, uhat, splits, caps, false));   // back to zero duals
+    }
+    if (c->opt.autotune && c->opt.precision == 16) {
+        TRY(autotune_tc(c));
+        TRY(load_batch(c, x_lo, x_hi, C, lhat, uhat, splits, caps, false));   // clean planes
     }
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     return AS_OK;

@@ -283,3 +283,26 @@ def test_window_and_gathered_products_agree(monkeypatch):
     for a, b in zip(out["1"], out["0"]):
         close = np.abs(a - b) <= 1e-5 * (1 + np.abs(b))
         assert close.mean() >= 0.999, close.mean()
+
+
+def test_autotuned_products_keep_the_bound():
+    """as_options.autotune in the BF16 form times each product's plans (window operands, gathered
+    operands at N tiles of 32-256 columns) and keeps the fastest: the bound stays within the bf16
+    gap of the oracle on the small conv net, and on 8 boxes of the conv4 batch it equals the untuned
+    context's up to the summation order of the products."""
+    prob = synth.problem("small_conv", S=3, seed=0)
+    kw = dict(bigm_iters=20, as_iters=40, omega=12, max_cuts=5)
+    ctx = binding.context_for(prob, binding.default_options(graph_chunk=0, precision=16, autotune=1, **kw))
+    ctx.as_step(60)
+    b = ctx.bound()
+    for s, P in enumerate(nw.problems(prob)):
+        ref = AS.ActiveSet(P, AS.Options(**kw)).step(60).bound()
+        assert abs(b[s] - ref) <= GAP * (1 + abs(ref))
+    kw = dict(bigm_iters=20, as_iters=40, omega=12, max_cuts=5)
+    prob = synth.problem("conv4", S=1024, seed=0, part=(0, 8))
+    out = []
+    for tune in (1, 0):
+        ctx = binding.context_for(prob, binding.default_options(graph_chunk=25, precision=16, autotune=tune, **kw))
+        ctx.as_step(60)
+        out.append(ctx.bound())
+    np.testing.assert_allclose(out[0], out[1], rtol=1e-3, atol=1e-3)
